@@ -1,0 +1,253 @@
+"""Oracle lambda weights and ensemble mixture, FP64 (numpy + math.erf).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The ensemble hypothesis (Sec. II, Eq. ensemble_hypothesis) writes a high-Reynolds-number average as
+an integral over the injection-rate parameter lambda with weight P(lambda; Z).
+For the quadratic scaling exponents zeta_p = p/3 - c (p^2 - 3p)/2 (Sec. IV, Eq. quadratic_scaling_exponents),
+K(t; Z) = 9 c (t^2 - t) Z / 2 (Sec. IV) and P is Gaussian with mean
+-9cZ/2 and variance 9cZ (Sec. IV, Eq. gaussian_lambda_pdf).  Each member owns a lambda bin and its
+weight is the integral of P over that bin (Sec. IV, after Eq. gaussian_lambda_pdf); any
+average is then a weighted sum over members, e.g. PDFs (Sec. II, Eq.
+pdf_superposition) and the skewness prediction (Sec. VII).
+
+Readings [R] where the paper is silent:
+  - bin edges are midpoints between neighbouring distinct lambda values; the
+    outer edges lie half a neighbour spacing beyond the extreme members; a
+    single member's bin is the whole line;
+  - members with equal lambda share their bin's mass equally;
+  - weights are renormalised to sum to one by default; the raw covered mass
+    is returned alongside;
+  - Z = 0 is the delta distribution at lambda = 0 (Sec. VII).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# lambda distributions
+# ---------------------------------------------------------------------------
+def zeta_quadratic(p, c=0.023):
+    """Log-normal scaling exponents, Sec. IV, Eq. quadratic_scaling_exponents."""
+    return p / 3.0 - c * (p * p - 3.0 * p) / 2.0
+
+
+def K_from_zeta(t, Z, zeta):
+    """Cumulant generating function from Sec. III, Eq. exponents_KZ_1: K(p/3; Z) = (p/3 - zeta_p) Z."""
+    return (t - zeta(3.0 * t)) * Z
+
+
+def gauss_params(c, Z):
+    """Mean and standard deviation of P(lambda; Z), Sec. IV, Eq. gaussian_lambda_pdf."""
+    return -4.5 * c * Z, math.sqrt(9.0 * c * Z)
+
+
+def gauss_pdf(lam, c, Z):
+    """P(lambda; Z) of Sec. IV, Eq. gaussian_lambda_pdf, written out."""
+    lam = np.asarray(lam, dtype=np.float64)
+    return np.exp(-(lam + 9.0 * c * Z / 2.0) ** 2 / (18.0 * c * Z)) / math.sqrt(18.0 * math.pi * c * Z)
+
+
+def _norm_cdf(x):
+    """Standard normal CDF, accurate in both tails."""
+    if x == math.inf:
+        return 1.0
+    if x == -math.inf:
+        return 0.0
+    return 0.5 * math.erfc(-x / math.sqrt(2.0))
+
+
+def _norm_sf(x):
+    """Standard normal upper tail 1 - CDF."""
+    if x == math.inf:
+        return 0.0
+    if x == -math.inf:
+        return 1.0
+    return 0.5 * math.erfc(x / math.sqrt(2.0))
+
+
+def normal_interval_mass(a, b, mu, sigma):
+    """Mass of N(mu, sigma^2) on [a, b]; differences taken on the tail
+    closer to the interval so that tiny masses keep their digits."""
+    za, zb = (a - mu) / sigma, (b - mu) / sigma
+    if za >= 0.0:
+        return _norm_sf(za) - _norm_sf(zb)
+    return _norm_cdf(zb) - _norm_cdf(za)
+
+
+def truncated_gauss_params(c, Z):
+    """Appendix, Eq. truncated_gaussian: P = N exp(-(lambda-mu)^2 / (18 c Z)) Theta(Z - lambda).
+    Returns (mu, sigma, cut) with mu solved in FP64 so that int P e^lambda = 1.
+    Normalisation: N = 1 / (sigma sqrt(2 pi) Phi((Z - mu)/sigma))."""
+    sigma = math.sqrt(9.0 * c * Z)
+
+    def constraint(mu):
+        # int_{-inf}^{Z} e^l N(l; mu, s^2) dl / Phi((Z - mu)/s) - 1, in logs
+        a = mu + 0.5 * sigma * sigma
+        return a + math.log(_norm_cdf((Z - mu - sigma * sigma) / sigma)) - math.log(
+            _norm_cdf((Z - mu) / sigma))
+
+    lo, hi = -4.5 * c * Z - 10.0 * sigma - 1.0, 10.0
+    flo, fhi = constraint(lo), constraint(hi)
+    assert flo < 0.0 < fhi
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        f = constraint(mid)
+        if f < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi), sigma, Z
+
+
+def lambda_pdf_from_K(K, lam_grid):
+    """Numerical inverse two-sided Laplace transform (Sec. VII): evaluate
+    exp(K(i s)) (the characteristic function) and Fourier-transform it.
+    K must accept complex arguments.  Returns P on lam_grid (uniform)."""
+    lam = np.asarray(lam_grid, dtype=np.float64)
+    n = lam.size
+    dl = lam[1] - lam[0]
+    s = 2.0 * math.pi * np.fft.fftfreq(n, d=dl)
+    phi = np.exp(np.array([K(1j * si) for si in s], dtype=np.complex128))
+    # P(l) = 1/(2 pi) int ds exp(-i s l) phi(s)  ~  (1/(n dl)) sum_s exp(-i s l) phi(s)
+    P = np.real(np.exp(-1j * np.outer(lam - lam[0], s)) @ (phi * np.exp(-1j * s * lam[0]))) / (n * dl)
+    return P
+
+
+# ---------------------------------------------------------------------------
+# lambda bins and member weights
+# ---------------------------------------------------------------------------
+def lambda_bins(lams):
+    """Per-member bin [lo, hi] and the multiplicity of its lambda value."""
+    lams = np.asarray(lams, dtype=np.float64)
+    vals = np.unique(lams)
+    if vals.size == 1:
+        edges = np.array([-math.inf, math.inf])
+    else:
+        mids = 0.5 * (vals[1:] + vals[:-1])
+        edges = np.concatenate(([vals[0] - 0.5 * (vals[1] - vals[0])], mids,
+                                [vals[-1] + 0.5 * (vals[-1] - vals[-2])]))
+    lo = np.empty_like(lams)
+    hi = np.empty_like(lams)
+    mult = np.empty_like(lams)
+    for i, l in enumerate(lams):
+        j = int(np.searchsorted(vals, l))
+        lo[i], hi[i] = edges[j], edges[j + 1]
+        mult[i] = np.count_nonzero(lams == l)
+    return lo, hi, mult
+
+
+def member_weights(lams, kind="gauss_paper", c=0.023, Z=1.0, mu=0.0, sigma=1.0, user=None,
+                   renormalize=True):
+    """Bin masses w_i of the members; returns (w, covered_mass).
+
+    kind: 'gauss_paper' (Eq. gaussian_lambda_pdf with c, Z), 'gauss'
+    (mu, sigma), 'trunc_gauss' (Appendix, c, Z) or 'user' (given weights)."""
+    lams = np.asarray(lams, dtype=np.float64)
+    lo, hi, mult = lambda_bins(lams)
+    w = np.zeros_like(lams)
+    if kind == "user":
+        w = np.asarray(user, dtype=np.float64).copy()
+    elif kind == "gauss_paper" and Z == 0.0:
+        # P(lambda; 0) = delta(lambda): the whole mass sits in the bin holding 0
+        for i in range(lams.size):
+            if lo[i] <= 0.0 < hi[i]:
+                w[i] = 1.0 / mult[i]
+    elif kind in ("gauss_paper", "gauss"):
+        m, s = gauss_params(c, Z) if kind == "gauss_paper" else (mu, sigma)
+        for i in range(lams.size):
+            w[i] = normal_interval_mass(lo[i], hi[i], m, s) / mult[i]
+    elif kind == "trunc_gauss":
+        m, s, cut = truncated_gauss_params(c, Z)
+        norm = _norm_cdf((cut - m) / s)
+        for i in range(lams.size):
+            a, b = lo[i], min(hi[i], cut)
+            w[i] = (normal_interval_mass(a, b, m, s) / norm / mult[i]) if b > a else 0.0
+    else:
+        raise ValueError(kind)
+    covered = float(w.sum())
+    if renormalize and covered > 0.0:
+        w = w / covered
+    return w, covered
+
+
+# ---------------------------------------------------------------------------
+# mixture of member statistics
+# ---------------------------------------------------------------------------
+def mix_counts(counts, weights, h):
+    """Weighted PDFs from per-member histogram counts (Sec. II, Eq. pdf_superposition, discretised):
+    PDF_mix(b) = sum_i w_i h_i(b) / (n_i db), n_i = all points of member i.
+    counts: [n_members, counts_len] (layout of oracle.HistSpec).
+    Returns (pdf_qr [nq, nq], pdf_eps [nt], pdf_ens [nt]) per unit of the
+    bin coordinates (Q/q0, R/q0^1.5; log10 of the tail variables)."""
+    counts = np.asarray(counts, dtype=np.float64)
+    nq, nt = h.qr_bins, h.tail_bins
+    npts = counts[:, nq * nq + 2 * nt + 6]
+    frac = counts / npts[:, None]
+    mix = (np.asarray(weights)[:, None] * frac).sum(axis=0)
+    dq = 2.0 * h.q_lim / nq
+    dr = 2.0 * h.r_lim / nq
+    dl = (h.tail_hi - h.tail_lo) / nt
+    qr = mix[: nq * nq].reshape(nq, nq) / (dq * dr)
+    e = mix[nq * nq: nq * nq + nt] / dl
+    w = mix[nq * nq + nt: nq * nq + 2 * nt] / dl
+    return qr, e, w
+
+
+def mix_moments(moments, npoints, weights):
+    """<X^p>_mix = sum_i w_i <X^p>_i (Sec. II, Eq. ensemble_hypothesis with X a power)."""
+    moments = np.asarray(moments, dtype=np.float64)
+    per = moments / np.asarray(npoints, dtype=np.float64)[:, None]
+    return (np.asarray(weights)[:, None] * per).sum(axis=0)
+
+
+LONGITUDINAL = (0, 4, 8)          # A_11, A_22, A_33 (row-major index)
+TRANSVERSE = (1, 2, 3, 5, 6, 7)
+
+
+def gradient_moment_ratios(mixed):
+    """Skewness, flatness and hyper-flatness of gradient components from
+    mixed moments (Sec. VII, Eq. def_skewness_flatness and the skewness
+    prediction that follows it), isotropy-averaged over the three
+    longitudinal and six transverse components.  mixed: the 48 mixed
+    moment averages (layout of the stats moments)."""
+    def avg(comps, p):
+        idx = {2: 0, 3: 1, 4: 2, 6: 3}[p]
+        return float(np.mean([mixed[4 * c + idx] for c in comps]))
+    L2, L3, L4, L6 = (avg(LONGITUDINAL, p) for p in (2, 3, 4, 6))
+    T2, T4, T6 = (avg(TRANSVERSE, p) for p in (2, 4, 6))
+    return {"S_long": L3 / L2 ** 1.5, "F_long": L4 / L2 ** 2, "F_trans": T4 / T2 ** 2,
+            "H_long": L6 / L2 ** 3, "H_trans": T6 / T2 ** 3}
+
+
+def member_contributions(counts, weights, h, which="eps"):
+    """Per-member contribution w_i h_i(b)/n_i to each tail bin (Sec. VII,
+    choice of the lambda range): [n_members, nt]."""
+    counts = np.asarray(counts, dtype=np.float64)
+    nq, nt = h.qr_bins, h.tail_bins
+    npts = counts[:, nq * nq + 2 * nt + 6]
+    off = nq * nq + (0 if which == "eps" else nt)
+    return np.asarray(weights)[:, None] * counts[:, off:off + nt] / npts[:, None]
+
+
+def hellinger(p, q):
+    """Hellinger distance between two discrete distributions (each
+    normalised to unit sum here)."""
+    p = np.asarray(p, dtype=np.float64).ravel()
+    q = np.asarray(q, dtype=np.float64).ravel()
+    p = p / p.sum()
+    q = q / q.sum()
+    return math.sqrt(max(0.0, 1.0 - float(np.sum(np.sqrt(p * q)))))
+
+
+def cost_ratio(R_ref, R_ens, n):
+    """Sec. VI, cost estimate: Cost_DNS / Cost_ens ~ (R_ref / R_ens)^5 / n."""
+    return (R_ref / R_ens) ** 5 / n
+
+
+def Z_from_Rlambda(R_ref, R_ens):
+    """Sec. V, Eq. Rlambda_Z_relation: R_ref ~ exp(2Z/3) with the constant fixed at Z = 0."""
+    return 1.5 * math.log(R_ref / R_ens)

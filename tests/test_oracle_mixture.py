@@ -1,0 +1,151 @@
+"""Pins of the oracle lambda weights and mixture (no GPU).
+
+Pins: the mean-injection constraint int P e^lambda = 1 (Sec. II), the
+convolution property P(.; 2Z) = P(.; Z) * P(.; Z) (Sec. III), the printed
+bin mass 3.1e-6 of the member at lambda = 3.93 for R_lambda = 1300 with
+ens256 (Sec. VII), the printed cost ratio 7.8e4 (Sec. VI), Z = 0 giving the
+central member (Sec. VII), the truncated Gaussian of the Appendix, and the
+numerical inverse Laplace transform (Sec. VII) reproducing the Gaussian.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.mixture as M
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")
+
+
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def test_gaussian_pdf_moments_and_constraint():
+    c, Z = 0.023, 2.0
+    lam = np.linspace(-30, 30, 600001)
+    P = M.gauss_pdf(lam, c, Z)
+    assert np.trapezoid(P, lam) == pytest.approx(1.0, abs=1e-12)
+    assert np.trapezoid(P * np.exp(lam), lam) == pytest.approx(1.0, abs=1e-10)
+    mu, s = M.gauss_params(c, Z)
+    assert np.trapezoid(P * lam, lam) == pytest.approx(mu, abs=1e-12)
+    assert np.trapezoid(P * (lam - mu) ** 2, lam) == pytest.approx(s * s, rel=1e-10)
+    # K(t; Z) = log int P e^{lambda t} equals 9c(t^2 - t)Z/2 and (t - zeta_3t) Z
+    for t in (0.5, 1.0, 2.0, 3.0):
+        K = math.log(np.trapezoid(P * np.exp(lam * t), lam))
+        assert K == pytest.approx(9 * c * (t * t - t) * Z / 2, abs=1e-9)
+        assert K == pytest.approx(M.K_from_zeta(t, Z, lambda p: M.zeta_quadratic(p, c)), abs=1e-9)
+
+
+def test_convolution_property():
+    c, Z = 0.023, 1.3
+    lam = np.linspace(-20, 20, 8001)
+    dl = lam[1] - lam[0]
+    P1 = M.gauss_pdf(lam, c, Z)
+    conv = np.convolve(P1, P1, mode="same") * dl
+    P2 = M.gauss_pdf(lam, c, 2 * Z)
+    assert np.abs(conv - P2).max() < 1e-9 * P2.max()
+
+
+def test_paper_bin_mass_pin():
+    g = golden()["bin_mass_lambda_3.93"]
+    lams = np.linspace(g["lambda_min"], g["lambda_max"], g["n_members"])
+    Z = M.Z_from_Rlambda(g["R_ref"], g["R_ens"])
+    w, covered = M.member_weights(lams, "gauss_paper", c=g["c"], Z=Z, renormalize=False)
+    i = int(np.argmin(np.abs(lams - g["lambda"])))
+    assert abs(lams[i] - g["lambda"]) < 0.02
+    # the paper prints 3.1e-6 (two digits)
+    assert round(w[i] * 1e7) / 10 == pytest.approx(g["mass"] * 1e6, abs=0.051)
+    assert 0.999 < covered <= 1.0
+
+
+def test_paper_cost_ratio_pin():
+    g = golden()["cost_ratio"]
+    r = M.cost_ratio(g["R_ref"], g["R_ens"], g["n"])
+    assert r == pytest.approx(g["value"], rel=0.01)
+
+
+def test_scale_gap_zero_gives_central_member():
+    lams = np.linspace(-3, 3, 7)
+    w, covered = M.member_weights(lams, "gauss_paper", c=0.023, Z=0.0)
+    assert w[3] == 1.0 and w.sum() == 1.0
+
+
+def test_weights_bins_and_duplicates():
+    lams = np.array([0.0, 1.0, 1.0, 3.0])
+    lo, hi, mult = M.lambda_bins(lams)
+    assert list(lo) == [-0.5, 0.5, 0.5, 2.0] and list(hi) == [0.5, 2.0, 2.0, 4.0]
+    assert list(mult) == [1, 2, 2, 1]
+    w, cov = M.member_weights(lams, "gauss", mu=0.5, sigma=1.0, renormalize=False)
+    ref_mid = (M._norm_cdf(1.5) - M._norm_cdf(0.0)) / 2
+    assert w[1] == pytest.approx(ref_mid, rel=1e-14) and w[1] == w[2]
+    assert cov == pytest.approx(M._norm_cdf(3.5) - M._norm_cdf(-1.0), rel=1e-14)
+    wn, _ = M.member_weights(lams, "gauss", mu=0.5, sigma=1.0)
+    assert wn.sum() == pytest.approx(1.0, abs=1e-15)
+    # a single member owns the whole line
+    w1, c1 = M.member_weights([0.4], "gauss", mu=-3, sigma=0.1, renormalize=False)
+    assert w1[0] == 1.0 and c1 == 1.0
+
+
+def test_truncated_gaussian():
+    c, Z = 0.023, 2.0
+    mu, s, cut = M.truncated_gauss_params(c, Z)
+    assert cut == Z
+    lam = np.linspace(-30, Z, 800001)
+    P = np.exp(-(lam - mu) ** 2 / (18 * c * Z))
+    P /= np.trapezoid(P, lam)
+    assert np.trapezoid(P * np.exp(lam), lam) == pytest.approx(1.0, abs=1e-8)
+    # bin masses: nothing above the cut
+    lams = np.linspace(-3, 4, 15)
+    w, cov = M.member_weights(lams, "trunc_gauss", c=c, Z=Z, renormalize=False)
+    assert np.all(w[lams - 0.25 >= Z] == 0.0)
+    assert 0.99 < cov <= 1.0 + 1e-12
+
+
+def test_inverse_laplace_reproduces_gaussian():
+    c, Z = 0.023, 2.5
+    lam = np.linspace(-12, 12, 1024, endpoint=False)
+    P = M.lambda_pdf_from_K(lambda t: 9 * c * (t * t - t) * Z / 2, lam)
+    assert np.abs(P - M.gauss_pdf(lam, c, Z)).max() < 1e-10
+
+
+def test_mixture_of_counts():
+    h = O.HistSpec(qr_bins=4, tail_bins=4, q_lim=2.0, r_lim=2.0, tail_lo=-1.0, tail_hi=1.0)
+    L = h.counts_len
+    rng = np.random.default_rng(0)
+    counts = rng.integers(0, 100, size=(3, L)).astype(np.uint64)
+    npts = counts[:, :16].sum(axis=1) + counts[:, 16 + 8]   # in range + qr_out
+    counts[:, 16 + 8 + 6] = npts
+    w = np.array([0.2, 0.5, 0.3])
+    qr, e, ww = M.mix_counts(counts, w, h)
+    # integrals of the mixed PDFs equal the mixed in-range fractions
+    frac = (w * counts[:, :16].sum(axis=1) / npts).sum()
+    assert (qr * (1.0 * 1.0)).sum() == pytest.approx(frac, rel=1e-14)
+    # a single member with weight 1 reproduces its normalised histogram
+    qr1, _, _ = M.mix_counts(counts[1:2], np.array([1.0]), h)
+    assert np.allclose(qr1.ravel(), counts[1, :16] / npts[1], rtol=1e-15)
+
+
+def test_moment_ratios_of_gaussian_components():
+    """Gaussian gradient components: S = 0, F = 3, H = 15."""
+    mixed = np.zeros(48)
+    for comp in range(9):
+        s2 = 1.0 + comp
+        mixed[4 * comp + 0] = s2
+        mixed[4 * comp + 1] = 0.0
+        mixed[4 * comp + 2] = 3 * s2 ** 2
+        mixed[4 * comp + 3] = 15 * s2 ** 3
+    r = M.gradient_moment_ratios(mixed)
+    assert r["S_long"] == 0.0
+    # per-component averages of moments of different variances: F of the average
+    assert r["F_long"] == pytest.approx(3 * np.mean([1, 25, 81]) / np.mean([1, 5, 9]) ** 2)
+
+
+def test_hellinger():
+    p = np.array([0.5, 0.5, 0.0])
+    assert M.hellinger(p, p) == 0.0
+    assert M.hellinger(p, np.array([0.0, 0.0, 1.0])) == pytest.approx(1.0)
