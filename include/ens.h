@@ -1,0 +1,244 @@
+/*
+ * libens: GB300-native ensemble DNS hot path (C ABI).
+ *
+ * Implements the data-parallel path of the ensemble method of Bentkamp &
+ * Wilczek, "Predicting any small-scale statistics of high-Reynolds-number
+ * turbulence using ensemble simulations":
+ *   - a heterogeneous ensemble of periodic-box Navier-Stokes DNS members that
+ *     differ only in their energy injection rate exp(lambda) * eps_bar, with a
+ *     forcing that amplifies the velocity Fourier coefficients of a
+ *     wavenumber band at every step so that the injection rate is fixed
+ *     (Sec. II, Eq. ensemble_hypothesis; Sec. IV);
+ *   - per-member velocity-gradient statistics: the joint PDF of
+ *     Q = -1/2 Tr A^2 and R = -1/3 Tr A^3 (Sec. V), PDFs of the dissipation
+ *     eps = 2 nu Tr S^2 and of the enstrophy omega^2 (Sec. VI), and moments
+ *     of the gradient components (Sec. VII, Eq. def_skewness_flatness);
+ *   - the mixture over lambda with the Gaussian weights of Sec. IV
+ *     (Eq. gaussian_lambda_pdf, one lambda bin per member) or the truncated
+ *     Gaussian of the Appendix (Eq. truncated_gaussian).
+ *
+ * Conventions shared by all calls:
+ *   - Box [0, 2 pi)^3, grid x_j = 2 pi j / N.  Forward transform normalised:
+ *     uh_k = N^-3 sum_x u(x) exp(-i k.x).
+ *   - Host spectral arrays ("full layout") are [3][N][N][N/2+1] complex
+ *     doubles (re, im interleaved), index [comp][kx mod N][ky mod N][kz];
+ *     modes outside the dealiased set (max_i |k_i| > ceil(N/3) - 1) are zero.
+ *   - Host physical arrays are [3][N][N][N] doubles, index [comp][x][y][z].
+ *   - The library owns its device memory: either a caller-provided workspace
+ *     (size from ens_query; device memory the caller keeps alive until
+ *     ens_destroy) or, when workspace is NULL, memory it allocates itself.
+ *   - Work is ordered on the CUDA stream given to ens_create.  Calls that
+ *     return host data synchronise that stream; the others return at once.
+ *   - No exceptions cross the ABI.  Every call returns an ens_status.  A
+ *     context remembers its first error ("sticky"); ens_last_error gives the
+ *     message.  One context must not be used from two threads at once.
+ */
+#ifndef ENS_H
+#define ENS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ENS_OK = 0,
+    ENS_EINVAL = 1,        /* invalid argument (sizes, band, viscosity, ...) */
+    ENS_ENOMEM = 2,        /* device memory or workspace too small */
+    ENS_ECUDA = 3,         /* a CUDA call failed */
+    ENS_ENONFINITE = 4,    /* a member field became non-finite */
+    ENS_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    ENS_ESTATE = 6,        /* a member's band energy vanished (forcing undefined) */
+    ENS_EUNSUPPORTED = 7   /* grid size without a compiled FFT plan */
+} ens_status;
+
+typedef struct ens_ctx ens_ctx;
+
+/* One ensemble member (Sec. IV: same viscosity and forcing band across the
+ * ensemble in the paper's setting; the library accepts any per-member
+ * values).  N must be one of 16, 32, 64, 128, 256, 384, 512. */
+typedef struct {
+    int N;               /* grid points per direction */
+    int rk_order;        /* 2 or 3: integrating-factor SSP Runge-Kutta order */
+    double nu;           /* kinematic viscosity, > 0 */
+    double lambda;       /* injection rate exp(lambda) * eps_bar */
+    double eps_bar;      /* reference injection rate, > 0 */
+    double k_lo, k_hi;   /* forcing band k_lo <= |k| <= k_hi, k_hi <= ceil(N/3)-1 */
+    double dt;           /* > 0: fixed time step; <= 0: CFL-adaptive */
+    double cfl;          /* CFL number of the adaptive step (Sec. IV: 0.2) */
+    double dt_max;       /* cap on the adaptive step, <= 0: none */
+    uint64_t seed;       /* seed of the random initial field */
+    double init_energy;  /* kinetic energy of the initial field */
+} ens_member_desc;
+
+/* Histogram specification (common physical bin edges for all members so
+ * that histograms can be mixed).  Q axis in units q0 = eps_norm/(2 nu_norm),
+ * R axis in q0^(3/2), tails in log10(eps/eps_norm) and
+ * log10(omega^2 nu_norm / eps_norm). */
+typedef struct {
+    int qr_bins;        /* bins per axis of the Q-R histogram (e.g. 64) */
+    double q_lim;       /* Q/q0 in [-q_lim, q_lim) */
+    double r_lim;       /* R/q0^1.5 in [-r_lim, r_lim) */
+    int tail_bins;      /* bins of each tail histogram (e.g. 256) */
+    double tail_lo;     /* log10 axis range [tail_lo, tail_hi) */
+    double tail_hi;
+    double eps_norm;    /* normalising injection rate */
+    double nu_norm;     /* normalising viscosity */
+} ens_hist_spec;
+
+/* Per-member counts vector layout (uint64):
+ *   [qr_bins*qr_bins | tail_bins (dissipation) | tail_bins (enstrophy) |
+ *    8 counters: qr_out, eps_under, eps_over, ens_under, ens_over,
+ *                nonfinite, npoints, 0]
+ * Moments (48 doubles per member): sums over points of A_c^p for the nine
+ * components c (row-major A_ij = d_j u_i) and p = 2, 3, 4, 6 (index 4c + k),
+ * then sums of Q, R, eps, omega^2, Q^2, R^2, eps^2, omega^4, then 4 zeros. */
+#define ENS_NMOM 48
+#define ENS_NCOUNTERS 8
+
+/* Per-member diagnostics (FP64). */
+typedef struct {
+    double t;         /* simulated time */
+    double dt;        /* last time step */
+    double E;         /* kinetic energy 1/2 sum_k |uh_k|^2 */
+    double diss;      /* dissipation rate nu sum_k k^2 |uh_k|^2 */
+    double EB;        /* energy in the forcing band */
+    double P;         /* injected power of the last stage (= exp(lambda) eps_bar) */
+    double umax;      /* max_i max_x |u_i| of the last step's first stage */
+    double Rlambda;   /* Taylor-scale Reynolds number sqrt(20 E^2 / (3 nu diss)) */
+    double kmeta;     /* k_max eta with k_max = N/3, eta = (nu^3/diss)^(1/4) */
+    int64_t steps;    /* steps taken */
+    int32_t flags;    /* bit 0: non-finite field, bit 1: band energy vanished */
+    int32_t reserved;
+} ens_diag;
+
+/* Weight specification of the lambda mixture. */
+typedef enum {
+    ENS_W_GAUSS_PAPER = 0,  /* Eq. gaussian_lambda_pdf: mean -9cZ/2, variance 9cZ */
+    ENS_W_GAUSS = 1,        /* Gaussian with given mean and standard deviation */
+    ENS_W_USER = 2,         /* caller-given weights */
+    ENS_W_TRUNC_GAUSS = 3   /* Appendix, Eq. truncated_gaussian (c, Z) */
+} ens_weight_kind;
+
+typedef struct {
+    int kind;              /* ens_weight_kind */
+    double c, Z;           /* scaling parameter c and scale gap Z */
+    double mu, sigma;      /* ENS_W_GAUSS */
+    const double *user;    /* ENS_W_USER: n host weights */
+    int renormalize;       /* 1: divide by the covered mass */
+} ens_weight_spec;
+
+/* Mixture result; all pointers are caller-owned host buffers (any may be
+ * NULL except as noted). */
+typedef struct {
+    double *weights;     /* [n] member weights (bin masses) */
+    double covered;      /* total mass of the members' lambda bins */
+    double *pdf_qr;      /* [qr_bins*qr_bins] joint PDF in units of Q/q0, R/q0^1.5 */
+    double *pdf_eps;     /* [tail_bins] PDF of log10(eps/eps_norm) */
+    double *pdf_ens;     /* [tail_bins] PDF of log10(omega^2 nu_norm/eps_norm) */
+    double *moments;     /* [ENS_NMOM] mixed per-point averages */
+    double ratios[5];    /* S_long, F_long, F_trans, H_long, H_trans */
+} ens_mixture_out;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Device workspace bytes for ens_create with the same arguments.
+ * Errors: ENS_EINVAL / ENS_EUNSUPPORTED on an invalid member. */
+ens_status ens_query(const ens_member_desc *members, int n, const ens_hist_spec *hist, size_t *workspace_bytes);
+
+/* Create an ensemble of n members and build each member's seeded random
+ * initial field on the device (white noise from splitmix64 + Box-Muller,
+ * projected, dealiased, shell spectrum E0(s) ~ s^4 exp(-s^2/2), total
+ * energy init_energy).  workspace: device pointer of at least
+ * ens_query() bytes, or NULL for library-owned memory.  stream: a
+ * cudaStream_t (NULL: legacy default stream).  On failure *out is NULL. */
+ens_status ens_create(const ens_member_desc *members, int n, const ens_hist_spec *hist, void *workspace,
+                      size_t workspace_bytes, void *stream, ens_ctx **out);
+ens_status ens_destroy(ens_ctx *ctx);
+const char *ens_last_error(const ens_ctx *ctx);
+const char *ens_status_string(ens_status s);
+
+/* ---- time stepping (Sec. IV) -------------------------------------------- */
+
+/* Advance every member by nsteps steps (asynchronous on the context stream;
+ * one CUDA-graph replay per step).  Each step: one RK stage after another,
+ * each stage = inverse transforms of u and omega = i k x u, the rotational
+ * nonlinear term u x omega with 2/3 dealiasing and max|u| for the CFL step,
+ * forward transforms, Leray projection, constant-power band forcing
+ * alpha u with alpha = exp(lambda) eps_bar / (2 E_B), and the
+ * integrating-factor SSP-RK stage update. */
+ens_status ens_step(ens_ctx *ctx, int nsteps);
+/* Same, launching the kernels directly instead of replaying a graph. */
+ens_status ens_step_nograph(ens_ctx *ctx, int nsteps);
+
+/* ---- statistics (Secs. V-VII) ---------------------------------------- */
+
+/* One snapshot of every member: gradient fields, invariants, histograms and
+ * moments.  accumulate = 0 clears the member statistics first. */
+ens_status ens_gradient_stats(ens_ctx *ctx, int accumulate);
+/* Copy statistics to the host: counts [n][counts_len] (uint64), moments
+ * [n][ENS_NMOM]; either may be NULL.  Synchronises. */
+ens_status ens_get_stats(ens_ctx *ctx, uint64_t *counts, double *moments);
+/* counts_len of a histogram specification. */
+int ens_counts_len(const ens_hist_spec *hist);
+
+/* ---- mixture (Sec. II, Eq. pdf_superposition; Sec. IV) ---------------- */
+
+/* Mix the context's current member statistics with lambda weights.
+ * Synchronises.  Errors: ENS_EINVAL on a bad weight spec. */
+ens_status ens_mixture(ens_ctx *ctx, const ens_weight_spec *w, ens_mixture_out *out);
+/* Mix statistics gathered elsewhere (e.g. from several processes): host
+ * inputs lambdas [n], counts [n][counts_len], moments [n][ENS_NMOM]; runs on
+ * the device with temporary device memory on `stream`.  n <= 1024. */
+ens_status ens_mixture_host(int n, const double *lambdas, const uint64_t *counts, const double *moments,
+                            const ens_hist_spec *hist, const ens_weight_spec *w, ens_mixture_out *out,
+                            void *stream);
+
+/* ---- state access ------------------------------------------------------ */
+
+/* Member spectral field <-> host full layout (FP64; converted from/to the
+ * library's FP32 compact layout).  Synchronises.  Uploading recomputes the
+ * member's spectral sums and forcing amplitude. */
+ens_status ens_get_field(ens_ctx *ctx, int member, double *host_spec);
+ens_status ens_set_field(ens_ctx *ctx, int member, const double *host_spec);
+/* The whole ensemble state in the library's FP32 compact layout, as raw
+ * bytes (ens_state_bytes of them), to/from host memory (pinned memory
+ * recommended).  Synchronises. */
+size_t ens_state_bytes(const ens_ctx *ctx);
+ens_status ens_get_state(ens_ctx *ctx, void *host, size_t bytes);
+ens_status ens_set_state(ens_ctx *ctx, const void *host, size_t bytes);
+/* Physical velocity of a member (inverse transforms on the device) /
+ * spectral field from a physical velocity (forward transforms on the
+ * device, dealiased; no projection).  Host physical layout.  Synchronise. */
+ens_status ens_get_velocity(ens_ctx *ctx, int member, double *host_phys);
+ens_status ens_set_velocity(ens_ctx *ctx, int member, const double *host_phys);
+/* Right-hand side F(u) = P N(u) + alpha u 1_B of every member at its
+ * current state, returned for one member in the host full layout. */
+ens_status ens_rhs(ens_ctx *ctx, int member, double *host_spec);
+
+/* Diagnostics of every member (n entries).  Synchronises.  Returns
+ * ENS_ENONFINITE or ENS_ESTATE if a member is flagged (the array is still
+ * filled). */
+ens_status ens_diagnostics(ens_ctx *ctx, ens_diag *out);
+ens_status ens_synchronize(ens_ctx *ctx);
+
+/* ---- introspection / profiling ----------------------------------------- */
+
+/* Number of members, grid size of a member. */
+int ens_members(const ens_ctx *ctx);
+int ens_member_n(const ens_ctx *ctx, int member);
+/* Launch one pass of one RK stage for every member (profiling): pass 0 IX,
+ * 1 IY, 2 ZNL, 3 FY, 4 FXU.  Asynchronous. */
+ens_status ens_run_pass(ens_ctx *ctx, int pass, int stage);
+/* Kernels one ens_step launches per step (graph nodes). */
+int ens_kernels_per_step(const ens_ctx *ctx);
+/* Algorithmic HBM bytes of one pass for all members (unique bytes read +
+ * written, valid modes only); pass as in ens_run_pass, stage 0..2. */
+double ens_pass_bytes(const ens_ctx *ctx, int pass, int stage);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

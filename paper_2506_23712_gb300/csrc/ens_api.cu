@@ -1,0 +1,837 @@
+// C-ABI layer of libens: context, device memory layout, stream/graph
+// orchestration of the hot-path kernels, host<->device marshalling.
+#include "../../include/ens.h"
+#include "ens_launch.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace ens;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Group {
+    Geo geo;
+    std::vector<int> members;   // global member indices, in order
+};
+
+struct Arena {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t count)
+    {
+        off = (off + kAlign - 1) / kAlign * kAlign;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += sizeof(T) * count;
+        return p;
+    }
+};
+
+int kc_of(int N) { return (N + 2) / 3 - 1; }
+
+}  // namespace
+
+struct ens_ctx {
+    std::vector<ens_member_desc> desc;
+    ens_hist_spec hist{};
+    std::vector<Group> groups;
+    std::vector<int> member_group, member_local;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    void *workspace = nullptr;
+    bool owns = false;
+    size_t ws_bytes = 0;
+    MemberDev *md = nullptr;
+    double *partial = nullptr;
+    int partial_blocks = 0;
+    unsigned long long *counts = nullptr;
+    double *moments = nullptr;
+    double *mom_partial = nullptr;
+    int mom_blocks = 0;
+    float *edges = nullptr;
+    HistDev hd{};
+    double *mix = nullptr;       // mixture scratch
+    cudaGraphExec_t graph = nullptr;
+    int rk = 3;
+    ens_status sticky = ENS_OK;
+    std::string err;
+};
+
+namespace {
+
+ens_status fail(ens_ctx *ctx, ens_status s, const std::string &msg)
+{
+    if (ctx && ctx->sticky == ENS_OK) {
+        ctx->sticky = s;
+        ctx->err = msg;
+    }
+    return s;
+}
+
+ens_status cuda_fail(ens_ctx *ctx, const char *what, cudaError_t e)
+{
+    return fail(ctx, ENS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define ENS_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return cuda_fail(ctx, #call, _e); \
+    } while (0)
+
+ens_status validate(const ens_member_desc *m, int n, const ens_hist_spec *h, std::string &why)
+{
+    if (!m || n <= 0) { why = "no members"; return ENS_EINVAL; }
+    if (n > 1024) { why = "at most 1024 members"; return ENS_EINVAL; }
+    if (!h) { why = "no histogram specification"; return ENS_EINVAL; }
+    for (int i = 0; i < n; ++i) {
+        const ens_member_desc &d = m[i];
+        char buf[160];
+        if (!supported_n(d.N)) {
+            snprintf(buf, sizeof buf, "member %d: N=%d has no FFT plan (16,32,64,128,256,384,512)", i, d.N);
+            why = buf;
+            return ENS_EUNSUPPORTED;
+        }
+        const int kc = kc_of(d.N);
+        if (d.rk_order != 2 && d.rk_order != 3) { snprintf(buf, sizeof buf, "member %d: rk_order must be 2 or 3", i); why = buf; return ENS_EINVAL; }
+        if (d.rk_order != m[0].rk_order) { why = "all members must share rk_order"; return ENS_EINVAL; }
+        if (!(d.nu > 0.0) || !(d.eps_bar > 0.0) || !std::isfinite(d.lambda)) { snprintf(buf, sizeof buf, "member %d: nu, eps_bar must be > 0 and lambda finite", i); why = buf; return ENS_EINVAL; }
+        if (!(d.k_lo >= 0.0) || !(d.k_hi >= d.k_lo) || d.k_hi > kc + 1e-9) {
+            snprintf(buf, sizeof buf, "member %d: band [%g, %g] must lie inside the dealiased set |k| <= %d", i, d.k_lo, d.k_hi, kc);
+            why = buf;
+            return ENS_EINVAL;
+        }
+        if (!(d.dt > 0.0) && !(d.cfl > 0.0)) { snprintf(buf, sizeof buf, "member %d: need dt > 0 or cfl > 0", i); why = buf; return ENS_EINVAL; }
+        if (!(d.init_energy > 0.0)) { snprintf(buf, sizeof buf, "member %d: init_energy must be > 0", i); why = buf; return ENS_EINVAL; }
+    }
+    if (h->qr_bins < 1 || h->qr_bins > 256 || h->tail_bins < 1 || h->tail_bins > 4096) { why = "histogram bins out of range"; return ENS_EINVAL; }
+    if (!(h->q_lim > 0) || !(h->r_lim > 0) || !(h->tail_hi > h->tail_lo) || !(h->eps_norm > 0) || !(h->nu_norm > 0)) {
+        why = "invalid histogram ranges or normalisation";
+        return ENS_EINVAL;
+    }
+    return ENS_OK;
+}
+
+// Group members by N (ascending), carve the workspace (base == nullptr: size only).
+size_t carve(const ens_member_desc *m, int n, const ens_hist_spec *h, char *base, ens_ctx *ctx)
+{
+    Arena ar{base};
+    std::vector<int> Ns;
+    for (int i = 0; i < n; ++i) Ns.push_back(m[i].N);
+    std::sort(Ns.begin(), Ns.end());
+    Ns.erase(std::unique(Ns.begin(), Ns.end()), Ns.end());
+    MemberDev *md = ar.take<MemberDev>(n);
+    std::vector<Group> groups;
+    int PB = 1, MB = 1;
+    int first = 0;
+    for (int N : Ns) {
+        Group gr;
+        for (int i = 0; i < n; ++i)
+            if (m[i].N == N) gr.members.push_back(i);
+        Geo &g = gr.geo;
+        g.N = N;
+        g.kc = kc_of(N);
+        g.NK = 2 * g.kc + 1;
+        g.NZ = g.kc + 1;
+        g.NZp = (g.NZ + kTile - 1) / kTile * kTile;
+        g.members = (int)gr.members.size();
+        g.first = first;
+        first += g.members;
+        g.sU = (long long)g.NK * g.NK * g.NZp;
+        g.sA = (long long)g.NK * N * g.NZp;
+        g.sB = (long long)N * N * g.NZp;
+        g.tw = ar.take<float2>(N);
+        g.U = ar.take<float2>(3 * g.sU * g.members);
+        g.S = ar.take<float2>(3 * g.sU * g.members);
+        g.A = ar.take<float2>((size_t)kFields * g.sA * g.members);
+        g.B = ar.take<float2>((size_t)kFields * g.sB * g.members);
+        g.shells = (int)std::ceil(std::sqrt(3.0) * g.kc) + 2;
+        g.shell = ar.take<double>((size_t)g.shells * g.members);
+        PB = std::max(PB, g.NK * g.NZp / kTile);
+        MB = std::max(MB, stats_blocks(N));
+        groups.push_back(gr);
+    }
+    const long long L = counts_len_of(h->qr_bins, h->tail_bins);
+    double *partial = ar.take<double>((size_t)n * PB * 4);
+    unsigned long long *counts = ar.take<unsigned long long>((size_t)n * L);
+    double *moments = ar.take<double>((size_t)n * kNMom);
+    double *mom_partial = ar.take<double>((size_t)n * MB * kNMom);
+    float *edges = ar.take<float>((size_t)2 * (h->qr_bins + 1) + h->tail_bins + 1);
+    // mixture scratch: lambdas, user weights, weights, covered, pdf, mixed moments, ratios
+    double *mix = ar.take<double>((size_t)3 * n + 1 + L + kNMom + 8);
+    if (ctx) {
+        ctx->md = md;
+        ctx->partial = partial;
+        ctx->partial_blocks = PB;
+        ctx->counts = counts;
+        ctx->moments = moments;
+        ctx->mom_partial = mom_partial;
+        ctx->mom_blocks = MB;
+        ctx->edges = edges;
+        ctx->mix = mix;
+        ctx->member_group.assign(n, 0);
+        ctx->member_local.assign(n, 0);
+        // renumber: members are stored group by group (global index = g.first + local)
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            Geo &g = groups[gi].geo;
+            g.partial = partial;
+            g.partial_blocks = PB;
+            g.counts = counts;
+            g.mom_partial = mom_partial;
+            g.mom_blocks = MB;
+            for (int k = 0; k < g.members; ++k) {
+                ctx->member_group[groups[gi].members[k]] = (int)gi;
+                ctx->member_local[groups[gi].members[k]] = k;
+            }
+        }
+        ctx->groups = groups;
+    }
+    return ar.off + kAlign;
+}
+
+// device slot of user member i
+int slot_of(const ens_ctx *ctx, int i) { return ctx->groups[ctx->member_group[i]].geo.first + ctx->member_local[i]; }
+
+// Geo restricted to one member of a group (pointers shifted).
+Geo single(const ens_ctx *ctx, int i)
+{
+    Geo g = ctx->groups[ctx->member_group[i]].geo;
+    const int k = ctx->member_local[i];
+    g.U += (long long)k * 3 * g.sU;
+    g.S += (long long)k * 3 * g.sU;
+    g.A += (long long)k * kFields * g.sA;
+    g.B += (long long)k * kFields * g.sB;
+    g.shell += (long long)k * g.shells;
+    g.first += k;
+    g.members = 1;
+    return g;
+}
+
+void record_step(ens_ctx *ctx, cudaStream_t s)
+{
+    const int nst = ctx->rk;
+    const int n = (int)ctx->desc.size();
+    for (int st = 0; st < nst; ++st) {
+        const int last = st == nst - 1;
+        for (auto &gr : ctx->groups) {
+            const Geo &g = gr.geo;
+            launch_pass(Pass::IX, 0, g, ctx->md, nullptr, st, last, st > 0 ? 1 : 0, s);
+            launch_pass(Pass::IY, 0, g, ctx->md, nullptr, st, last, 6, s);
+            launch_pass(Pass::Z, 0, g, ctx->md, nullptr, st, last, 0, s);
+            launch_pass(Pass::FY, 0, g, ctx->md, nullptr, st, last, 0, s);
+            launch_pass(Pass::FX, 0, g, ctx->md, nullptr, st, last, 0, s);
+        }
+        launch_finish(ctx->md, n, ctx->partial, ctx->partial_blocks, st, last, 0, s);
+    }
+}
+
+ens_status resum(ens_ctx *ctx)
+{
+    // partial slots the sums kernel does not write must read as zero
+    ENS_CUDA(ctx, cudaMemsetAsync(ctx->partial, 0, sizeof(double) * ctx->desc.size() * ctx->partial_blocks * 4,
+                                  ctx->stream));
+    for (auto &gr : ctx->groups) launch_state_sums(gr.geo, ctx->md, ctx->stream);
+    launch_finish(ctx->md, (int)ctx->desc.size(), ctx->partial, ctx->partial_blocks, 0, 0, 1, ctx->stream);
+    ENS_CUDA(ctx, cudaGetLastError());
+    return ENS_OK;
+}
+
+ens_status check(ens_ctx *ctx)
+{
+    if (!ctx) return ENS_EINVAL;
+    return ctx->sticky;
+}
+
+void to_full(const ens_ctx *ctx, int i, const float2 *compact, double *full)
+{
+    const Geo &g = ctx->groups[ctx->member_group[i]].geo;
+    const int N = g.N, H = N / 2 + 1;
+    const size_t L = (size_t)N * N * H;
+    std::memset(full, 0, sizeof(double) * 2 * 3 * L);
+    for (int q = 0; q < 3; ++q)
+        for (int ix = 0; ix < g.NK; ++ix)
+            for (int iy = 0; iy < g.NK; ++iy)
+                for (int kz = 0; kz < g.NZ; ++kz) {
+                    const int kx = ix <= g.kc ? ix : ix - g.NK, ky = iy <= g.kc ? iy : iy - g.NK;
+                    const size_t dst = q * L + ((size_t)((kx + N) % N) * N + (ky + N) % N) * H + kz;
+                    const float2 v = compact[q * g.sU + ((size_t)ix * g.NK + iy) * g.NZp + kz];
+                    full[2 * dst] = v.x;
+                    full[2 * dst + 1] = v.y;
+                }
+}
+
+void from_full(const ens_ctx *ctx, int i, const double *full, float2 *compact)
+{
+    const Geo &g = ctx->groups[ctx->member_group[i]].geo;
+    const int N = g.N, H = N / 2 + 1;
+    const size_t L = (size_t)N * N * H;
+    std::memset(compact, 0, sizeof(float2) * 3 * g.sU);
+    for (int q = 0; q < 3; ++q)
+        for (int ix = 0; ix < g.NK; ++ix)
+            for (int iy = 0; iy < g.NK; ++iy)
+                for (int kz = 0; kz < g.NZ; ++kz) {
+                    const int kx = ix <= g.kc ? ix : ix - g.NK, ky = iy <= g.kc ? iy : iy - g.NK;
+                    const size_t src = q * L + ((size_t)((kx + N) % N) * N + (ky + N) % N) * H + kz;
+                    compact[q * g.sU + ((size_t)ix * g.NK + iy) * g.NZp + kz] =
+                        make_float2((float)full[2 * src], (float)full[2 * src + 1]);
+                }
+}
+
+}  // namespace
+
+static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, const ens_hist_spec *h)
+{
+    ens_status s = ENS_OK;
+
+    // member parameters
+    std::vector<MemberDev> md(n);
+    for (int i = 0; i < n; ++i) {
+        const ens_member_desc &d = m[i];
+        MemberDev &x = md[slot_of(ctx, i)];
+        std::memset(&x, 0, sizeof x);
+        x.nu = d.nu;
+        x.eps_inj = std::exp(d.lambda) * d.eps_bar;
+        x.klo2 = d.k_lo * d.k_lo;
+        x.khi2 = d.k_hi * d.k_hi;
+        x.dt_fixed = d.dt > 0.0 ? d.dt : 0.0;
+        x.cfl = d.cfl;
+        x.dt_max = d.dt_max;
+        x.rk = d.rk_order;
+        x.N = d.N;
+        x.group = ctx->member_group[i];
+        x.index_in_group = ctx->member_local[i];
+        x.seed = d.seed;
+        x.init_energy = d.init_energy;
+        const Geo &g = ctx->groups[x.group].geo;
+        x.nblk = g.NK * g.NZp / kTile;   // update-pass CTAs (>= sums-kernel CTAs)
+        x.dt = x.dt_fixed;
+    }
+    cudaStream_t st = ctx->stream;
+    ENS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    ENS_CUDA(ctx, cudaMemcpyAsync(ctx->md, md.data(), sizeof(MemberDev) * n, cudaMemcpyHostToDevice, st));
+    ENS_CUDA(ctx, cudaMemsetAsync(ctx->partial, 0, sizeof(double) * n * ctx->partial_blocks * 4, st));
+    const long long L = counts_len_of(h->qr_bins, h->tail_bins);
+    ENS_CUDA(ctx, cudaMemsetAsync(ctx->counts, 0, sizeof(unsigned long long) * n * L, st));
+    ENS_CUDA(ctx, cudaMemsetAsync(ctx->moments, 0, sizeof(double) * n * kNMom, st));
+    // histogram edges and scalings
+    HistDev &hd = ctx->hd;
+    hd.nq = h->qr_bins;
+    hd.nt = h->tail_bins;
+    hd.counts_len = (int)L;
+    const double q0 = h->eps_norm / (2.0 * h->nu_norm);
+    hd.q_scale = (float)(1.0 / q0);
+    hd.r_scale = (float)(1.0 / std::pow(q0, 1.5));
+    hd.eps_scale = (float)(1.0 / h->eps_norm);
+    hd.ens_scale = (float)(h->nu_norm / h->eps_norm);
+    hd.q_lo = (float)(-h->q_lim);
+    hd.q_inv_w = (float)(h->qr_bins / (2.0 * h->q_lim));
+    hd.r_lo = (float)(-h->r_lim);
+    hd.r_inv_w = (float)(h->qr_bins / (2.0 * h->r_lim));
+    hd.t_lo = (float)h->tail_lo;
+    hd.t_inv_w = (float)(h->tail_bins / (h->tail_hi - h->tail_lo));
+    hd.edges_q = ctx->edges;
+    hd.edges_r = ctx->edges + (h->qr_bins + 1);
+    hd.edges_t = ctx->edges + 2 * (h->qr_bins + 1);
+    launch_edges(ctx->edges, ctx->edges + (h->qr_bins + 1), ctx->edges + 2 * (h->qr_bins + 1), h->qr_bins,
+                 h->tail_bins, h->q_lim, h->r_lim, h->tail_lo, h->tail_hi, st);
+    for (auto &gr : ctx->groups) {
+        ENS_CUDA(ctx, prepare_kernels(gr.geo.N, h->qr_bins, h->tail_bins));
+        launch_twiddles(const_cast<float2 *>(gr.geo.tw), gr.geo.N, st);
+        ENS_CUDA(ctx, cudaMemsetAsync(gr.geo.U, 0, sizeof(float2) * 3 * gr.geo.sU * gr.geo.members, st));
+        ENS_CUDA(ctx, cudaMemsetAsync(gr.geo.S, 0, sizeof(float2) * 3 * gr.geo.sU * gr.geo.members, st));
+        launch_ic(gr.geo, ctx->md, st);
+    }
+    ENS_CUDA(ctx, cudaGetLastError());
+    s = resum(ctx);
+    if (s != ENS_OK) return s;
+    ENS_CUDA(ctx, cudaStreamSynchronize(st));
+    return ENS_OK;
+}
+
+extern "C" {
+
+const char *ens_status_string(ens_status s)
+{
+    switch (s) {
+    case ENS_OK: return "ok";
+    case ENS_EINVAL: return "invalid argument";
+    case ENS_ENOMEM: return "out of device memory";
+    case ENS_ECUDA: return "CUDA error";
+    case ENS_ENONFINITE: return "non-finite field";
+    case ENS_ETIMEOUT: return "device wait timed out";
+    case ENS_ESTATE: return "band energy vanished";
+    case ENS_EUNSUPPORTED: return "unsupported grid size";
+    }
+    return "unknown status";
+}
+
+const char *ens_last_error(const ens_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.empty() ? "" : ctx->err.c_str();
+}
+
+int ens_counts_len(const ens_hist_spec *h) { return h ? (int)counts_len_of(h->qr_bins, h->tail_bins) : 0; }
+
+ens_status ens_query(const ens_member_desc *m, int n, const ens_hist_spec *h, size_t *bytes)
+{
+    std::string why;
+    const ens_status s = validate(m, n, h, why);
+    if (s != ENS_OK) return s;
+    if (!bytes) return ENS_EINVAL;
+    *bytes = carve(m, n, h, nullptr, nullptr);
+    return ENS_OK;
+}
+
+ens_status ens_create(const ens_member_desc *m, int n, const ens_hist_spec *h, void *workspace, size_t ws_bytes,
+                      void *stream, ens_ctx **out)
+{
+    if (!out) return ENS_EINVAL;
+    *out = nullptr;
+    std::string why;
+    ens_status s = validate(m, n, h, why);
+    if (s != ENS_OK) {
+        fprintf(stderr, "ens_create: %s\n", why.c_str());
+        return s;
+    }
+    ens_ctx *ctx = new ens_ctx();
+    ctx->desc.assign(m, m + n);
+    ctx->hist = *h;
+    ctx->rk = m[0].rk_order;
+    ctx->stream = (cudaStream_t)stream;
+    const size_t need = carve(m, n, h, nullptr, nullptr);
+    if (workspace) {
+        if (ws_bytes < need) {
+            delete ctx;
+            return ENS_ENOMEM;
+        }
+        ctx->workspace = workspace;
+    } else {
+        cudaError_t e = cudaMalloc(&ctx->workspace, need);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return e == cudaErrorMemoryAllocation ? ENS_ENOMEM : ENS_ECUDA;
+        }
+        ctx->owns = true;
+    }
+    ctx->ws_bytes = need;
+    char *base = reinterpret_cast<char *>(
+        (reinterpret_cast<uintptr_t>(ctx->workspace) + kAlign - 1) / kAlign * kAlign);
+    carve(m, n, h, base, ctx);
+    s = init_context(ctx, m, n, h);
+    if (s != ENS_OK) {
+        fprintf(stderr, "ens_create: %s\n", ctx->err.c_str());
+        ens_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return ENS_OK;
+}
+
+ens_status ens_destroy(ens_ctx *ctx)
+{
+    if (!ctx) return ENS_EINVAL;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->owns && ctx->workspace) cudaFree(ctx->workspace);
+    delete ctx;
+    return ENS_OK;
+}
+
+int ens_members(const ens_ctx *ctx) { return ctx ? (int)ctx->desc.size() : 0; }
+int ens_member_n(const ens_ctx *ctx, int i)
+{
+    return (ctx && i >= 0 && i < (int)ctx->desc.size()) ? ctx->desc[i].N : 0;
+}
+int ens_kernels_per_step(const ens_ctx *ctx) { return ctx ? ctx->rk * (5 * (int)ctx->groups.size() + 1) : 0; }
+
+ens_status ens_step_nograph(ens_ctx *ctx, int nsteps)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (nsteps < 0) return fail(ctx, ENS_EINVAL, "nsteps < 0");
+    for (int k = 0; k < nsteps; ++k) record_step(ctx, ctx->stream);
+    ENS_CUDA(ctx, cudaGetLastError());
+    return ENS_OK;
+}
+
+ens_status ens_step(ens_ctx *ctx, int nsteps)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (nsteps < 0) return fail(ctx, ENS_EINVAL, "nsteps < 0");
+    if (!ctx->graph) {
+        cudaGraph_t graph;
+        ENS_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        record_step(ctx, ctx->cap_stream);
+        ENS_CUDA(ctx, cudaStreamEndCapture(ctx->cap_stream, &graph));
+        cudaError_t e = cudaGraphInstantiate(&ctx->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, "cudaGraphInstantiate", e);
+    }
+    for (int k = 0; k < nsteps; ++k) ENS_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+    return ENS_OK;
+}
+
+ens_status ens_synchronize(ens_ctx *ctx)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ENS_OK;
+}
+
+ens_status ens_run_pass(ens_ctx *ctx, int pass, int stage)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (pass < 0 || pass > 4 || stage < 0 || stage >= ctx->rk) return fail(ctx, ENS_EINVAL, "bad pass/stage");
+    const Pass kind[5] = {Pass::IX, Pass::IY, Pass::Z, Pass::FY, Pass::FX};
+    for (auto &gr : ctx->groups) {
+        const int mode = 0;
+        const int arg = pass == 0 ? (stage > 0) : (pass == 1 ? 6 : 0);
+        // the update pass is timed without writing the state back over U: it
+        // targets S (not the last stage) so repeated profiling launches leave
+        // the member state unchanged
+        launch_pass(kind[pass], mode, gr.geo, ctx->md, nullptr, stage, 0, arg, ctx->stream);
+    }
+    ENS_CUDA(ctx, cudaGetLastError());
+    return ENS_OK;
+}
+
+double ens_pass_bytes(const ens_ctx *ctx, int pass, int stage)
+{
+    if (!ctx) return 0.0;
+    double total = 0.0;
+    for (auto &gr : ctx->groups) {
+        const Geo &g = gr.geo;
+        const double c = 8.0;   // bytes per complex value
+        const double st = (double)g.NK * g.NK * g.NZ * c;      // one state component
+        const double a = (double)g.NK * g.N * g.NZ * c;        // one buffer-A field
+        const double b = (double)g.N * g.N * g.NZ * c;         // one buffer-B field
+        double bytes = 0.0;
+        switch (pass) {
+        case 0: bytes = 3 * st + 6 * a; break;
+        case 1: bytes = 6 * a + 6 * b; break;
+        case 2: bytes = 6 * b + 3 * b; break;
+        case 3: bytes = 3 * b + 3 * a; break;
+        case 4: bytes = 3 * a + (stage > 0 ? 2 : 1) * 3 * st + 3 * st; break;
+        default: bytes = 0.0;
+        }
+        total += bytes * g.members;
+    }
+    return total;
+}
+
+ens_status ens_gradient_stats(ens_ctx *ctx, int accumulate)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    const int n = (int)ctx->desc.size();
+    cudaStream_t st = ctx->stream;
+    const long long L = ctx->hd.counts_len;
+    if (!accumulate) {
+        ENS_CUDA(ctx, cudaMemsetAsync(ctx->counts, 0, sizeof(unsigned long long) * n * L, st));
+    }
+    ENS_CUDA(ctx, cudaMemsetAsync(ctx->mom_partial, 0, sizeof(double) * n * ctx->mom_blocks * kNMom, st));
+    for (auto &gr : ctx->groups) {
+        const Geo &g = gr.geo;
+        launch_pass(Pass::IX, 1, g, ctx->md, nullptr, 0, 0, 0, st);
+        launch_pass(Pass::IY, 0, g, ctx->md, nullptr, 0, 0, 8, st);
+        launch_pass(Pass::ZSTAT, 0, g, ctx->md, &ctx->hd, 0, 0, 0, st);
+    }
+    launch_finish_stats(ctx->mom_partial, ctx->mom_blocks, ctx->moments, n, accumulate, st);
+    ENS_CUDA(ctx, cudaGetLastError());
+    return ENS_OK;
+}
+
+ens_status ens_get_stats(ens_ctx *ctx, uint64_t *counts, double *moments)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    const int n = (int)ctx->desc.size();
+    const long long L = ctx->hd.counts_len;
+    std::vector<unsigned long long> c((size_t)n * L);
+    std::vector<double> mo((size_t)n * kNMom);
+    ENS_CUDA(ctx, cudaMemcpyAsync(c.data(), ctx->counts, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    ENS_CUDA(ctx, cudaMemcpyAsync(mo.data(), ctx->moments, sizeof(double) * mo.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < n; ++i) {
+        const int sl = slot_of(ctx, i);
+        if (counts) std::memcpy(counts + (size_t)i * L, c.data() + (size_t)sl * L, sizeof(uint64_t) * L);
+        if (moments) std::memcpy(moments + (size_t)i * kNMom, mo.data() + (size_t)sl * kNMom, sizeof(double) * kNMom);
+    }
+    return ENS_OK;
+}
+
+static ens_status mixture_device(ens_ctx *ctx, int n, const double *d_lam, const unsigned long long *d_counts,
+                                 const double *d_mom, const ens_hist_spec *h, const ens_weight_spec *w,
+                                 const double *d_user, double *d_scratch, ens_mixture_out *out, cudaStream_t st)
+{
+    MixWeightArgs wa{};
+    wa.kind = w->kind;
+    wa.c = w->c;
+    wa.Z = w->Z;
+    wa.mu = w->mu;
+    wa.sigma = w->sigma;
+    wa.user = d_user;
+    wa.renormalize = w->renormalize;
+    MixPdfArgs pa{};
+    pa.nq = h->qr_bins;
+    pa.nt = h->tail_bins;
+    pa.counts_len = (int)counts_len_of(h->qr_bins, h->tail_bins);
+    pa.dq = 2.0 * h->q_lim / h->qr_bins;
+    pa.dr = 2.0 * h->r_lim / h->qr_bins;
+    pa.dt = (h->tail_hi - h->tail_lo) / h->tail_bins;
+    const int nb = pa.counts_len - 8;
+    double *d_w = d_scratch, *d_cov = d_w + n, *d_pdf = d_cov + 1, *d_mm = d_pdf + nb, *d_rat = d_mm + kNMom;
+    launch_mixture(d_lam, n, wa, d_counts, d_mom, pa, d_w, d_cov, d_pdf, d_mm, d_rat, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ctx ? cuda_fail(ctx, "mixture kernels", e) : ENS_ECUDA;
+    std::vector<double> host((size_t)n + 1 + nb + kNMom + 5);
+    e = cudaMemcpyAsync(host.data(), d_scratch, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ctx ? cuda_fail(ctx, "mixture copy", e) : ENS_ECUDA;
+    const double *hw = host.data(), *hc = hw + n, *hp = hc + 1, *hm = hp + nb, *hr = hm + kNMom;
+    if (out->weights) std::memcpy(out->weights, hw, sizeof(double) * n);
+    out->covered = *hc;
+    const int nq2 = h->qr_bins * h->qr_bins;
+    if (out->pdf_qr) std::memcpy(out->pdf_qr, hp, sizeof(double) * nq2);
+    if (out->pdf_eps) std::memcpy(out->pdf_eps, hp + nq2, sizeof(double) * h->tail_bins);
+    if (out->pdf_ens) std::memcpy(out->pdf_ens, hp + nq2 + h->tail_bins, sizeof(double) * h->tail_bins);
+    if (out->moments) std::memcpy(out->moments, hm, sizeof(double) * kNMom);
+    for (int k = 0; k < 5; ++k) out->ratios[k] = hr[k];
+    return ENS_OK;
+}
+
+static bool weight_spec_ok(const ens_weight_spec *w)
+{
+    if (!w) return false;
+    switch (w->kind) {
+    case ENS_W_GAUSS_PAPER: return w->c > 0.0 && w->Z >= 0.0;
+    case ENS_W_TRUNC_GAUSS: return w->c > 0.0 && w->Z > 0.0;
+    case ENS_W_GAUSS: return w->sigma > 0.0;
+    case ENS_W_USER: return w->user != nullptr;
+    }
+    return false;
+}
+
+ens_status ens_mixture(ens_ctx *ctx, const ens_weight_spec *w, ens_mixture_out *out)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (!out || !weight_spec_ok(w)) return fail(ctx, ENS_EINVAL, "invalid weight specification");
+    const int n = (int)ctx->desc.size();
+    // lambdas and user weights in device slot order
+    std::vector<double> lam(n), user(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        lam[slot_of(ctx, i)] = ctx->desc[i].lambda;
+        if (w->kind == ENS_W_USER) user[slot_of(ctx, i)] = w->user[i];
+    }
+    double *d_lam = ctx->mix, *d_user = ctx->mix + n, *d_scr = ctx->mix + 2 * n;
+    ENS_CUDA(ctx, cudaMemcpyAsync(d_lam, lam.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    ENS_CUDA(ctx, cudaMemcpyAsync(d_user, user.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<double> wslot(n);
+    ens_mixture_out tmp = *out;
+    tmp.weights = wslot.data();
+    s = mixture_device(ctx, n, d_lam, ctx->counts, ctx->moments, &ctx->hist, w, d_user, d_scr, &tmp, ctx->stream);
+    if (s != ENS_OK) return s;
+    double *keep = out->weights;
+    *out = tmp;
+    out->weights = keep;
+    if (keep)
+        for (int i = 0; i < n; ++i) keep[i] = wslot[slot_of(ctx, i)];
+    return ENS_OK;
+}
+
+ens_status ens_mixture_host(int n, const double *lambdas, const uint64_t *counts, const double *moments,
+                            const ens_hist_spec *h, const ens_weight_spec *w, ens_mixture_out *out, void *stream)
+{
+    if (n <= 0 || n > 1024 || !lambdas || !counts || !moments || !h || !out || !weight_spec_ok(w))
+        return ENS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long L = counts_len_of(h->qr_bins, h->tail_bins);
+    const size_t nd = (size_t)3 * n + 1 + L + kNMom + 8 + (size_t)n * kNMom;
+    const size_t bytes = sizeof(double) * nd + sizeof(unsigned long long) * n * L;
+    void *mem = nullptr;
+    if (cudaMallocAsync(&mem, bytes, st) != cudaSuccess) return ENS_ENOMEM;
+    double *d = (double *)mem;
+    double *d_lam = d, *d_user = d + n, *d_mom = d + 2 * n, *d_scr = d_mom + (size_t)n * kNMom;
+    unsigned long long *d_counts = reinterpret_cast<unsigned long long *>(d + nd);
+    std::vector<double> user(n, 0.0);
+    if (w->kind == ENS_W_USER) std::memcpy(user.data(), w->user, sizeof(double) * n);
+    ens_status s = ENS_OK;
+    if (cudaMemcpyAsync(d_lam, lambdas, sizeof(double) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_user, user.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_mom, moments, sizeof(double) * n * kNMom, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_counts, counts, sizeof(uint64_t) * n * L, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        s = ENS_ECUDA;
+    if (s == ENS_OK) s = mixture_device(nullptr, n, d_lam, d_counts, d_mom, h, w, d_user, d_scr, out, st);
+    cudaFreeAsync(mem, st);
+    cudaStreamSynchronize(st);
+    return s;
+}
+
+ens_status ens_get_field(ens_ctx *ctx, int i, double *host)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (i < 0 || i >= (int)ctx->desc.size() || !host) return fail(ctx, ENS_EINVAL, "bad member or buffer");
+    const Geo g = single(ctx, i);
+    std::vector<float2> c((size_t)3 * g.sU);
+    ENS_CUDA(ctx, cudaMemcpyAsync(c.data(), g.U, sizeof(float2) * c.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    to_full(ctx, i, c.data(), host);
+    return ENS_OK;
+}
+
+ens_status ens_set_field(ens_ctx *ctx, int i, const double *host)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (i < 0 || i >= (int)ctx->desc.size() || !host) return fail(ctx, ENS_EINVAL, "bad member or buffer");
+    const Geo g = single(ctx, i);
+    std::vector<float2> c((size_t)3 * g.sU);
+    from_full(ctx, i, host, c.data());
+    ENS_CUDA(ctx, cudaMemcpyAsync(g.U, c.data(), sizeof(float2) * c.size(), cudaMemcpyHostToDevice, ctx->stream));
+    s = resum(ctx);
+    if (s != ENS_OK) return s;
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ENS_OK;
+}
+
+size_t ens_state_bytes(const ens_ctx *ctx)
+{
+    if (!ctx) return 0;
+    size_t b = 0;
+    for (auto &gr : ctx->groups) b += sizeof(float2) * 3 * gr.geo.sU * gr.geo.members;
+    return b;
+}
+
+ens_status ens_get_state(ens_ctx *ctx, void *host, size_t bytes)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (!host || bytes < ens_state_bytes(ctx)) return fail(ctx, ENS_EINVAL, "state buffer too small");
+    char *p = (char *)host;
+    for (auto &gr : ctx->groups) {
+        const size_t b = sizeof(float2) * 3 * gr.geo.sU * gr.geo.members;
+        ENS_CUDA(ctx, cudaMemcpyAsync(p, gr.geo.U, b, cudaMemcpyDeviceToHost, ctx->stream));
+        p += b;
+    }
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ENS_OK;
+}
+
+ens_status ens_set_state(ens_ctx *ctx, const void *host, size_t bytes)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (!host || bytes < ens_state_bytes(ctx)) return fail(ctx, ENS_EINVAL, "state buffer too small");
+    const char *p = (const char *)host;
+    for (auto &gr : ctx->groups) {
+        const size_t b = sizeof(float2) * 3 * gr.geo.sU * gr.geo.members;
+        ENS_CUDA(ctx, cudaMemcpyAsync(gr.geo.U, p, b, cudaMemcpyHostToDevice, ctx->stream));
+        p += b;
+    }
+    return resum(ctx);
+}
+
+ens_status ens_get_velocity(ens_ctx *ctx, int i, double *host)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (i < 0 || i >= (int)ctx->desc.size() || !host) return fail(ctx, ENS_EINVAL, "bad member or buffer");
+    const Geo g = single(ctx, i);
+    launch_pass(Pass::IX, 0, g, ctx->md, nullptr, 0, 0, 0, ctx->stream);
+    launch_pass(Pass::IY, 0, g, ctx->md, nullptr, 0, 0, 3, ctx->stream);
+    launch_pass(Pass::Z, 3, g, ctx->md, nullptr, 0, 0, 0, ctx->stream);
+    ENS_CUDA(ctx, cudaGetLastError());
+    const size_t n3 = (size_t)g.N * g.N * g.N;
+    std::vector<float> f(3 * n3);
+    ENS_CUDA(ctx, cudaMemcpyAsync(f.data(), g.A, sizeof(float) * f.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t k = 0; k < f.size(); ++k) host[k] = f[k];
+    return ENS_OK;
+}
+
+ens_status ens_set_velocity(ens_ctx *ctx, int i, const double *host)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (i < 0 || i >= (int)ctx->desc.size() || !host) return fail(ctx, ENS_EINVAL, "bad member or buffer");
+    const Geo g = single(ctx, i);
+    const size_t n3 = (size_t)g.N * g.N * g.N;
+    std::vector<float> f(3 * n3);
+    for (size_t k = 0; k < f.size(); ++k) f[k] = (float)host[k];
+    ENS_CUDA(ctx, cudaMemcpyAsync(g.A, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, ctx->stream));
+    launch_pass(Pass::Z, 4, g, ctx->md, nullptr, 0, 0, 0, ctx->stream);
+    launch_pass(Pass::FY, 0, g, ctx->md, nullptr, 0, 0, 0, ctx->stream);
+    launch_pass(Pass::FX, 3, g, ctx->md, nullptr, 0, 0, 0, ctx->stream);
+    ENS_CUDA(ctx, cudaGetLastError());
+    s = resum(ctx);
+    if (s != ENS_OK) return s;
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ENS_OK;
+}
+
+ens_status ens_rhs(ens_ctx *ctx, int i, double *host)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (i < 0 || i >= (int)ctx->desc.size() || !host) return fail(ctx, ENS_EINVAL, "bad member or buffer");
+    const Geo g = single(ctx, i);
+    launch_pass(Pass::IX, 0, g, ctx->md, nullptr, 0, 0, 0, ctx->stream);
+    launch_pass(Pass::IY, 0, g, ctx->md, nullptr, 0, 0, 6, ctx->stream);
+    launch_pass(Pass::Z, 0, g, ctx->md, nullptr, 3, 0, 0, ctx->stream);   // max|u| into the spare slot 3
+    launch_pass(Pass::FY, 0, g, ctx->md, nullptr, 0, 0, 0, ctx->stream);
+    launch_pass(Pass::FX, 1, g, ctx->md, nullptr, 0, 0, 0, ctx->stream);
+    ENS_CUDA(ctx, cudaGetLastError());
+    std::vector<float2> c((size_t)3 * g.sU);
+    ENS_CUDA(ctx, cudaMemcpyAsync(c.data(), g.S, sizeof(float2) * c.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    to_full(ctx, i, c.data(), host);
+    return ENS_OK;
+}
+
+ens_status ens_diagnostics(ens_ctx *ctx, ens_diag *out)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (!out) return fail(ctx, ENS_EINVAL, "null output");
+    const int n = (int)ctx->desc.size();
+    std::vector<MemberDev> md(n);
+    ENS_CUDA(ctx, cudaMemcpyAsync(md.data(), ctx->md, sizeof(MemberDev) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ens_status flag = ENS_OK;
+    for (int i = 0; i < n; ++i) {
+        const MemberDev &d = md[slot_of(ctx, i)];
+        ens_diag &o = out[i];
+        o.t = d.t;
+        o.dt = d.dt;
+        o.E = d.E;
+        o.diss = d.diss;
+        o.EB = d.EB;
+        o.P = d.P;
+        o.umax = d.umax;
+        o.Rlambda = d.diss > 0 ? std::sqrt(20.0 * d.E * d.E / (3.0 * d.nu * d.diss)) : 0.0;
+        o.kmeta = d.diss > 0 ? (d.N / 3.0) * std::pow(d.nu * d.nu * d.nu / d.diss, 0.25) : 0.0;
+        o.steps = d.steps;
+        o.flags = d.flags;
+        o.reserved = 0;
+        if ((d.flags & kFlagNonFinite) && flag == ENS_OK) flag = ENS_ENONFINITE;
+        if ((d.flags & kFlagNoBandEnergy) && flag == ENS_OK) flag = ENS_ESTATE;
+    }
+    return flag;
+}
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+// Register/shared-memory Stockham FFT engine for sm_103a.
+//
+// A length-N complex line is held by P threads, V = N/P values each.  A plan
+// N = R0 * R1 (* R2) runs one radix-R pass per factor: every thread applies
+// the inter-pass twiddles to its butterflies, computes R-point DFTs in
+// registers, and hands the results to the next pass through shared memory
+// (one exchange per pass boundary).  Pass s with radix R after Ns points of
+// previous radices reads positions j + t N/R and writes position
+// (j / Ns) Ns R + (j mod Ns) + t Ns (Stockham autosort: natural order out).
+// The first pass's inputs come straight from global memory and the last
+// pass's outputs go straight back, so a plan with two factors touches shared
+// memory once.
+//
+// The transforms are the discrete Fourier series of the member fields
+// (Sec. IV: the forcing acts on "velocity Fourier coefficients"); sign -1 is
+// the analysis (forward) direction, +1 synthesis.  All arithmetic is FP32;
+// twiddles come from an FP64-generated table rounded to FP32.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ens {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+// cos(2 pi j / 48), j = 0..48: every radix used here divides 48.
+__host__ __device__ constexpr double cos48(int j)
+{
+    constexpr double t[49] = {
+        1,
+        0.99144486137381038,
+        0.96592582628906831,
+        0.92387953251128674,
+        0.86602540378443871,
+        0.79335334029123517,
+        0.70710678118654757,
+        0.60876142900872066,
+        0.50000000000000011,
+        0.38268343236508984,
+        0.25881904510252074,
+        0.13052619222005171,
+        6.123233995736766e-17,
+        -0.1305261922200516,
+        -0.25881904510252063,
+        -0.3826834323650895,
+        -0.49999999999999978,
+        -0.60876142900872066,
+        -0.70710678118654746,
+        -0.79335334029123505,
+        -0.86602540378443871,
+        -0.92387953251128674,
+        -0.9659258262890682,
+        -0.99144486137381038,
+        -1,
+        -0.99144486137381038,
+        -0.96592582628906831,
+        -0.92387953251128685,
+        -0.86602540378443882,
+        -0.79335334029123517,
+        -0.70710678118654791,
+        -0.60876142900872088,
+        -0.50000000000000044,
+        -0.3826834323650895,
+        -0.25881904510252063,
+        -0.13052619222005163,
+        -1.8369701987210297e-16,
+        0.13052619222005127,
+        0.2588190451025203,
+        0.38268343236508917,
+        0.50000000000000011,
+        0.60876142900871988,
+        0.70710678118654735,
+        0.79335334029123494,
+        0.86602540378443837,
+        0.92387953251128685,
+        0.96592582628906809,
+        0.99144486137381038,
+        1};
+    return t[j];
+}
+
+// Multiply by W_R^K = exp(s 2 pi i K / R), s = -1 forward, +1 inverse.
+template <int R, int K, bool FWD>
+__device__ __forceinline__ float2 twmul(float2 a)
+{
+    static_assert(48 % R == 0, "radix must divide 48");
+    constexpr int j = (K * (48 / R)) % 48;
+    if constexpr (j == 0) {
+        return a;
+    } else if constexpr (j == 12) {   // W = -i (fwd) / +i (inv)
+        return FWD ? mul_mi(a) : mul_i(a);
+    } else if constexpr (j == 24) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (j == 36) {
+        return FWD ? mul_i(a) : mul_mi(a);
+    } else {
+        constexpr float c = (float)cos48(j);
+        constexpr float s = (float)cos48((j + 36) % 48) * (FWD ? -1.0f : 1.0f);
+        return cmul(a, make_float2(c, s));
+    }
+}
+
+// In-register R-point DFT, natural order in and out.
+template <int R, bool FWD>
+struct Dft {
+    template <int K>
+    static __device__ __forceinline__ void combine(float2 *v, const float2 *e, const float2 *o)
+    {
+        if constexpr (K < R / 2) {
+            const float2 t = twmul<R, K, FWD>(o[K]);
+            v[K] = cadd(e[K], t);
+            v[K + R / 2] = csub(e[K], t);
+            combine<K + 1>(v, e, o);
+        }
+    }
+    static __device__ __forceinline__ void run(float2 *v)
+    {
+        static_assert(R % 2 == 0, "odd radix needs its own base case");
+        constexpr int H = R / 2;
+        float2 e[H], o[H];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        Dft<H, FWD>::run(e);
+        Dft<H, FWD>::run(o);
+        combine<0>(v, e, o);
+    }
+};
+
+template <bool FWD>
+struct Dft<1, FWD> {
+    static __device__ __forceinline__ void run(float2 *) {}
+};
+
+template <bool FWD>
+struct Dft<2, FWD> {
+    static __device__ __forceinline__ void run(float2 *v)
+    {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <bool FWD>
+struct Dft<3, FWD> {
+    static __device__ __forceinline__ void run(float2 *v)
+    {
+        // X1,2 = v0 - (v1+v2)/2 -/+ s i (sqrt3/2)(v1 - v2), s = +1 fwd
+        constexpr float h = 0.86602540378443865f;
+        const float2 s = cadd(v[1], v[2]);
+        const float2 d = cscale(csub(v[1], v[2]), FWD ? -h : h);
+        const float2 m = make_float2(v[0].x - 0.5f * s.x, v[0].y - 0.5f * s.y);
+        v[0] = cadd(v[0], s);
+        v[1] = cadd(m, mul_i(d));
+        v[2] = csub(m, mul_i(d));
+    }
+};
+
+// Plans: N = R0 * R1 (* R2), P threads per line, V = N / P values per thread.
+template <int N>
+struct Plan;
+template <> struct Plan<16>  { static constexpr int P = 4,  NP = 2, R0 = 4,  R1 = 4,  R2 = 1; };
+template <> struct Plan<32>  { static constexpr int P = 4,  NP = 2, R0 = 8,  R1 = 4,  R2 = 1; };
+template <> struct Plan<64>  { static constexpr int P = 8,  NP = 2, R0 = 8,  R1 = 8,  R2 = 1; };
+template <> struct Plan<128> { static constexpr int P = 8,  NP = 2, R0 = 16, R1 = 8,  R2 = 1; };
+template <> struct Plan<256> { static constexpr int P = 16, NP = 2, R0 = 16, R1 = 16, R2 = 1; };
+template <> struct Plan<384> { static constexpr int P = 16, NP = 3, R0 = 8,  R1 = 6,  R2 = 8; };
+template <> struct Plan<512> { static constexpr int P = 32, NP = 3, R0 = 8,  R1 = 8,  R2 = 8; };
+
+template <int N>
+struct PlanInfo {
+    using PL = Plan<N>;
+    static constexpr int P = PL::P;
+    static constexpr int V = N / P;
+    static constexpr int NP = PL::NP;
+    static constexpr int R0 = PL::R0, R1 = PL::R1, R2 = PL::R2;
+    static constexpr int RL = NP == 2 ? R1 : R2;        // radix of the last pass
+    static constexpr bool matched = (R0 == RL);        // last-pass positions == first-pass positions
+    static_assert(R0 * R1 * R2 == N, "plan must factor N");
+    static_assert(N % (R0 * P) == 0 && N % (R1 * P) == 0 && (R2 == 1 || N % (R2 * P) == 0), "plan/P mismatch");
+    // position of register slot i in the first pass' input order
+    static __device__ __forceinline__ int in_pos(int p, int i)
+    {
+        return p + (i / R0) * P + (i % R0) * (N / R0);
+    }
+    // position of register slot i in the last pass' output order
+    static __device__ __forceinline__ int out_pos(int p, int i)
+    {
+        return p + (i / RL) * P + (i % RL) * (N / RL);
+    }
+};
+
+// One radix-R pass on the registers: twiddles then R-point DFTs.
+template <int N, int R, int Ns, int P, bool FWD>
+__device__ __forceinline__ void pass_regs(float2 *v, int p, const float2 *__restrict__ tw)
+{
+    constexpr int B = N / (R * P);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if constexpr (Ns > 1) {
+            const int j = p + b * P;
+            const int k = j % Ns;
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                float2 w = tw[t * k * (N / (Ns * R))];
+                if (!FWD) w.y = -w.y;
+                v[b * R + t] = cmul(v[b * R + t], w);
+            }
+        }
+        Dft<R, FWD>::run(&v[b * R]);
+    }
+}
+
+// Hand the outputs of a pass (radix R, Ns) to the next pass (radix R2n).
+// `at(pos)` returns the shared-memory slot of line position pos for this
+// thread's line.  Brackets the exchange with block barriers.
+template <int N, int R, int Ns, int Rn, int P, class At>
+__device__ __forceinline__ void exchange(float2 *v, int p, At at)
+{
+    constexpr int B = N / (R * P);
+    constexpr int Bn = N / (Rn * P);
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = p + b * P;
+        const int base = (j / Ns) * Ns * R + (j % Ns);
+#pragma unroll
+        for (int t = 0; t < R; ++t) *at(base + t * Ns) = v[b * R + t];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < Bn; ++b) {
+        const int j = p + b * P;
+#pragma unroll
+        for (int t = 0; t < Rn; ++t) v[b * Rn + t] = *at(j + t * (N / Rn));
+    }
+}
+
+// Full line transform.  In: v in first-pass input order.  Out: v in
+// last-pass output order (PlanInfo::out_pos).  Every thread of the block
+// must call it (it contains block barriers).
+template <int N, bool FWD, class At>
+__device__ __forceinline__ void fft_line(float2 *v, int p, const float2 *__restrict__ tw, At at)
+{
+    using PI = PlanInfo<N>;
+    constexpr int P = PI::P;
+    pass_regs<N, PI::R0, 1, P, FWD>(v, p, tw);
+    exchange<N, PI::R0, 1, PI::R1, P>(v, p, at);
+    pass_regs<N, PI::R1, PI::R0, P, FWD>(v, p, tw);
+    if constexpr (PI::NP == 3) {
+        exchange<N, PI::R1, PI::R0, PI::R2, P>(v, p, at);
+        pass_regs<N, PI::R2, PI::R0 * PI::R1, P, FWD>(v, p, tw);
+    }
+}
+
+}  // namespace ens

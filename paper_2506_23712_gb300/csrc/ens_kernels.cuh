@@ -1,0 +1,567 @@
+// Hot-path kernels of the ensemble DNS (sm_103a).
+//
+// One member is a forced periodic-box Navier-Stokes DNS whose injection
+// rate is exp(lambda) eps_bar (Sec. II, Eq. ensemble_hypothesis; Sec. IV).
+// Its state is the dealiased half spectrum in a compact layout that stores
+// only the modes the cubic 2/3 rule keeps (|k_i| <= kc = ceil(N/3) - 1), so
+// every transform is pruned: the inverse passes skip the zero band and the
+// forward passes drop it on output.  One RK stage is five passes:
+//
+//   IX  : state (3 comps) -> u, omega = i k x u, transformed along x   [A]
+//   IY  : A -> transformed along y                                      [B]
+//   ZNL : B -> along z to physical space, n = u x omega, max|u|, and
+//         straight back along z (two real rows per complex line)        [B]
+//   FY  : B -> forward along y, dealiased rows dropped                  [A]
+//   FXU : A -> forward along x, 1/N^3, Leray projection, constant-power
+//         band forcing, integrating-factor RK stage, FP64 partial sums  [U/S]
+//
+// The statistics snapshot reuses IX/IY with the eight independent gradient
+// components and ends in ZSTAT: Q, R, dissipation and enstrophy per point,
+// shared-memory histograms and moment sums (Secs. V-VII).
+#pragma once
+
+#include "ens_fft.cuh"
+#include "ens_internal.h"
+
+namespace ens {
+
+// rows handled per CTA by the z-direction passes
+template <int N>
+struct RowCfg {
+    static constexpr int P = PlanInfo<N>::P;
+    static constexpr int RZ = 256 / P;
+    static constexpr int SROW = N + N / 16 + 1;   // padded shared row stride (float2)
+};
+
+__host__ __device__ constexpr int threads_cols(int P) { return kTile * P; }
+
+// Launch helpers (host): shared memory bytes per pass.
+template <int N>
+constexpr size_t smem_cols() { return sizeof(float2) * (size_t)(N + N * kTile); }
+template <int N>
+constexpr size_t smem_rows() { return sizeof(float2) * (size_t)(N + RowCfg<N>::RZ * RowCfg<N>::SROW); }
+
+__device__ __forceinline__ int wnum(int pos, int N) { return pos <= N / 2 ? pos : pos - N; }
+
+__device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restrict__ g, int N)
+{
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g[i];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// IX: inverse transform along x of fields built from the state.
+//   MODE 0: u_x, u_y, u_z, omega_x, omega_y, omega_z   (omega = i k x u)
+//   MODE 1: A_ij = i k_j u_i for ij = 11,12,13,21,22,23,31,32
+// grid (NK*NZp/kTile, members), block kTile*P.
+// ---------------------------------------------------------------------------
+template <int N, int MODE>
+__global__ void __launch_bounds__(kTile * PlanInfo<N>::P)
+k_inv_x(Geo g, int use_S)
+{
+    using PI = PlanInfo<N>;
+    constexpr int P = PI::P, V = PI::V;
+    constexpr int NF = MODE == 0 ? 6 : 8;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm, *buf = sm + N;
+    load_twiddles(tw, g.tw, N);
+
+    const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
+    const int m = blockIdx.y;
+    const int col = blockIdx.x * kTile + c;
+    const int iy = col / g.NZp, kz = col % g.NZp;
+    const bool valid = kz < g.NZ;
+    const float ky = (float)(iy <= g.kc ? iy : iy - g.NK);
+    const float kzf = (float)kz;
+    const long long rowU = (long long)g.NK * g.NZp;
+    const float2 *X = (use_S ? g.S : g.U) + (long long)m * 3 * g.sU + col;
+
+    float2 u0[V], u1[V], u2[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int kx = wnum(PI::in_pos(p, i), N);
+        const bool keep = valid && kx >= -g.kc && kx <= g.kc;
+        const long long ix = kx >= 0 ? kx : kx + g.NK;
+        u0[i] = keep ? X[ix * rowU] : make_float2(0.f, 0.f);
+        u1[i] = keep ? X[g.sU + ix * rowU] : make_float2(0.f, 0.f);
+        u2[i] = keep ? X[2 * g.sU + ix * rowU] : make_float2(0.f, 0.f);
+    }
+    float2 *dst0 = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
+    auto at = [&](int pos) { return &buf[pos * kTile + c]; };
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) {
+        float2 v[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const float kx = (float)wnum(PI::in_pos(p, i), N);
+            const float2 a = u0[i], b = u1[i], d = u2[i];
+            // component selection without dynamic register indexing
+            const float2 ui = f % 3 == 0 ? a : (f % 3 == 1 ? b : d);
+            if (MODE == 0) {
+                if (f < 3) {
+                    v[i] = ui;
+                } else {
+                    // omega = i k x u: (k x u)_x = ky uz - kz uy, _y = kz ux - kx uz, _z = kx uy - ky ux
+                    float2 cr;
+                    if (f == 3) cr = make_float2(ky * d.x - kzf * b.x, ky * d.y - kzf * b.y);
+                    else if (f == 4) cr = make_float2(kzf * a.x - kx * d.x, kzf * a.y - kx * d.y);
+                    else cr = make_float2(kx * b.x - ky * a.x, kx * b.y - ky * a.y);
+                    v[i] = mul_i(cr);
+                }
+            } else {
+                // A_ij = i k_j u_i, f = 3 i + j
+                const float2 uc = f < 3 ? a : (f < 6 ? b : d);
+                const int cj = f % 3;
+                const float kj = cj == 0 ? kx : (cj == 1 ? ky : kzf);
+                v[i] = mul_i(cscale(uc, kj));
+            }
+        }
+        fft_line<N, false>(v, p, tw, at);
+        if (valid) {
+            float2 *dst = dst0 + (long long)f * g.sA;
+#pragma unroll
+            for (int i = 0; i < V; ++i) dst[(long long)PI::out_pos(p, i) * g.NZp] = v[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// IY: inverse transform along y of buffer-A fields [f0, f0+nf) into B.
+// grid (N*NZp/kTile, nf, members).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kTile * PlanInfo<N>::P)
+k_inv_y(Geo g, int f0)
+{
+    using PI = PlanInfo<N>;
+    constexpr int P = PI::P, V = PI::V;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm, *buf = sm + N;
+    load_twiddles(tw, g.tw, N);
+    const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
+    const int f = f0 + blockIdx.y, m = blockIdx.z;
+    const int col = blockIdx.x * kTile + c;       // (x, kz) flat
+    const bool valid = (col % g.NZp) < g.NZ;
+    const long long row = (long long)N * g.NZp;
+    const float2 *src = g.A + ((long long)m * kFields + f) * g.sA + col;
+    float2 *dst = g.B + ((long long)m * kFields + f) * g.sB + col;
+    float2 v[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int ky = wnum(PI::in_pos(p, i), N);
+        const bool keep = valid && ky >= -g.kc && ky <= g.kc;
+        const int iy = ky >= 0 ? ky : ky + g.NK;
+        v[i] = keep ? src[iy * row] : make_float2(0.f, 0.f);
+    }
+    fft_line<N, false>(v, p, tw, [&](int pos) { return &buf[pos * kTile + c]; });
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) dst[PI::out_pos(p, i) * row] = v[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FY: forward transform along y of B fields [0, nf) into A (kept ky only).
+// grid (N*NZp/kTile, nf, members).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kTile * PlanInfo<N>::P)
+k_fwd_y(Geo g)
+{
+    using PI = PlanInfo<N>;
+    constexpr int P = PI::P, V = PI::V;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm, *buf = sm + N;
+    load_twiddles(tw, g.tw, N);
+    const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
+    const int f = blockIdx.y, m = blockIdx.z;
+    const int col = blockIdx.x * kTile + c;
+    const bool valid = (col % g.NZp) < g.NZ;
+    const long long row = (long long)N * g.NZp;
+    const float2 *src = g.B + ((long long)m * kFields + f) * g.sB + col;
+    float2 *dst = g.A + ((long long)m * kFields + f) * g.sA + col;
+    float2 v[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) v[i] = valid ? src[PI::in_pos(p, i) * row] : make_float2(0.f, 0.f);
+    fft_line<N, true>(v, p, tw, [&](int pos) { return &buf[pos * kTile + c]; });
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const int ky = wnum(PI::out_pos(p, i), N);
+            if (ky >= -g.kc && ky <= g.kc) dst[(ky >= 0 ? ky : ky + g.NK) * row] = v[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z-direction passes.  Each line is one (y, x) row of NZ complex values; two
+// real rows travel as the real and imaginary parts of one complex line.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ float2 *row_slot(float2 *buf, int r, int pos)
+{
+    return &buf[r * RowCfg<N>::SROW + pos + (pos >> 4)];
+}
+
+// Hermitian-extended pair line a + i b at position pos from half spectra.
+__device__ __forceinline__ float2 pair_at(const float2 *__restrict__ Xa, const float2 *__restrict__ Xb,
+                                          int pos, int N, int kc)
+{
+    if (pos == 0) {
+        const float2 a = Xa[0], b = Xb[0];
+        return make_float2(a.x, b.x);   // real parts only (C2R convention)
+    }
+    if (pos <= kc) {
+        const float2 a = Xa[pos], b = Xb[pos];
+        return make_float2(a.x - b.y, a.y + b.x);
+    }
+    if (pos >= N - kc) {
+        const float2 a = Xa[N - pos], b = Xb[N - pos];   // conj(a) + i conj(b)
+        return make_float2(a.x + b.y, b.x - a.y);
+    }
+    return make_float2(0.f, 0.f);
+}
+
+// Forward transform of two real rows held as v (first-pass order), then the
+// half spectra of both rows for kz < NZ written to dstA, dstB (dstB may be
+// null: single real row in v.x).
+template <int N>
+__device__ __forceinline__ void forward_pair_store(float2 *v, int p, int r, const float2 *tw, float2 *buf,
+                                                   float2 *dstA, float2 *dstB, int NZ, bool row_ok)
+{
+    using PI = PlanInfo<N>;
+    constexpr int V = PI::V, P = PI::P;
+    auto at = [&](int pos) { return row_slot<N>(buf, r, pos); };
+    fft_line<N, true>(v, p, tw, at);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < V; ++i) *at(PI::out_pos(p, i)) = v[i];
+    __syncthreads();
+    if (row_ok) {
+        for (int k = p; k < NZ; k += P) {
+            const float2 z = *at(k);
+            const float2 w = cconj(*at(k == 0 ? 0 : N - k));
+            // Xa = (Z_k + conj Z_{N-k}) / 2 ; Xb = (Z_k - conj Z_{N-k}) / (2i)
+            dstA[k] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y + w.y));
+            if (dstB) dstB[k] = make_float2(0.5f * (z.y - w.y), -0.5f * (z.x - w.x));
+        }
+    }
+}
+
+// MODE 0: nonlinear term (fields 0..5 of B -> fields 0..2 of B, in place)
+// MODE 1: initial white noise (seeded, no input) -> fields 0..2 of B
+// MODE 3: velocity to physical space: fields 0..2 of B -> A as reals [3][x][y][z]
+// MODE 4: physical reals in A [3][x][y][z] -> forward along z into B fields 0..2
+// grid (N*N/RZ, members), block RZ*P.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float white_noise(uint64_t seed, uint64_t counter)
+{
+    const double u1 = ((double)(splitmix64_at(seed, 2 * counter) >> 11) + 1.0) * 0x1.0p-53;
+    const double u2 = ((double)(splitmix64_at(seed, 2 * counter + 1) >> 11) + 1.0) * 0x1.0p-53;
+    return (float)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(256)
+k_z(Geo g, MemberDev *md, int stage)
+{
+    using PI = PlanInfo<N>;
+    using RC = RowCfg<N>;
+    constexpr int P = PI::P, V = PI::V, RZ = RC::RZ;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm, *buf = sm + N;
+    load_twiddles(tw, g.tw, N);
+    const int p = threadIdx.x % P, r = threadIdx.x / P;
+    const int m = blockIdx.y;
+    const long long rho = (long long)blockIdx.x * RZ + r;   // row = y*N + x
+    const int yy = (int)(rho / N), xx = (int)(rho % N);
+    float2 *B = g.B + (long long)m * kFields * g.sB + rho * g.NZp;
+    auto at = [&](int pos) { return row_slot<N>(buf, r, pos); };
+
+    float2 w0[V], w1[V];   // forward inputs in first-pass order
+    if constexpr (MODE == 0 || MODE == 3) {
+        float2 a[V], b[V], cc[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) a[i] = pair_at(B, B + g.sB, PI::in_pos(p, i), N, g.kc);
+        fft_line<N, false>(a, p, tw, at);
+        if constexpr (MODE == 3) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) b[i] = pair_at(B + 2 * g.sB, B + 2 * g.sB, PI::in_pos(p, i), N, g.kc);
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) b[i] = pair_at(B + 2 * g.sB, B + 3 * g.sB, PI::in_pos(p, i), N, g.kc);
+        }
+        fft_line<N, false>(b, p, tw, at);
+        if constexpr (MODE == 3) {
+            // physical u_c(x, y, z) into A viewed as floats [member][3][x][y][z]
+            float *out = reinterpret_cast<float *>(g.A + (long long)m * kFields * g.sA);
+            const long long n3 = (long long)N * N * N;
+            const long long base = ((long long)xx * N + yy) * N;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const int q = PI::out_pos(p, i);
+                out[base + q] = a[i].x;
+                out[n3 + base + q] = a[i].y;
+                out[2 * n3 + base + q] = b[i].x;
+            }
+            return;
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) cc[i] = pair_at(B + 4 * g.sB, B + 5 * g.sB, PI::in_pos(p, i), N, g.kc);
+            fft_line<N, false>(cc, p, tw, at);
+            // a = ux + i uy, b = uz + i wx, cc = wy + i wz at positions out_pos
+            float umax = 0.f;
+            bool finite = true;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const float ux = a[i].x, uy = a[i].y, uz = b[i].x;
+                const float wx = b[i].y, wy = cc[i].x, wz = cc[i].y;
+                umax = fmaxf(umax, fmaxf(fabsf(ux), fmaxf(fabsf(uy), fabsf(uz))));
+                finite = finite && isfinite(ux + uy + uz + wx + wy + wz);
+                w0[i] = make_float2(uy * wz - uz * wy, uz * wx - ux * wz);
+                w1[i] = make_float2(ux * wy - uy * wx, 0.f);
+            }
+            // block max of |u| -> member slot of this stage
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+            const unsigned ballot = __ballot_sync(0xffffffffu, !finite);
+            if ((threadIdx.x & 31) == 0) {
+                atomicMax(&md[g.first + m].umax_bits[stage], __float_as_uint(umax));
+                if (ballot) atomicOr(&md[g.first + m].flags, kFlagNonFinite);
+            }
+            if constexpr (!PI::matched) {
+                // reorder from last-pass positions to first-pass positions
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < V; ++i) *at(PI::out_pos(p, i)) = w0[i];
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < V; ++i) w0[i] = *at(PI::in_pos(p, i));
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < V; ++i) *at(PI::out_pos(p, i)) = w1[i];
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < V; ++i) w1[i] = *at(PI::in_pos(p, i));
+            }
+        }
+    } else if constexpr (MODE == 1) {
+        const uint64_t seed = (uint64_t)md[g.first + m].seed;
+        const uint64_t n3 = (uint64_t)N * N * N;
+        const uint64_t base = ((uint64_t)xx * N + yy) * N;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const uint64_t idx = base + PI::in_pos(p, i);
+            w0[i] = make_float2(white_noise(seed, idx), white_noise(seed, n3 + idx));
+            w1[i] = make_float2(white_noise(seed, 2 * n3 + idx), 0.f);
+        }
+    } else if constexpr (MODE == 4) {
+        const float *in = reinterpret_cast<const float *>(g.A + (long long)m * kFields * g.sA);
+        const long long n3 = (long long)N * N * N;
+        const long long base = ((long long)xx * N + yy) * N;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const int q = PI::in_pos(p, i);
+            w0[i] = make_float2(in[base + q], in[n3 + base + q]);
+            w1[i] = make_float2(in[2 * n3 + base + q], 0.f);
+        }
+    }
+    if constexpr (MODE == 1 || MODE == 4) {
+        __syncthreads();   // all threads reach the stores below after their loads
+    }
+    forward_pair_store<N>(w0, p, r, tw, buf, B, B + g.sB, g.NZ, true);
+    forward_pair_store<N>(w1, p, r, tw, buf, B + 2 * g.sB, nullptr, g.NZ, true);
+}
+
+// ---------------------------------------------------------------------------
+// FXU: forward along x of B-derived A fields 0..2, then per kept mode:
+//   MODE 0: RK stage update (IF-SSP-RK2/3) of the state, FP64 partial sums
+//   MODE 1: write F = P N + f into S (right-hand side, for checks)
+//   MODE 2: initial field: write the projected noise spectrum to U and
+//           accumulate shell energies
+//   MODE 3: write the normalised forward transform (no projection) to U
+// grid (NK*NZp/kTile, members), block kTile*P.
+// ---------------------------------------------------------------------------
+struct StageCoef {
+    float a, ha, b, hb;   // out = a E(ha dt) u^n + b E(hb dt) (u^s + dt F)
+};
+
+__device__ __forceinline__ StageCoef stage_coef(int rk, int stage)
+{
+    if (rk == 2) {
+        if (stage == 0) return {0.f, 0.f, 1.f, 1.f};
+        return {0.5f, 1.f, 0.5f, 0.f};
+    }
+    if (stage == 0) return {0.f, 0.f, 1.f, 1.f};
+    if (stage == 1) return {0.75f, 0.5f, 0.25f, -0.5f};
+    return {1.f / 3.f, 1.f, 2.f / 3.f, 0.5f};
+}
+
+__device__ __forceinline__ double member_dt(const MemberDev &d, int N)
+{
+    if (d.dt_fixed > 0.0) return d.dt_fixed;
+    const double umax = (double)__uint_as_float(d.umax_bits[0]);
+    double dt = d.cfl * (2.0 * 3.14159265358979323846 / N) / umax;
+    if (d.dt_max > 0.0 && dt > d.dt_max) dt = d.dt_max;
+    return dt;
+}
+
+template <int NW>
+__device__ __forceinline__ void block_sum_to(double *out, double (&vals)[NW], double *scratch)
+{
+    // scratch: (blockDim/32) * NW doubles
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        double v = vals[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        vals[q] = v;
+    }
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) scratch[warp * NW + q] = vals[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < NW) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += scratch[w * NW + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(kTile * PlanInfo<N>::P)
+k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
+{
+    using PI = PlanInfo<N>;
+    constexpr int P = PI::P, V = PI::V;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm, *buf = sm + N;
+    load_twiddles(tw, g.tw, N);
+    const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
+    const int m = blockIdx.y;
+    const int col = blockIdx.x * kTile + c;   // (ky, kz) flat
+    const int iy = col / g.NZp, kz = col % g.NZp;
+    const bool valid = kz < g.NZ;
+    const int kyi = iy <= g.kc ? iy : iy - g.NK;
+    const float2 *Ain = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
+    auto at = [&](int pos) { return &buf[pos * kTile + c]; };
+    float2 X[3][V];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+            X[q][i] = valid ? Ain[(long long)q * g.sA + (long long)PI::in_pos(p, i) * g.NZp] : make_float2(0.f, 0.f);
+        fft_line<N, true>(X[q], p, tw, at);
+    }
+    const MemberDev &d = md[g.first + m];
+    const float inv_n3 = 1.0f / ((float)N * (float)N * (float)N);
+    const long long rowU = (long long)g.NK * g.NZp;
+    float2 *U = g.U + (long long)m * 3 * g.sU + col;
+    float2 *S = g.S + (long long)m * 3 * g.sU + col;
+    const float wgt = kz == 0 ? 1.f : 2.f;   // Hermitian multiplicity in the full spectrum
+    float se = 0.f, sd = 0.f, sb = 0.f;
+    double dt = 0.0;
+    float alpha = 0.f, nu = 0.f;
+    StageCoef co{};
+    if constexpr (MODE == 0 || MODE == 1) {
+        dt = member_dt(d, N);
+        alpha = (float)d.alpha;
+        nu = (float)d.nu;
+        co = stage_coef(d.rk, stage);
+    }
+    double *shell_smem = reinterpret_cast<double *>(buf);   // reused after the FFTs (MODE 2)
+    if constexpr (MODE == 2) {
+        __syncthreads();
+        for (int s = threadIdx.x; s < g.shells; s += blockDim.x) shell_smem[s] = 0.0;
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int kx = wnum(PI::out_pos(p, i), N);
+        if (!valid || kx < -g.kc || kx > g.kc) continue;
+        const int ix = kx >= 0 ? kx : kx + g.NK;
+        const long long off = ix * rowU;
+        const float fk[3] = {(float)kx, (float)kyi, (float)kz};
+        const int k2i = kx * kx + kyi * kyi + kz * kz;
+        const float k2 = (float)k2i;
+        float2 n[3] = {cscale(X[0][i], inv_n3), cscale(X[1][i], inv_n3), cscale(X[2][i], inv_n3)};
+        if (MODE != 3) {
+            // Leray projection P_ij = delta_ij - k_i k_j / k^2; k = 0 held at zero
+            if (k2i == 0) {
+                n[0] = n[1] = n[2] = make_float2(0.f, 0.f);
+            } else {
+                const float inv = 1.f / k2;
+                const float dr = (fk[0] * n[0].x + fk[1] * n[1].x + fk[2] * n[2].x) * inv;
+                const float di = (fk[0] * n[0].y + fk[1] * n[1].y + fk[2] * n[2].y) * inv;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) n[q] = make_float2(n[q].x - fk[q] * dr, n[q].y - fk[q] * di);
+            }
+        }
+        if constexpr (MODE == 2 || MODE == 3) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) U[q * g.sU + off] = n[q];
+            if constexpr (MODE == 2) {
+                const int s = (int)lrint(sqrt((double)k2i));
+                float a2 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a2 += n[q].x * n[q].x + n[q].y * n[q].y;
+                atomicAdd(&shell_smem[s], 0.5 * (double)(wgt * a2));
+            }
+            continue;
+        } else {
+            const bool band = (double)k2i >= d.klo2 - 1e-9 && (double)k2i <= d.khi2 + 1e-9;
+            float2 us[3], un[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                un[q] = U[q * g.sU + off];
+                us[q] = stage == 0 ? un[q] : S[q * g.sU + off];
+                if (band) n[q] = make_float2(n[q].x + alpha * us[q].x, n[q].y + alpha * us[q].y);
+            }
+            if constexpr (MODE == 1) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) S[q * g.sU + off] = n[q];
+                continue;
+            } else {
+                const float dtf = (float)dt;
+                const float ea = co.a != 0.f ? expf(-nu * k2 * co.ha * dtf) : 0.f;
+                const float eb = expf(-nu * k2 * co.hb * dtf);
+                float2 *dst = last_stage ? U : S;
+                float a2 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float rx = us[q].x + dtf * n[q].x, ry = us[q].y + dtf * n[q].y;
+                    const float ox = co.a * ea * un[q].x + co.b * eb * rx;
+                    const float oy = co.a * ea * un[q].y + co.b * eb * ry;
+                    dst[q * g.sU + off] = make_float2(ox, oy);
+                    a2 += ox * ox + oy * oy;
+                }
+                se += 0.5f * wgt * a2;
+                sd += nu * k2 * wgt * a2;
+                if (band) sb += 0.5f * wgt * a2;
+            }
+        }
+    }
+    if constexpr (MODE == 2) {
+        __syncthreads();
+        double *shell = g.shell + (long long)m * g.shells;
+        for (int s = threadIdx.x; s < g.shells; s += blockDim.x)
+            if (shell_smem[s] != 0.0) atomicAdd(&shell[s], shell_smem[s]);
+    }
+    if constexpr (MODE == 0) {
+        __syncthreads();   // buf is reused as reduction scratch
+        double vals[3] = {(double)se, (double)sd, (double)sb};
+        double *out = g.partial + ((long long)(g.first + m) * g.partial_blocks + blockIdx.x) * 4;
+        block_sum_to<3>(out, vals, reinterpret_cast<double *>(buf));
+    }
+}
+
+}  // namespace ens

@@ -1,0 +1,394 @@
+"""Thin Python binding of libens (include/ens.h).
+
+Argument marshalling only: every computation runs in the CUDA library.
+PyTorch provides the device workspace (``torch.empty`` on the GPU) and the
+CUDA stream (the current torch stream).  There is no CPU fallback: if the
+library is missing or no GPU is present the calls fail loudly.
+
+The module exposes the C entry points under their C names (``ens_create``,
+``ens_step``, ``ens_gradient_stats``, ``ens_mixture``, ...) plus
+:class:`Ensemble`, a small owner object that keeps the workspace alive.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libens.so")
+
+ENS_NMOM = 48
+ENS_NCOUNTERS = 8
+STATUS = {0: "ENS_OK", 1: "ENS_EINVAL", 2: "ENS_ENOMEM", 3: "ENS_ECUDA", 4: "ENS_ENONFINITE",
+          5: "ENS_ETIMEOUT", 6: "ENS_ESTATE", 7: "ENS_EUNSUPPORTED"}
+W_GAUSS_PAPER, W_GAUSS, W_USER, W_TRUNC_GAUSS = 0, 1, 2, 3
+
+
+class EnsError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+
+
+class MemberDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("rk_order", ctypes.c_int), ("nu", ctypes.c_double),
+                ("lam", ctypes.c_double), ("eps_bar", ctypes.c_double), ("k_lo", ctypes.c_double),
+                ("k_hi", ctypes.c_double), ("dt", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("dt_max", ctypes.c_double), ("seed", ctypes.c_uint64), ("init_energy", ctypes.c_double)]
+
+
+class HistSpec(ctypes.Structure):
+    _fields_ = [("qr_bins", ctypes.c_int), ("q_lim", ctypes.c_double), ("r_lim", ctypes.c_double),
+                ("tail_bins", ctypes.c_int), ("tail_lo", ctypes.c_double), ("tail_hi", ctypes.c_double),
+                ("eps_norm", ctypes.c_double), ("nu_norm", ctypes.c_double)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("t", "dt", "E", "diss", "EB", "P", "umax", "Rlambda", "kmeta")] + \
+               [("steps", ctypes.c_int64), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class WeightSpec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("c", ctypes.c_double), ("Z", ctypes.c_double), ("mu", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("user", ctypes.POINTER(ctypes.c_double)), ("renormalize", ctypes.c_int)]
+
+
+class MixtureOut(ctypes.Structure):
+    _fields_ = [("weights", ctypes.POINTER(ctypes.c_double)), ("covered", ctypes.c_double),
+                ("pdf_qr", ctypes.POINTER(ctypes.c_double)), ("pdf_eps", ctypes.POINTER(ctypes.c_double)),
+                ("pdf_ens", ctypes.POINTER(ctypes.c_double)), ("moments", ctypes.POINTER(ctypes.c_double)),
+                ("ratios", ctypes.c_double * 5)]
+
+
+# every symbol declared in include/ens.h: (name, restype, argtypes)
+_P = ctypes.POINTER
+_vp, _i, _d, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+SIGNATURES = [
+    ("ens_query", _i, [_P(MemberDesc), _i, _P(HistSpec), _P(_sz)]),
+    ("ens_create", _i, [_P(MemberDesc), _i, _P(HistSpec), _vp, _sz, _vp, _P(_vp)]),
+    ("ens_destroy", _i, [_vp]),
+    ("ens_last_error", ctypes.c_char_p, [_vp]),
+    ("ens_status_string", ctypes.c_char_p, [_i]),
+    ("ens_step", _i, [_vp, _i]),
+    ("ens_step_nograph", _i, [_vp, _i]),
+    ("ens_gradient_stats", _i, [_vp, _i]),
+    ("ens_get_stats", _i, [_vp, _vp, _vp]),
+    ("ens_counts_len", _i, [_P(HistSpec)]),
+    ("ens_mixture", _i, [_vp, _P(WeightSpec), _P(MixtureOut)]),
+    ("ens_mixture_host", _i, [_i, _vp, _vp, _vp, _P(HistSpec), _P(WeightSpec), _P(MixtureOut), _vp]),
+    ("ens_get_field", _i, [_vp, _i, _vp]),
+    ("ens_set_field", _i, [_vp, _i, _vp]),
+    ("ens_state_bytes", _sz, [_vp]),
+    ("ens_get_state", _i, [_vp, _vp, _sz]),
+    ("ens_set_state", _i, [_vp, _vp, _sz]),
+    ("ens_get_velocity", _i, [_vp, _i, _vp]),
+    ("ens_set_velocity", _i, [_vp, _i, _vp]),
+    ("ens_rhs", _i, [_vp, _i, _vp]),
+    ("ens_diagnostics", _i, [_vp, _P(Diag)]),
+    ("ens_synchronize", _i, [_vp]),
+    ("ens_members", _i, [_vp]),
+    ("ens_member_n", _i, [_vp, _i]),
+    ("ens_run_pass", _i, [_vp, _i, _i]),
+    ("ens_kernels_per_step", _i, [_vp]),
+    ("ens_pass_bytes", _d, [_vp, _i, _i]),
+]
+
+_lib = None
+
+
+def lib():
+    """Load libens.so (built by ``__graft_entry__.build()``); no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libens.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = lib().ens_last_error(ctx).decode() if ctx else ""
+        raise EnsError(status, msg)
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# C entry points under their own names (marshalling only)
+# ---------------------------------------------------------------------------
+def ens_query(members: Sequence[MemberDesc], hist: HistSpec) -> int:
+    arr = (MemberDesc * len(members))(*members)
+    out = ctypes.c_size_t()
+    _check(lib().ens_query(arr, len(members), ctypes.byref(hist), ctypes.byref(out)))
+    return out.value
+
+
+def ens_create(members, hist, workspace_ptr, workspace_bytes, stream_ptr):
+    arr = (MemberDesc * len(members))(*members)
+    ctx = ctypes.c_void_p()
+    _check(lib().ens_create(arr, len(members), ctypes.byref(hist), ctypes.c_void_p(workspace_ptr),
+                            workspace_bytes, stream_ptr, ctypes.byref(ctx)))
+    return ctx
+
+
+def ens_destroy(ctx):
+    _check(lib().ens_destroy(ctx))
+
+
+def ens_step(ctx, nsteps=1):
+    _check(lib().ens_step(ctx, nsteps), ctx)
+
+
+def ens_step_nograph(ctx, nsteps=1):
+    _check(lib().ens_step_nograph(ctx, nsteps), ctx)
+
+
+def ens_gradient_stats(ctx, accumulate=True):
+    _check(lib().ens_gradient_stats(ctx, int(bool(accumulate))), ctx)
+
+
+def ens_counts_len(hist: HistSpec) -> int:
+    return lib().ens_counts_len(ctypes.byref(hist))
+
+
+def ens_get_stats(ctx, n, counts_len):
+    counts = np.zeros((n, counts_len), dtype=np.uint64)
+    moments = np.zeros((n, ENS_NMOM), dtype=np.float64)
+    _check(lib().ens_get_stats(ctx, _ptr(counts), _ptr(moments)), ctx)
+    return counts, moments
+
+
+def _weight_spec(kind, c=0.023, Z=1.0, mu=0.0, sigma=1.0, user=None, renormalize=True):
+    ws = WeightSpec(kind, c, Z, mu, sigma, None, int(bool(renormalize)))
+    keep = None
+    if user is not None:
+        keep = np.ascontiguousarray(user, dtype=np.float64)
+        ws.user = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return ws, keep
+
+
+def _mixture_out(n, hist):
+    nq, nt = hist.qr_bins, hist.tail_bins
+    bufs = {"weights": np.zeros(n), "pdf_qr": np.zeros(nq * nq), "pdf_eps": np.zeros(nt),
+            "pdf_ens": np.zeros(nt), "moments": np.zeros(ENS_NMOM)}
+    out = MixtureOut()
+    for k, v in bufs.items():
+        setattr(out, k, v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out, bufs
+
+
+def _mixture_result(out, bufs, hist):
+    nq = hist.qr_bins
+    return {"weights": bufs["weights"], "covered": out.covered, "pdf_qr": bufs["pdf_qr"].reshape(nq, nq),
+            "pdf_eps": bufs["pdf_eps"], "pdf_ens": bufs["pdf_ens"], "moments": bufs["moments"],
+            "ratios": dict(zip(("S_long", "F_long", "F_trans", "H_long", "H_trans"), list(out.ratios)))}
+
+
+def ens_mixture(ctx, n, hist, **weights):
+    ws, keep = _weight_spec(**weights)
+    out, bufs = _mixture_out(n, hist)
+    _check(lib().ens_mixture(ctx, ctypes.byref(ws), ctypes.byref(out)), ctx)
+    return _mixture_result(out, bufs, hist)
+
+
+def ens_mixture_host(lambdas, counts, moments, hist, stream_ptr=None, **weights):
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    moments = np.ascontiguousarray(moments, dtype=np.float64)
+    n = lam.size
+    ws, keep = _weight_spec(**weights)
+    out, bufs = _mixture_out(n, hist)
+    if stream_ptr is None:
+        stream_ptr = _stream_ptr()
+    _check(lib().ens_mixture_host(n, _ptr(lam), _ptr(counts), _ptr(moments), ctypes.byref(hist),
+                                  ctypes.byref(ws), ctypes.byref(out), stream_ptr))
+    return _mixture_result(out, bufs, hist)
+
+
+def _full_shape(N):
+    return (3, N, N, N // 2 + 1)
+
+
+def ens_get_field(ctx, member, N):
+    out = np.zeros(_full_shape(N), dtype=np.complex128)
+    _check(lib().ens_get_field(ctx, member, _ptr(out)), ctx)
+    return out
+
+
+def ens_set_field(ctx, member, field_):
+    a = np.ascontiguousarray(field_, dtype=np.complex128)
+    _check(lib().ens_set_field(ctx, member, _ptr(a)), ctx)
+
+
+def ens_get_velocity(ctx, member, N):
+    out = np.zeros((3, N, N, N), dtype=np.float64)
+    _check(lib().ens_get_velocity(ctx, member, _ptr(out)), ctx)
+    return out
+
+
+def ens_set_velocity(ctx, member, u):
+    a = np.ascontiguousarray(u, dtype=np.float64)
+    _check(lib().ens_set_velocity(ctx, member, _ptr(a)), ctx)
+
+
+def ens_rhs(ctx, member, N):
+    out = np.zeros(_full_shape(N), dtype=np.complex128)
+    _check(lib().ens_rhs(ctx, member, _ptr(out)), ctx)
+    return out
+
+
+def ens_state_bytes(ctx) -> int:
+    return lib().ens_state_bytes(ctx)
+
+
+def ens_get_state(ctx, host_ptr, nbytes):
+    _check(lib().ens_get_state(ctx, ctypes.c_void_p(host_ptr), nbytes), ctx)
+
+
+def ens_set_state(ctx, host_ptr, nbytes):
+    _check(lib().ens_set_state(ctx, ctypes.c_void_p(host_ptr), nbytes), ctx)
+
+
+DIAG_KEYS = ("t", "dt", "E", "diss", "EB", "P", "umax", "Rlambda", "kmeta", "steps", "flags")
+
+
+def ens_diagnostics(ctx, n, raise_on_flag=True):
+    arr = (Diag * n)()
+    st = lib().ens_diagnostics(ctx, arr)
+    if st not in (0, 4, 6) or (raise_on_flag and st != 0):
+        _check(st, ctx)
+    return [{k: getattr(d, k) for k in DIAG_KEYS} for d in arr], st
+
+
+def ens_synchronize(ctx):
+    _check(lib().ens_synchronize(ctx), ctx)
+
+
+def ens_run_pass(ctx, pass_id, stage=0):
+    _check(lib().ens_run_pass(ctx, pass_id, stage), ctx)
+
+
+def ens_pass_bytes(ctx, pass_id, stage=0) -> float:
+    return lib().ens_pass_bytes(ctx, pass_id, stage)
+
+
+def ens_kernels_per_step(ctx) -> int:
+    return lib().ens_kernels_per_step(ctx)
+
+
+# ---------------------------------------------------------------------------
+# owner object
+# ---------------------------------------------------------------------------
+@dataclass
+class Member:
+    """One ensemble member (mirrors ens_member_desc)."""
+    N: int
+    nu: float
+    lam: float = 0.0
+    eps_bar: float = 0.1
+    k_lo: float = 1.0
+    k_hi: float = 2.0
+    dt: float = 0.01
+    cfl: float = 0.2
+    dt_max: float = 0.0
+    rk_order: int = 3
+    seed: int = 0
+    init_energy: float = 0.5
+
+    def c(self) -> MemberDesc:
+        return MemberDesc(self.N, self.rk_order, self.nu, self.lam, self.eps_bar, self.k_lo, self.k_hi, self.dt,
+                          self.cfl, self.dt_max, self.seed, self.init_energy)
+
+
+def hist_spec(qr_bins=64, q_lim=10.0, r_lim=10.0, tail_bins=256, tail_lo=-8.0, tail_hi=8.0, eps_norm=0.1,
+              nu_norm=0.01) -> HistSpec:
+    return HistSpec(qr_bins, q_lim, r_lim, tail_bins, tail_lo, tail_hi, eps_norm, nu_norm)
+
+
+class Ensemble:
+    """An ensemble on the current CUDA device.  Torch allocates the device
+    workspace and supplies the stream; libens does all the work."""
+
+    def __init__(self, members: Sequence[Member], hist: Optional[HistSpec] = None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libens needs a CUDA GPU; no CPU fallback exists")
+        self.members = list(members)
+        self.hist = hist if hist is not None else hist_spec(nu_norm=self.members[0].nu,
+                                                             eps_norm=self.members[0].eps_bar)
+        descs = [m.c() for m in self.members]
+        nbytes = ens_query(descs, self.hist)
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = ens_create(descs, self.hist, self._ws.data_ptr(), nbytes, _stream_ptr(self._stream))
+        self.counts_len = ens_counts_len(self.hist)
+
+    @property
+    def n(self):
+        return len(self.members)
+
+    def step(self, nsteps=1, graph=True):
+        (ens_step if graph else ens_step_nograph)(self.ctx, nsteps)
+
+    def gradient_stats(self, accumulate=True):
+        ens_gradient_stats(self.ctx, accumulate)
+
+    def stats(self):
+        return ens_get_stats(self.ctx, self.n, self.counts_len)
+
+    def mixture(self, **weights):
+        return ens_mixture(self.ctx, self.n, self.hist, **weights)
+
+    def field(self, i):
+        return ens_get_field(self.ctx, i, self.members[i].N)
+
+    def set_field(self, i, f):
+        ens_set_field(self.ctx, i, f)
+
+    def velocity(self, i):
+        return ens_get_velocity(self.ctx, i, self.members[i].N)
+
+    def set_velocity(self, i, u):
+        ens_set_velocity(self.ctx, i, u)
+
+    def rhs(self, i):
+        return ens_rhs(self.ctx, i, self.members[i].N)
+
+    def diagnostics(self, raise_on_flag=True):
+        return ens_diagnostics(self.ctx, self.n, raise_on_flag)[0]
+
+    def synchronize(self):
+        ens_synchronize(self.ctx)
+
+    def state_bytes(self):
+        return ens_state_bytes(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ens_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,308 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances: relative L2 error <= 1e-5 after one step and <= 1e-3 after 100
+steps at 32^3 (the target of this implementation); transforms and the
+right-hand side of a single evaluation, computed in FP32 with FP32
+accumulation, are held to <= 2e-6.  Histograms: every bin holding more than
+1000 counts within 2%; point totals exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ens_inputs as I
+import oracle as O
+import oracle.mixture as OM
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def E():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2506_23712_gb300 import build as B
+    B.build()
+    import paper_2506_23712_gb300.ens as ens
+    return ens
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def config0(E, **kw):
+    p = dict(N=32, nu=0.02, lam=0.0, eps_bar=0.1, k_lo=1, k_hi=2, dt=0.01, rk_order=2, seed=0, init_energy=0.5)
+    p.update(kw)
+    return E.Member(**p)
+
+
+def oracle_member(m):
+    return O.Member(N=m.N, nu=m.nu, lam=m.lam, eps_bar=m.eps_bar, k_lo=m.k_lo, k_hi=m.k_hi, dt=m.dt, cfl=m.cfl,
+                    dt_max=m.dt_max, rk_order=m.rk_order, seed=m.seed, init_energy=m.init_energy)
+
+
+@pytest.mark.parametrize("N", [16, 32, 64])
+def test_initial_field_matches_oracle(E, N):
+    m = config0(E, N=N, k_hi=min(2, O.kc(N)), seed=7)
+    ens = E.Ensemble([m])
+    got = ens.field(0)
+    ref = O.initial_field(oracle_member(m))
+    assert rel(got, ref) < 2e-6
+    d = ens.diagnostics()[0]
+    assert d["E"] == pytest.approx(0.5, rel=1e-5)
+    ens.close()
+
+
+@pytest.mark.parametrize("N", [16, 32, 64, 128])
+def test_inverse_transform_matches_oracle(E, N):
+    ens = E.Ensemble([config0(E, N=N)])
+    uh = I.random_spectral(N, 100 + N)
+    ens.set_field(0, uh)
+    got = ens.velocity(0)
+    ref = np.stack([O.irfft3(c) for c in uh])
+    assert rel(got, ref) < 2e-6
+    ens.close()
+
+
+@pytest.mark.parametrize("N", [16, 32, 64, 128])
+def test_forward_transform_matches_oracle(E, N):
+    ens = E.Ensemble([config0(E, N=N)])
+    u = I.random_physical(N, N)
+    ens.set_velocity(0, u)
+    got = ens.field(0)
+    ref = np.stack([O.rfft3(c) for c in u])
+    ref[:, ~I.kept_mask(N)] = 0.0
+    assert rel(got, ref) < 2e-6
+    ens.close()
+
+
+@pytest.mark.parametrize("N", [256, 384, 512])
+def test_transform_round_trip_large(E, N):
+    """Property at full size: a band-limited field comes back exactly, and its
+    spectral coefficients are the known cosine amplitudes a/2."""
+    kc = O.kc(N)
+    modes = [(0, (1, 2, 3), 0.7), (1, (kc, -5, 2), 0.3), (2, (-7, kc, kc), 0.2), (0, (0, 0, kc), 0.1)]
+    u = I.cosine_modes(N, modes)
+    ens = E.Ensemble([config0(E, N=N, rk_order=3)])
+    ens.set_velocity(0, u)
+    f = ens.field(0)
+    assert abs(f[0, 1, 2, 3] - 0.35) < 1e-5 and abs(f[1, kc, N - 5, 2] - 0.15) < 1e-5
+    assert abs(f[2, N - 7, kc, kc] - 0.1) < 1e-5 and abs(f[0, 0, 0, kc] - 0.05) < 1e-5
+    back = ens.velocity(0)
+    assert np.abs(back - u).max() < 2e-5
+    ens.close()
+
+
+@pytest.mark.parametrize("N,rk", [(16, 2), (32, 2), (32, 3), (64, 3)])
+def test_rhs_matches_oracle(E, N, rk):
+    m = config0(E, N=N, rk_order=rk, lam=0.4, k_lo=1, k_hi=2, seed=3)
+    ens = E.Ensemble([m])
+    F = ens.rhs(0)                       # at the library's own initial field
+    om = oracle_member(m)
+    Fref, nl, umax, alpha = O.rhs(om, O.initial_field(om))
+    assert rel(F, Fref) < 2e-6
+    ens.close()
+
+
+def test_one_step_and_100_steps_config0(E):
+    """32^3, nu = 0.02, band [1,2], IF-RK2, dt = 0.01 (the single-member
+    configuration): rel L2 <= 1e-5 after 1 step, <= 1e-3 after 100."""
+    m = config0(E)
+    ens = E.Ensemble([m])
+    om = oracle_member(m)
+    ref = O.initial_field(om)
+    ens.step(1)
+    st, d = O.step(om, ref, 1)
+    assert st == 0
+    assert rel(ens.field(0), ref) < 1e-5
+    g = ens.diagnostics()[0]
+    assert g["t"] == pytest.approx(0.01) and g["steps"] == 1
+    assert g["E"] == pytest.approx(d["E"], rel=1e-5)
+    assert g["P"] == pytest.approx(0.1, rel=1e-5)
+    ens.step(99)
+    st, d = O.step(om, ref, 99)
+    err = rel(ens.field(0), ref)
+    assert err < 1e-3, err
+    g = ens.diagnostics()[0]
+    assert g["steps"] == 100 and g["t"] == pytest.approx(1.0)
+    assert g["E"] == pytest.approx(d["E"], rel=1e-3)
+    ens.close()
+
+
+def test_graph_and_direct_launch_agree(E):
+    ms = [config0(E, seed=s) for s in range(2)]
+    a = E.Ensemble(ms)
+    b = E.Ensemble(ms)
+    a.step(3, graph=True)
+    b.step(3, graph=False)
+    for i in range(2):
+        assert np.array_equal(a.field(i), b.field(i))
+    a.close()
+    b.close()
+
+
+def test_cfl_rk3_ensemble_members_match_oracle(E):
+    """Several members of uneven lambda in one launch, RK3, CFL-adaptive
+    step (Sec. IV: CFL = 0.2), each equal to its own oracle run."""
+    lams = [-1.5, 0.0, 1.2]
+    ms = [E.Member(N=32, nu=0.02, lam=l, k_lo=1, k_hi=2, dt=-1, cfl=0.2, dt_max=0.02, rk_order=3, seed=10 + i)
+          for i, l in enumerate(lams)]
+    ens = E.Ensemble(ms)
+    ens.step(2)
+    diags = ens.diagnostics()
+    for i, m in enumerate(ms):
+        om = oracle_member(m)
+        ref = O.initial_field(om)
+        st, d = O.step(om, ref, 2)
+        assert rel(ens.field(i), ref) < 1e-5
+        assert diags[i]["dt"] == pytest.approx(d["dt"], rel=1e-5)
+        assert diags[i]["P"] == pytest.approx(math.exp(m.lam) * 0.1, rel=1e-5)
+    ens.close()
+
+
+def test_uneven_sizes_in_one_context(E):
+    """Members of different N share one context (grouped by N); each matches
+    its oracle run after one step."""
+    ms = [E.Member(N=n, nu=0.03, lam=0.1 * i, k_lo=1, k_hi=2, dt=0.005, rk_order=3, seed=20 + i)
+          for i, n in enumerate([32, 16, 32, 64])]
+    ens = E.Ensemble(ms)
+    ens.step(1)
+    for i, m in enumerate(ms):
+        om = oracle_member(m)
+        ref = O.initial_field(om)
+        O.step(om, ref, 1)
+        assert rel(ens.field(i), ref) < 1e-5, (i, m.N)
+    ens.close()
+
+
+def test_statistics_match_oracle(E):
+    m = config0(E, init_energy=2.0)
+    N = m.N
+    h = E.hist_spec(qr_bins=64, q_lim=10.0, r_lim=10.0, tail_bins=256, tail_lo=-8, tail_hi=8, eps_norm=0.1,
+                    nu_norm=0.02)
+    ens = E.Ensemble([m], hist=h)
+    ens.step(2)
+    om = oracle_member(m)
+    uh = O.initial_field(om)             # the oracle's own state after two steps
+    assert O.step(om, uh, 2)[0] == 0
+    ens.gradient_stats(accumulate=False)
+    ens.gradient_stats(accumulate=True)
+    counts, mom = ens.stats()
+    oh = O.HistSpec(qr_bins=64, q_lim=10.0, r_lim=10.0, tail_bins=256, tail_lo=-8, tail_hi=8, eps_norm=0.1,
+                    nu_norm=0.02)
+    rc, rm = O.gradient_stats(uh, m.nu, oh)
+    rc2, rm2 = O.gradient_stats(uh, m.nu, oh, rc.copy(), rm.copy())
+    c, r = counts[0].astype(np.int64), rc2.astype(np.int64)
+    L = len(r)
+    assert c[L - 2] == r[L - 2] == 2 * N ** 3                    # npoints exact
+    for lo, hi in ((0, 64 * 64), (64 * 64, 64 * 64 + 256), (64 * 64 + 256, 64 * 64 + 512)):
+        assert c[lo:hi].sum() + 0 == pytest.approx(r[lo:hi].sum(), abs=max(4, 1e-3 * r[lo:hi].sum()))
+        big = r[lo:hi] > 1000
+        assert np.all(np.abs(c[lo:hi][big] - r[lo:hi][big]) <= 0.02 * r[lo:hi][big])
+    # moments: FP32 per point, FP64 reductions
+    for k in list(range(0, 36, 4)) + [38, 39]:
+        assert mom[0, k] == pytest.approx(rm2[k], rel=1e-4)
+    # <Q> = <R> = 0 (Sec. V definitions; periodic box): sums small vs |Q| scale
+    assert abs(mom[0, 36]) < 1e-4 * math.sqrt(mom[0, 40] * 2 * N ** 3)
+    ens.close()
+
+
+def test_mixture_matches_oracle(E):
+    lams = [-1.0, -0.3, 0.4, 1.1]
+    ms = [E.Member(N=16, nu=0.05, lam=l, k_lo=1, k_hi=2, dt=0.01, rk_order=2, seed=i) for i, l in enumerate(lams)]
+    h = E.hist_spec(qr_bins=16, q_lim=5.0, r_lim=5.0, tail_bins=32, tail_lo=-4, tail_hi=3, eps_norm=0.1,
+                    nu_norm=0.05)
+    ens = E.Ensemble(ms, hist=h)
+    ens.step(2)
+    ens.gradient_stats(accumulate=False)
+    counts, mom = ens.stats()
+    oh = O.HistSpec(qr_bins=16, q_lim=5.0, r_lim=5.0, tail_bins=32, tail_lo=-4, tail_hi=3, eps_norm=0.1,
+                    nu_norm=0.05)
+    for kind, kw in (("gauss_paper", dict(c=0.023, Z=2.0)), ("gauss", dict(mu=0.0, sigma=1.5)),
+                     ("trunc_gauss", dict(c=0.023, Z=2.0))):
+        wk = {"gauss_paper": E.W_GAUSS_PAPER, "gauss": E.W_GAUSS, "trunc_gauss": E.W_TRUNC_GAUSS}[kind]
+        got = ens.mixture(kind=wk, renormalize=True, **kw)
+        w, cov = OM.member_weights(lams, kind, **kw)
+        assert np.allclose(got["weights"], w, rtol=1e-12, atol=1e-15)
+        qr, pe, pw = OM.mix_counts(counts, w, oh)
+        assert np.allclose(got["pdf_qr"], qr, rtol=1e-12, atol=1e-15)
+        assert np.allclose(got["pdf_eps"], pe, rtol=1e-12, atol=1e-15)
+        npts = counts[:, -2]
+        mm = OM.mix_moments(mom, npts, w)
+        assert np.allclose(got["moments"], mm, rtol=1e-12, atol=1e-300)
+        ratios = OM.gradient_moment_ratios(mm)
+        for k, v in ratios.items():
+            assert got["ratios"][k] == pytest.approx(v, rel=1e-12)
+    # host-input variant on the same data
+    got = E.ens_mixture_host(lams, counts, mom, h, kind=E.W_GAUSS_PAPER, c=0.023, Z=2.0)
+    w, _ = OM.member_weights(lams, "gauss_paper", c=0.023, Z=2.0)
+    assert np.allclose(got["weights"], w, rtol=1e-12)
+    ens.close()
+
+
+def test_abc_flow_exact_decay_full_size(E):
+    """Property at 256^3: the ABC (Beltrami) flow has u x omega = 0, so with
+    negligible forcing it decays as exp(-nu t) mode by mode."""
+    N = 256
+    u = I.abc_flow(N)
+    m = E.Member(N=N, nu=0.005, lam=-60.0, k_lo=1, k_hi=1.5, dt=0.05, rk_order=3, seed=0)
+    ens = E.Ensemble([m])
+    ens.set_velocity(0, u)
+    E0 = ens.diagnostics()[0]["E"]
+    ens.step(4)
+    d = ens.diagnostics()[0]
+    assert d["E"] == pytest.approx(E0 * math.exp(-2 * 0.005 * 0.2), rel=2e-6)
+    ens.close()
+
+
+def test_full_size_member_properties(E):
+    """256^3 member of the ensemble configuration (nu = 0.005, band [6, 8],
+    RK3, CFL 0.2): solenoidal after steps, injected power exact, energy
+    budget dE/dt ~ P - eps, and the statistics' identities <Q> = <R> = 0,
+    <eps> = spectral dissipation."""
+    N = 256
+    m = E.Member(N=N, nu=0.005, lam=0.5, k_lo=6, k_hi=8, dt=-1, cfl=0.2, rk_order=3, seed=2026)
+    ens = E.Ensemble([m], hist=E.hist_spec(nu_norm=0.005))
+    d0 = ens.diagnostics()[0]
+    ens.step(2)
+    d1 = ens.diagnostics()[0]
+    assert d1["P"] == pytest.approx(math.exp(0.5) * 0.1, rel=1e-6)
+    f = ens.field(0)
+    k = np.fft.fftfreq(N, 1.0 / N)
+    KX, KY, KZ = np.meshgrid(k, k, np.arange(N // 2 + 1), indexing="ij")
+    div = np.abs(KX * f[0] + KY * f[1] + KZ * f[2]).max()
+    assert div < 1e-5 * np.abs(f).max() * O.kc(N)
+    # one more step, energy budget with the midpoint rule
+    dt = d1["dt"]
+    ens.step(1)
+    d2 = ens.diagnostics()[0]
+    dEdt = (d2["E"] - d1["E"]) / d2["dt"]
+    assert dEdt == pytest.approx(d2["P"] - 0.5 * (d1["diss"] + d2["diss"]), abs=0.05 * d2["P"])
+    ens.gradient_stats(accumulate=False)
+    counts, mom = ens.stats()
+    n3 = N ** 3
+    assert counts[0, -2] == n3
+    assert mom[0, 38] / n3 == pytest.approx(d2["diss"], rel=1e-4)
+    assert abs(mom[0, 36] / n3) < 1e-4 * math.sqrt(mom[0, 40] / n3)
+    assert abs(mom[0, 37] / n3) < 1e-3 * math.sqrt(mom[0, 41] / n3)
+    assert dt > 0
+    ens.close()
+
+
+def test_nonfinite_member_is_reported(E):
+    """A member poisoned on the host (NaN in one mode) is flagged after the
+    next step and ens_diagnostics returns ENS_ENONFINITE."""
+    ms = [config0(E, seed=1), config0(E, seed=2)]
+    ens = E.Ensemble(ms)
+    f = ens.field(1)
+    f[0, 1, 1, 1] = np.nan
+    ens.set_field(1, f)
+    ens.step(1)
+    diags, status = E.ens_diagnostics(ens.ctx, 2, raise_on_flag=False)
+    assert status == 4
+    assert diags[1]["flags"] & 1 and not diags[0]["flags"] & 1
+    ens.close()
