@@ -1,0 +1,385 @@
+"""Benchmark of the ensemble DNS hot path on GB300.
+
+Workload (one "step" = one IF-RK3 step of every member): 64 members on 256^3
+grids, nu = 0.005, forcing band 6 <= |k| <= 8 at injection rate
+exp(lambda) * 0.1 with lambda ~ N(0, 2^2) clipped to [-5.1, 5.8], CFL 0.2
+(the shape of the paper's ens256 ensemble, Sec. IV, Table I).  Synthetic
+seeded initial fields; the state (8.6 GB) is far larger than L2.
+
+Prints one JSON line: member-steps/s (value), grid-point updates/s, the
+roofline of the dominant kernel against the measured HBM copy bandwidth, the
+FP64 CPU oracle on the host cores (cpu_baseline), the same metric through
+the C ABI with the state streamed from/to pinned host memory every step
+(e2e), SM clocks sampled during the timed region, and the plain
+one-member-at-a-time torch.fft FP32 path on the same GPU for comparison.
+
+--impl reference times the FP64 oracle (the reference arm) on the host cores
+on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ensemble member-steps/s at 256^3, batched FP32 vs plain; % of HBM roofline"
+UNIT = "member-steps/s"
+WORKLOAD = "ensemble_256: 64 members x 256^3, nu=0.005, band 6<=|k|<=8, eps=exp(lambda)*0.1, " \
+           "lambda~N(0,2^2) clipped [-5.1,5.8], IF-RK3, CFL 0.2"
+PASS_NAMES = ["inv_x", "inv_y", "z_nonlinear", "fwd_y", "fwd_x_update"]
+PASS_KERNELS = ["k_inv_x", "k_inv_y", "k_z", "k_fwd_y", "k_fwd_x"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--members", type=int, default=64)
+    p.add_argument("--N", type=int, default=256)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# plain one-member-at-a-time FP32 path (comparison baseline; torch.fft + unfused ops)
+# ---------------------------------------------------------------------------
+def plain_member_steps(member, nsteps, torch):
+    N = member["N"]
+    dev = "cuda"
+    kc = (N + 2) // 3 - 1
+    k = torch.fft.fftfreq(N, 1.0 / N, device=dev)
+    kz = torch.arange(N // 2 + 1, device=dev, dtype=torch.float32)
+    KX, KY, KZ = torch.meshgrid(k, k, kz, indexing="ij")
+    K = torch.stack([KX, KY, KZ])
+    k2 = (K * K).sum(0)
+    k2s = torch.where(k2 == 0, torch.ones_like(k2), k2)
+    mask = ((KX.abs() <= kc) & (KY.abs() <= kc) & (KZ <= kc)).to(torch.float32)
+    band = ((k2 >= member["k_lo"] ** 2 - 1e-9) & (k2 <= member["k_hi"] ** 2 + 1e-9)).to(torch.float32)
+    wgt = torch.where(KZ == 0, torch.ones_like(KZ), 2 * torch.ones_like(KZ))
+    eps_inj = math.exp(member["lam"]) * member["eps_bar"]
+    nu = member["nu"]
+    g = torch.Generator(device=dev).manual_seed(member["seed"])
+    u0 = torch.randn((3, N, N, N), device=dev, generator=g)
+    uh = torch.fft.rfftn(u0, dim=(1, 2, 3), norm="forward") * mask
+    uh = uh - K * (K * uh).sum(0) / k2s
+    uh = uh * (0.5 / (0.5 * (wgt * (uh.abs() ** 2).sum(0)).sum())).sqrt()
+
+    def rhs(v):
+        w = 1j * torch.linalg.cross(K.to(v.dtype), v, dim=0)
+        u = torch.fft.irfftn(v, s=(N, N, N), dim=(1, 2, 3), norm="forward")
+        om = torch.fft.irfftn(w, s=(N, N, N), dim=(1, 2, 3), norm="forward")
+        umax = u.abs().max()
+        n = torch.linalg.cross(u, om, dim=0)
+        nh = torch.fft.rfftn(n, dim=(1, 2, 3), norm="forward") * mask
+        nh = nh - K * (K * nh).sum(0) / k2s
+        EB = 0.5 * (band * wgt * (v.abs() ** 2).sum(0)).sum()
+        return nh + (eps_inj / (2 * EB)) * band * v, umax
+
+    def E(h):
+        return torch.exp(-nu * k2 * h)
+
+    for _ in range(nsteps):
+        F, umax = rhs(uh)
+        dt = member["cfl"] * (2 * math.pi / N) / umax
+        u1 = E(dt) * (uh + dt * F)
+        F1, _ = rhs(u1)
+        u2 = 0.75 * E(dt / 2) * uh + 0.25 * E(-dt / 2) * (u1 + dt * F1)
+        F2, _ = rhs(u2)
+        uh = E(dt) * uh / 3 + 2.0 / 3.0 * E(dt / 2) * (u2 + dt * F2)
+    return uh
+
+
+def time_plain(members, torch, n_members=2, nsteps=2):
+    torch.cuda.synchronize()
+    plain_member_steps(members[0], 1, torch)   # warm-up (cuFFT plans)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    for m in members[:n_members]:
+        plain_member_steps(m, nsteps, torch)
+    end.record()
+    torch.cuda.synchronize()
+    sec = start.elapsed_time(end) / 1e3
+    return n_members * nsteps / sec
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_member(d):
+    import oracle as O
+    return O.Member(N=d["N"], nu=d["nu"], lam=d["lam"], eps_bar=d["eps_bar"], k_lo=d["k_lo"], k_hi=d["k_hi"],
+                    dt=d["dt"], cfl=d["cfl"], dt_max=d["dt_max"], rk_order=d["rk_order"], seed=d["seed"],
+                    init_energy=d["init_energy"])
+
+
+def cpu_baseline(member_dict):
+    """One full IF-RK3 step of one 256^3 member with the FP64 oracle."""
+    import oracle as O
+    O.build()
+    m = oracle_member(member_dict)
+    uh = O.initial_field(m)
+    t0 = time.perf_counter()
+    st, _ = O.step(m, uh, 1)
+    sec = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one IF-RK3 step of one %d^3 member (FP64 oracle, own FFT), %.1f s" % (m.N, sec)}
+
+
+def run_reference(args, members):
+    """Reference arm: the FP64 oracle, each step = one right-hand-side
+    evaluation (one RK stage, 1/3 of a member-step) of one 256^3 member."""
+    import oracle as O
+    O.build()
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    m = oracle_member(members[0])
+    uh = O.initial_field(m)
+    for _ in range(args.warmup):
+        O.rhs(m, uh)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.rhs(m, uh)
+    sec = time.perf_counter() - t0
+    value = (args.steps / 3.0) / sec
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "per step: one right-hand-side evaluation (one of three RK3 stages) of one %d^3 member" % m.N
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "members": len(members), "N": m.N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def traffic_for(kernel):
+    """ncu DRAM bytes per launch of the kernel (profiles/traffic.json), or None
+    if the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    src = os.path.join(ROOT, "paper_2506_23712_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(src)):
+        with open(os.path.join(src, name), "rb") as f:
+            h.update(f.read())
+    if t.get("source_sha256") != h.hexdigest():
+        return None
+    return t.get("kernels", {}).get(kernel)
+
+
+def main():
+    args = parse()
+    import ens_inputs as I
+    members = I.ensemble_256(args.members, args.N)
+    if args.impl == "reference":
+        run_reference(args, members)
+        return
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2506_23712_gb300 import ens as E
+
+    # weak scaling: every rank advances its own ensemble of the same shape
+    descs = [E.Member(N=d["N"], nu=d["nu"], lam=d["lam"], eps_bar=d["eps_bar"], k_lo=d["k_lo"], k_hi=d["k_hi"],
+                      dt=d["dt"], cfl=d["cfl"], dt_max=d["dt_max"], rk_order=d["rk_order"],
+                      seed=d["seed"] + 100000 * rank, init_energy=d["init_energy"]) for d in members]
+    hist = E.hist_spec(nu_norm=0.005, eps_norm=0.1)
+    stream = torch.cuda.current_stream()
+    ens = E.Ensemble(descs, hist=hist, stream=stream)
+    n_mem = len(descs)
+    kps = E.ens_kernels_per_step(ens.ctx)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ens.step(1)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    ens.step(args.steps)
+    end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n_mem * args.steps / (ms / 1e3)
+    diags = ens.diagnostics(raise_on_flag=False)
+    flagged = sum(1 for d in diags if d["flags"])
+
+    # per-pass device times (CUDA events on the library's stream), stage 1
+    hbm, peak_kind = measured_peaks()
+    passes = {}
+    reps = 5
+    for p, name in enumerate(PASS_NAMES):
+        E.ens_run_pass(ens.ctx, p, 1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            E.ens_run_pass(ens.ctx, p, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b) / reps
+        nbytes = E.ens_pass_bytes(ens.ctx, p, 1)
+        passes[name] = {"ms": round(pms, 4), "algorithmic_GB": round(nbytes / 1e9, 4),
+                        "GBps": round(nbytes / 1e9 / (pms / 1e3), 1),
+                        "frac": round(nbytes / 1e9 / (pms / 1e3) / hbm, 4)}
+    dom = max(passes, key=lambda k: passes[k]["ms"])
+    dom_idx = PASS_NAMES.index(dom)
+    achieved = passes[dom]["GBps"]
+    roofline = {"bound": "hbm", "kernel": PASS_KERNELS[dom_idx], "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_source": peak_kind + " hbm_gbs (copy)",
+                "traffic": traffic_for(PASS_KERNELS[dom_idx]),
+                "algorithmic_bytes_per_launch": passes[dom]["algorithmic_GB"] * 1e9}
+    step_bytes = sum(E.ens_pass_bytes(ens.ctx, p, s) for p in range(5) for s in range(3))
+    step_frac = step_bytes / 1e9 / (ms_per_step / 1e3) / hbm
+
+    # e2e: the state streamed from pinned host memory through the C ABI every step
+    e2e = None
+    if not args.no_e2e:
+        nbytes = ens.state_bytes()
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        E.ens_get_state(ens.ctx, host.data_ptr(), nbytes)
+        e2e_steps = max(2, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            E.ens_set_state(ens.ctx, host.data_ptr(), nbytes)
+            ens.step(1)
+            E.ens_get_state(ens.ctx, host.data_ptr(), nbytes)
+            dg, _ = E.ens_diagnostics(ens.ctx, n_mem, raise_on_flag=False)
+        barrier()
+        sec = time.perf_counter() - t0
+        diag_bytes = n_mem * 96
+        e2e = {"value": world * n_mem * e2e_steps / sec, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes + diag_bytes, "steps": e2e_steps,
+               "path": "ens_set_state(pinned host) + ens_step + ens_get_state(pinned host) + ens_diagnostics"}
+
+    plain = None
+    if not args.no_plain and rank == 0:
+        pv = time_plain(members, torch)
+        plain = {"value": pv, "unit": UNIT, "path": "one member at a time, torch.fft (cuFFT) FP32 + unfused torch ops",
+                 "batched_over_plain": value / world / pv}
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(members[0])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "members": n_mem, "N": args.N, "rk_order": 3,
+                           "grid_point_updates_per_s": value * args.N ** 3,
+                           "l2": "inputs larger than L2 (state %.1f GB, per-pass buffers %.0f GB)" % (
+                               ens.state_bytes() / 1e9, step_bytes / 1e9),
+                           "parallelism": "replicas per GPU" if world > 1 else "single GPU",
+                           "step_hbm_roofline_frac": round(step_frac, 4),
+                           "flagged_members": flagged},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kps * args.steps,
+                "clocks": clk, "plain": plain, "passes": passes}
+        print(json.dumps(line), flush=True)
+    ens.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
