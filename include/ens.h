@@ -196,6 +196,33 @@ ens_status ens_mixture_host(int n, const double *lambdas, const uint64_t *counts
                             const ens_hist_spec *hist, const ens_weight_spec *w, ens_mixture_out *out,
                             void *stream);
 
+/* Same mixture as ens_mixture_host, for callers that cannot allocate device
+ * memory: for instance a process whose GPU memory is entirely reserved by
+ * another allocator (a framework's caching allocator that has claimed the
+ * device), or an application that budgets every device byte up front.  The
+ * paper has no counterpart; this is a deployment convenience.
+ *
+ * It allocates nothing (no cudaMalloc, cudaMallocAsync or cudaFree, no
+ * allocating library call): inputs and results pass through one fixed
+ * scratch array compiled into the library, of about 4.3 MB, which every GPU
+ * that loads the library holds until the process exits.  Limits:
+ * n <= ENS_NOALLOC_MAX_MEMBERS and ens_counts_len(hist) <=
+ * ENS_NOALLOC_MAX_COUNTS; larger requests return ENS_EINVAL with a message
+ * on stderr (use ens_mixture_host for them).
+ *
+ * The first call on a device, made while that device is current, looks up
+ * the scratch array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls on a device share the one
+ * array and it keeps the last call's contents: calls that overlap on the
+ * GPU (from several threads or streams at once) race and give wrong
+ * results.  The call synchronises `stream` before it returns, so calls made
+ * one after another from one thread do not overlap. */
+#define ENS_NOALLOC_MAX_MEMBERS 64
+#define ENS_NOALLOC_MAX_COUNTS 8192
+ens_status ens_mixture_host_noalloc(int n, const double *lambdas, const uint64_t *counts, const double *moments,
+                                    const ens_hist_spec *hist, const ens_weight_spec *w, ens_mixture_out *out,
+                                    void *stream);
+
 /* ---- state access ------------------------------------------------------ */
 
 /* Member spectral field <-> host full layout (FP64; converted from/to the

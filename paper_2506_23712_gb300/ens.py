@@ -80,6 +80,7 @@ SIGNATURES = [
     ("ens_counts_len", _i, [_P(HistSpec)]),
     ("ens_mixture", _i, [_vp, _P(WeightSpec), _P(MixtureOut)]),
     ("ens_mixture_host", _i, [_i, _vp, _vp, _vp, _P(HistSpec), _P(WeightSpec), _P(MixtureOut), _vp]),
+    ("ens_mixture_host_noalloc", _i, [_i, _vp, _vp, _vp, _P(HistSpec), _P(WeightSpec), _P(MixtureOut), _vp]),
     ("ens_get_field", _i, [_vp, _i, _vp]),
     ("ens_set_field", _i, [_vp, _i, _vp]),
     ("ens_state_bytes", _sz, [_vp]),
@@ -221,6 +222,28 @@ def ens_mixture_host(lambdas, counts, moments, hist, stream_ptr=None, **weights)
         stream_ptr = _stream_ptr()
     _check(lib().ens_mixture_host(n, _ptr(lam), _ptr(counts), _ptr(moments), ctypes.byref(hist),
                                   ctypes.byref(ws), ctypes.byref(out), stream_ptr))
+    return _mixture_result(out, bufs, hist)
+
+
+ENS_NOALLOC_MAX_MEMBERS = 64
+ENS_NOALLOC_MAX_COUNTS = 8192
+
+
+def ens_mixture_host_noalloc(lambdas, counts, moments, hist, stream_ptr=None, **weights):
+    """ens_mixture_host without device allocation (fixed library scratch);
+    for callers that cannot allocate device memory.  Raises EnsError with
+    ENS_EINVAL beyond ENS_NOALLOC_MAX_MEMBERS members or
+    ENS_NOALLOC_MAX_COUNTS counts per member."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    moments = np.ascontiguousarray(moments, dtype=np.float64)
+    n = lam.size
+    ws, keep = _weight_spec(**weights)
+    out, bufs = _mixture_out(n, hist)
+    if stream_ptr is None:
+        stream_ptr = _stream_ptr()
+    _check(lib().ens_mixture_host_noalloc(n, _ptr(lam), _ptr(counts), _ptr(moments), ctypes.byref(hist),
+                                          ctypes.byref(ws), ctypes.byref(out), stream_ptr))
     return _mixture_result(out, bufs, hist)
 
 
