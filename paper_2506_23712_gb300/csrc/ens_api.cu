@@ -300,6 +300,9 @@ static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, co
         x.eps_inj = std::exp(d.lambda) * d.eps_bar;
         x.klo2 = d.k_lo * d.k_lo;
         x.khi2 = d.k_hi * d.k_hi;
+        // |k|^2 is an integer: k_lo <= |k| <= k_hi (1e-9 slack) as integer bounds
+        x.band_lo2 = (int)std::ceil(x.klo2 - 1e-9);
+        x.band_hi2 = (int)std::floor(x.khi2 + 1e-9);
         x.dt_fixed = d.dt > 0.0 ? d.dt : 0.0;
         x.cfl = d.cfl;
         x.dt_max = d.dt_max;
@@ -343,6 +346,8 @@ static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, co
                  h->tail_bins, h->q_lim, h->r_lim, h->tail_lo, h->tail_hi, st);
     for (auto &gr : ctx->groups) {
         ENS_CUDA(ctx, prepare_kernels(gr.geo.N, h->qr_bins, h->tail_bins));
+        gr.geo.z_ctas = znl_ctas(gr.geo.N);
+        if (gr.geo.z_ctas <= 0) return fail(ctx, ENS_ECUDA, "occupancy query of the z pass failed");
         launch_twiddles(const_cast<float2 *>(gr.geo.tw), gr.geo.N, st);
         ENS_CUDA(ctx, cudaMemsetAsync(gr.geo.U, 0, sizeof(float2) * 3 * gr.geo.sU * gr.geo.members, st));
         ENS_CUDA(ctx, cudaMemsetAsync(gr.geo.S, 0, sizeof(float2) * 3 * gr.geo.sU * gr.geo.members, st));
@@ -830,6 +835,7 @@ ens_status ens_diagnostics(ens_ctx *ctx, ens_diag *out)
         o.reserved = 0;
         if ((d.flags & kFlagNonFinite) && flag == ENS_OK) flag = ENS_ENONFINITE;
         if ((d.flags & kFlagNoBandEnergy) && flag == ENS_OK) flag = ENS_ESTATE;
+        if ((d.flags & kFlagTimeout) && flag == ENS_OK) flag = ENS_ETIMEOUT;
     }
     return flag;
 }

@@ -265,4 +265,77 @@ __device__ __forceinline__ void fft_line(float2 *v, int p, const float2 *__restr
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-local lines: a line lives inside one warp (P <= 32 threads, 32/P
+// lines per warp), so the pass exchanges need only __syncwarp and warps run
+// independently of each other.  Used by the contiguous-axis (z) passes.
+// ---------------------------------------------------------------------------
+template <int N>
+struct WPlan;
+template <> struct WPlan<16>  { static constexpr int P = 4,  NP = 2, R0 = 4,  R1 = 4, R2 = 1, R3 = 1; };
+template <> struct WPlan<32>  { static constexpr int P = 8,  NP = 3, R0 = 4,  R1 = 2, R2 = 4, R3 = 1; };
+template <> struct WPlan<64>  { static constexpr int P = 8,  NP = 2, R0 = 8,  R1 = 8, R2 = 1, R3 = 1; };
+template <> struct WPlan<128> { static constexpr int P = 16, NP = 3, R0 = 8,  R1 = 2, R2 = 8, R3 = 1; };
+template <> struct WPlan<256> { static constexpr int P = 32, NP = 3, R0 = 8,  R1 = 4, R2 = 8, R3 = 1; };
+template <> struct WPlan<384> { static constexpr int P = 32, NP = 4, R0 = 4,  R1 = 4, R2 = 6, R3 = 4; };
+template <> struct WPlan<512> { static constexpr int P = 32, NP = 3, R0 = 16, R1 = 2, R2 = 16, R3 = 1; };
+
+template <int N>
+struct WPlanInfo {
+    using PL = WPlan<N>;
+    static constexpr int P = PL::P;
+    static constexpr int V = N / P;
+    static constexpr int NP = PL::NP;
+    static constexpr int R0 = PL::R0, R1 = PL::R1, R2 = PL::R2, R3 = PL::R3;
+    static constexpr int RL = NP == 2 ? R1 : (NP == 3 ? R2 : R3);
+    static constexpr bool matched = (R0 == RL);
+    static_assert(R0 * R1 * R2 * R3 == N, "plan must factor N");
+    static_assert(32 % P == 0, "a line must fit in one warp");
+    static_assert(V % R0 == 0 && V % R1 == 0 && V % R2 == 0 && V % R3 == 0, "radix must divide V");
+    static __device__ __forceinline__ int in_pos(int p, int i) { return p + (i / R0) * P + (i % R0) * (N / R0); }
+    static __device__ __forceinline__ int out_pos(int p, int i) { return p + (i / RL) * P + (i % RL) * (N / RL); }
+};
+
+template <int N, int R, int Ns, int Rn, int P, class At>
+__device__ __forceinline__ void exchange_warp(float2 *v, int p, At at)
+{
+    constexpr int B = N / (R * P);
+    constexpr int Bn = N / (Rn * P);
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = p + b * P;
+        const int base = (j / Ns) * Ns * R + (j % Ns);
+#pragma unroll
+        for (int t = 0; t < R; ++t) *at(base + t * Ns) = v[b * R + t];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < Bn; ++b) {
+        const int j = p + b * P;
+#pragma unroll
+        for (int t = 0; t < Rn; ++t) v[b * Rn + t] = *at(j + t * (N / Rn));
+    }
+}
+
+// Warp-local line transform; all 32 lanes of the warp must call it.
+template <int N, bool FWD, class At>
+__device__ __forceinline__ void fft_line_warp(float2 *v, int p, const float2 *__restrict__ tw, At at)
+{
+    using PI = WPlanInfo<N>;
+    constexpr int P = PI::P;
+    constexpr int R0 = PI::R0, R1 = PI::R1, R2 = PI::R2, R3 = PI::R3;
+    pass_regs<N, R0, 1, P, FWD>(v, p, tw);
+    exchange_warp<N, R0, 1, R1, P>(v, p, at);
+    pass_regs<N, R1, R0, P, FWD>(v, p, tw);
+    if constexpr (PI::NP >= 3) {
+        exchange_warp<N, R1, R0, R2, P>(v, p, at);
+        pass_regs<N, R2, R0 * R1, P, FWD>(v, p, tw);
+    }
+    if constexpr (PI::NP >= 4) {
+        exchange_warp<N, R2, R0 * R1, R3, P>(v, p, at);
+        pass_regs<N, R3, R0 * R1 * R2, P, FWD>(v, p, tw);
+    }
+}
+
 }  // namespace ens

@@ -21,6 +21,7 @@ struct MemberDev {
     unsigned long long seed;     // initial-field seed
     double init_energy;
     int nblk;                    // CTAs writing FP64 partial sums for this member
+    int band_lo2, band_hi2;      // forcing band as integer bounds on |k|^2
     int pad0;
     // run state
     double t, dt, E, diss, EB, alpha, P, umax;
@@ -30,7 +31,7 @@ struct MemberDev {
     int pad;
 };
 
-enum : int { kFlagNonFinite = 1, kFlagNoBandEnergy = 2 };
+enum : int { kFlagNonFinite = 1, kFlagNoBandEnergy = 2, kFlagTimeout = 4 };
 
 // Geometry of one group of members sharing a grid size N.
 //   state  U, S : [member][3][NK][NK][NZp]     (kx, ky, kz; compact dealiased)
@@ -52,6 +53,7 @@ struct Geo {
     unsigned long long *counts;  // statistics counts [member][counts_len]
     double *mom_partial;         // per-CTA moment partials [member][blocks][kNMom]
     int mom_blocks;
+    int z_ctas;                  // persistent CTAs of the z-direction nonlinear pass
 };
 
 struct HistDev {

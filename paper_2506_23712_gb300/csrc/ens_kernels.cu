@@ -2,6 +2,7 @@
 // and the per-N launch dispatch of the templated passes.
 #include "ens_launch.h"
 #include "ens_stats.cuh"
+#include "ens_znl.cuh"
 
 #include <cmath>
 
@@ -33,7 +34,7 @@ __global__ void k_state_sums(Geo g, MemberDev *md)
                 }
                 se += 0.5f * wgt * a2;
                 sd += (float)d.nu * (float)k2i * wgt * a2;
-                if ((double)k2i >= d.klo2 - 1e-9 && (double)k2i <= d.khi2 + 1e-9) sb += 0.5f * wgt * a2;
+                if (k2i >= d.band_lo2 && k2i <= d.band_hi2) sb += 0.5f * wgt * a2;
             }
         }
     }
@@ -296,20 +297,34 @@ static cudaError_t prepare_n(int nq, int nt)
 {
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    chk(allow_smem(k_inv_x<N, 0>, smem_cols<N>()));
-    chk(allow_smem(k_inv_x<N, 1>, smem_cols<N>()));
+    chk(allow_smem(k_inv_x<N, 0>, smem_x<N>()));
+    chk(allow_smem(k_inv_x<N, 1>, smem_x<N>()));
     chk(allow_smem(k_inv_y<N>, smem_cols<N>()));
     chk(allow_smem(k_fwd_y<N>, smem_cols<N>()));
-    chk(allow_smem(k_fwd_x<N, 0>, smem_cols<N>()));
-    chk(allow_smem(k_fwd_x<N, 1>, smem_cols<N>()));
-    chk(allow_smem(k_fwd_x<N, 2>, smem_cols<N>()));
-    chk(allow_smem(k_fwd_x<N, 3>, smem_cols<N>()));
+    chk(allow_smem(k_fwd_x<N, 0>, smem_x<N>()));
+    chk(allow_smem(k_fwd_x<N, 1>, smem_x<N>()));
+    chk(allow_smem(k_fwd_x<N, 2>, smem_x<N>()));
+    chk(allow_smem(k_fwd_x<N, 3>, smem_x<N>()));
     chk(allow_smem(k_z<N, 0>, smem_rows<N>()));
     chk(allow_smem(k_z<N, 1>, smem_rows<N>()));
     chk(allow_smem(k_z<N, 3>, smem_rows<N>()));
     chk(allow_smem(k_z<N, 4>, smem_rows<N>()));
     chk(allow_smem(k_z_stats<N>, smem_stats<N>(nq, nt)));
+    chk(allow_smem(k_znl<N>, ZCfg<N>::smem_bytes()));
     return e;
+}
+
+// persistent grid of the z nonlinear pass: resident CTAs per SM x SMs
+template <int N>
+static int znl_ctas_n()
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_znl<N>, 256, ZCfg<N>::smem_bytes()) !=
+        cudaSuccess)
+        return 0;
+    return std::max(1, per_sm) * sms;
 }
 
 template <int N>
@@ -319,13 +334,14 @@ static void launch_n(Pass pass, int mode, const Geo &g, MemberDev *md, const His
     constexpr int P = PlanInfo<N>::P;
     constexpr int TC = kTile * P;
     constexpr int RZ = RowCfg<N>::RZ;
+    constexpr int TZ = RZ * RowCfg<N>::P;   // 256 threads, warp-local rows
     const int col_tiles_state = g.NK * g.NZp / kTile;
     const int col_tiles_mid = N * g.NZp / kTile;
     switch (pass) {
     case Pass::IX: {
         dim3 grid(col_tiles_state, g.members);
-        if (mode == 0) k_inv_x<N, 0><<<grid, TC, smem_cols<N>(), s>>>(g, arg);
-        else k_inv_x<N, 1><<<grid, TC, smem_cols<N>(), s>>>(g, arg);
+        if (mode == 0) k_inv_x<N, 0><<<grid, TC, smem_x<N>(), s>>>(g, arg);
+        else k_inv_x<N, 1><<<grid, TC, smem_x<N>(), s>>>(g, arg);
         break;
     }
     case Pass::IY: {
@@ -337,10 +353,10 @@ static void launch_n(Pass pass, int mode, const Geo &g, MemberDev *md, const His
     case Pass::Z: {
         dim3 grid(N * N / RZ, g.members);
         switch (mode) {
-        case 0: k_z<N, 0><<<grid, RZ * P, smem_rows<N>(), s>>>(g, md, stage); break;
-        case 1: k_z<N, 1><<<grid, RZ * P, smem_rows<N>(), s>>>(g, md, stage); break;
-        case 3: k_z<N, 3><<<grid, RZ * P, smem_rows<N>(), s>>>(g, md, stage); break;
-        default: k_z<N, 4><<<grid, RZ * P, smem_rows<N>(), s>>>(g, md, stage); break;
+        case 0: k_znl<N><<<g.z_ctas, 256, ZCfg<N>::smem_bytes(), s>>>(g, md, stage); break;
+        case 1: k_z<N, 1><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
+        case 3: k_z<N, 3><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
+        default: k_z<N, 4><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
         }
         break;
     }
@@ -352,17 +368,17 @@ static void launch_n(Pass pass, int mode, const Geo &g, MemberDev *md, const His
     case Pass::FX: {
         dim3 grid(col_tiles_state, g.members);
         switch (mode) {
-        case 0: k_fwd_x<N, 0><<<grid, TC, smem_cols<N>(), s>>>(g, md, stage, last); break;
-        case 1: k_fwd_x<N, 1><<<grid, TC, smem_cols<N>(), s>>>(g, md, stage, last); break;
-        case 2: k_fwd_x<N, 2><<<grid, TC, smem_cols<N>(), s>>>(g, md, stage, last); break;
-        default: k_fwd_x<N, 3><<<grid, TC, smem_cols<N>(), s>>>(g, md, stage, last); break;
+        case 0: k_fwd_x<N, 0><<<grid, TC, smem_x<N>(), s>>>(g, md, stage, last); break;
+        case 1: k_fwd_x<N, 1><<<grid, TC, smem_x<N>(), s>>>(g, md, stage, last); break;
+        case 2: k_fwd_x<N, 2><<<grid, TC, smem_x<N>(), s>>>(g, md, stage, last); break;
+        default: k_fwd_x<N, 3><<<grid, TC, smem_x<N>(), s>>>(g, md, stage, last); break;
         }
         break;
     }
     case Pass::ZSTAT: {
         const long long rows = (long long)N * N;
         dim3 grid((unsigned)((rows + (long long)RZ * kStatsIters - 1) / ((long long)RZ * kStatsIters)), g.members);
-        k_z_stats<N><<<grid, RZ * P, smem_stats<N>(h->nq, h->nt), s>>>(g, *h, md);
+        k_z_stats<N><<<grid, TZ, smem_stats<N>(h->nq, h->nt), s>>>(g, *h, md);
         break;
     }
     }
@@ -389,6 +405,14 @@ int plan_threads(int N)
 int stats_blocks(int N)
 {
 #define X(n) if (N == n) return (int)(((long long)n * n + (long long)RowCfg<n>::RZ * kStatsIters - 1) / ((long long)RowCfg<n>::RZ * kStatsIters));
+    ENS_SUPPORTED_N(X)
+#undef X
+    return 0;
+}
+
+int znl_ctas(int N)
+{
+#define X(n) if (N == n) return znl_ctas_n<n>();
     ENS_SUPPORTED_N(X)
 #undef X
     return 0;

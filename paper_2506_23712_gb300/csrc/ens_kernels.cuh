@@ -28,8 +28,8 @@ namespace ens {
 // rows handled per CTA by the z-direction passes
 template <int N>
 struct RowCfg {
-    static constexpr int P = PlanInfo<N>::P;
-    static constexpr int RZ = 256 / P;
+    static constexpr int P = WPlanInfo<N>::P;     // threads per row (warp-local lines)
+    static constexpr int RZ = 256 / P;            // rows per 256-thread CTA
     static constexpr int SROW = N + N / 16 + 1;   // padded shared row stride (float2)
 };
 
@@ -38,6 +38,10 @@ __host__ __device__ constexpr int threads_cols(int P) { return kTile * P; }
 // Launch helpers (host): shared memory bytes per pass.
 template <int N>
 constexpr size_t smem_cols() { return sizeof(float2) * (size_t)(N + N * kTile); }
+__host__ __device__ constexpr int kc_of_n(int N) { return (N + 2) / 3 - 1; }
+// x passes also stage the three components of a column tile: [3][NK][kTile]
+template <int N>
+constexpr size_t smem_x() { return smem_cols<N>() + sizeof(float2) * 3 * (2 * kc_of_n(N) + 1) * kTile; }
 template <int N>
 constexpr size_t smem_rows() { return sizeof(float2) * (size_t)(N + RowCfg<N>::RZ * RowCfg<N>::SROW); }
 
@@ -56,36 +60,48 @@ __device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restri
 // grid (NK*NZp/kTile, members), block kTile*P.
 // ---------------------------------------------------------------------------
 template <int N, int MODE>
-__global__ void __launch_bounds__(kTile * PlanInfo<N>::P)
+__global__ void __launch_bounds__(kTile * PlanInfo<N>::P, 256 / (kTile * PlanInfo<N>::P) > 0 ? 2 : 1)
 k_inv_x(Geo g, int use_S)
 {
     using PI = PlanInfo<N>;
     constexpr int P = PI::P, V = PI::V;
     constexpr int NF = MODE == 0 ? 6 : 8;
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *buf = sm + N;
-    load_twiddles(tw, g.tw, N);
+    float2 *tw = sm, *buf = sm + N, *tile = buf + N * kTile;   // tile: [3][NK][kTile]
 
     const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
     const int m = blockIdx.y;
-    const int col = blockIdx.x * kTile + c;
+    const int col0 = blockIdx.x * kTile;                    // a tile never straddles ky (NZp % kTile == 0)
+    const int col = col0 + c;
     const int iy = col / g.NZp, kz = col % g.NZp;
     const bool valid = kz < g.NZ;
     const float ky = (float)(iy <= g.kc ? iy : iy - g.NK);
     const float kzf = (float)kz;
     const long long rowU = (long long)g.NK * g.NZp;
-    const float2 *X = (use_S ? g.S : g.U) + (long long)m * 3 * g.sU + col;
-
-    float2 u0[V], u1[V], u2[V];
+    const float2 *X = (use_S ? g.S : g.U) + (long long)m * 3 * g.sU + col0;
+    // coalesced staging of the three velocity components of this column tile
+    const int per = g.NK * kTile;
+    constexpr int kBatch = 8;   // loads in flight per thread before the shared stores
+    for (int base = threadIdx.x; base < 3 * per; base += kBatch * blockDim.x) {
+        float2 tmp[kBatch];
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-        const int kx = wnum(PI::in_pos(p, i), N);
-        const bool keep = valid && kx >= -g.kc && kx <= g.kc;
-        const long long ix = kx >= 0 ? kx : kx + g.NK;
-        u0[i] = keep ? X[ix * rowU] : make_float2(0.f, 0.f);
-        u1[i] = keep ? X[g.sU + ix * rowU] : make_float2(0.f, 0.f);
-        u2[i] = keep ? X[2 * g.sU + ix * rowU] : make_float2(0.f, 0.f);
+        for (int k = 0; k < kBatch; ++k) {
+            const int idx = base + k * blockDim.x;
+            tmp[k] = make_float2(0.f, 0.f);
+            if (idx < 3 * per) {
+                const int q = idx / per, rem = idx % per;
+                const int ix = rem / kTile, cc = rem % kTile;
+                if (((col0 + cc) % g.NZp) < g.NZ) tmp[k] = X[q * g.sU + ix * rowU + cc];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int idx = base + k * blockDim.x;
+            if (idx < 3 * per) tile[idx] = tmp[k];
+        }
     }
+    load_twiddles(tw, g.tw, N);   // block barrier: tile complete
+
     float2 *dst0 = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
     auto at = [&](int pos) { return &buf[pos * kTile + c]; };
 #pragma unroll 1
@@ -93,13 +109,17 @@ k_inv_x(Geo g, int use_S)
         float2 v[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            const float kx = (float)wnum(PI::in_pos(p, i), N);
-            const float2 a = u0[i], b = u1[i], d = u2[i];
-            // component selection without dynamic register indexing
-            const float2 ui = f % 3 == 0 ? a : (f % 3 == 1 ? b : d);
+            const int kxi = wnum(PI::in_pos(p, i), N);
+            const bool keep = kxi >= -g.kc && kxi <= g.kc;
+            const int ix = kxi >= 0 ? kxi : kxi + g.NK;
+            const float kx = (float)kxi;
+            const float2 z = make_float2(0.f, 0.f);
+            const float2 a = keep ? tile[ix * kTile + c] : z;
+            const float2 b = keep ? tile[per + ix * kTile + c] : z;
+            const float2 d = keep ? tile[2 * per + ix * kTile + c] : z;
             if (MODE == 0) {
                 if (f < 3) {
-                    v[i] = ui;
+                    v[i] = f == 0 ? a : (f == 1 ? b : d);
                 } else {
                     // omega = i k x u: (k x u)_x = ky uz - kz uy, _y = kz ux - kx uz, _z = kx uy - ky ux
                     float2 cr;
@@ -229,14 +249,14 @@ template <int N>
 __device__ __forceinline__ void forward_pair_store(float2 *v, int p, int r, const float2 *tw, float2 *buf,
                                                    float2 *dstA, float2 *dstB, int NZ, bool row_ok)
 {
-    using PI = PlanInfo<N>;
+    using PI = WPlanInfo<N>;
     constexpr int V = PI::V, P = PI::P;
     auto at = [&](int pos) { return row_slot<N>(buf, r, pos); };
-    fft_line<N, true>(v, p, tw, at);
-    __syncthreads();
+    fft_line_warp<N, true>(v, p, tw, at);
+    __syncwarp();
 #pragma unroll
     for (int i = 0; i < V; ++i) *at(PI::out_pos(p, i)) = v[i];
-    __syncthreads();
+    __syncwarp();
     if (row_ok) {
         for (int k = p; k < NZ; k += P) {
             const float2 z = *at(k);
@@ -269,10 +289,10 @@ __device__ __forceinline__ float white_noise(uint64_t seed, uint64_t counter)
 }
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_z(Geo g, MemberDev *md, int stage)
 {
-    using PI = PlanInfo<N>;
+    using PI = WPlanInfo<N>;
     using RC = RowCfg<N>;
     constexpr int P = PI::P, V = PI::V, RZ = RC::RZ;
     extern __shared__ float2 sm[];
@@ -288,17 +308,20 @@ k_z(Geo g, MemberDev *md, int stage)
     float2 w0[V], w1[V];   // forward inputs in first-pass order
     if constexpr (MODE == 0 || MODE == 3) {
         float2 a[V], b[V], cc[V];
+        // all loads first (memory-level parallelism), then the transforms
 #pragma unroll
         for (int i = 0; i < V; ++i) a[i] = pair_at(B, B + g.sB, PI::in_pos(p, i), N, g.kc);
-        fft_line<N, false>(a, p, tw, at);
         if constexpr (MODE == 3) {
 #pragma unroll
             for (int i = 0; i < V; ++i) b[i] = pair_at(B + 2 * g.sB, B + 2 * g.sB, PI::in_pos(p, i), N, g.kc);
         } else {
 #pragma unroll
             for (int i = 0; i < V; ++i) b[i] = pair_at(B + 2 * g.sB, B + 3 * g.sB, PI::in_pos(p, i), N, g.kc);
+#pragma unroll
+            for (int i = 0; i < V; ++i) cc[i] = pair_at(B + 4 * g.sB, B + 5 * g.sB, PI::in_pos(p, i), N, g.kc);
         }
-        fft_line<N, false>(b, p, tw, at);
+        fft_line_warp<N, false>(a, p, tw, at);
+        fft_line_warp<N, false>(b, p, tw, at);
         if constexpr (MODE == 3) {
             // physical u_c(x, y, z) into A viewed as floats [member][3][x][y][z]
             float *out = reinterpret_cast<float *>(g.A + (long long)m * kFields * g.sA);
@@ -313,9 +336,7 @@ k_z(Geo g, MemberDev *md, int stage)
             }
             return;
         } else {
-#pragma unroll
-            for (int i = 0; i < V; ++i) cc[i] = pair_at(B + 4 * g.sB, B + 5 * g.sB, PI::in_pos(p, i), N, g.kc);
-            fft_line<N, false>(cc, p, tw, at);
+            fft_line_warp<N, false>(cc, p, tw, at);
             // a = ux + i uy, b = uz + i wx, cc = wy + i wz at positions out_pos
             float umax = 0.f;
             bool finite = true;
@@ -338,16 +359,16 @@ k_z(Geo g, MemberDev *md, int stage)
             }
             if constexpr (!PI::matched) {
                 // reorder from last-pass positions to first-pass positions
-                __syncthreads();
+                __syncwarp();
 #pragma unroll
                 for (int i = 0; i < V; ++i) *at(PI::out_pos(p, i)) = w0[i];
-                __syncthreads();
+                __syncwarp();
 #pragma unroll
                 for (int i = 0; i < V; ++i) w0[i] = *at(PI::in_pos(p, i));
-                __syncthreads();
+                __syncwarp();
 #pragma unroll
                 for (int i = 0; i < V; ++i) *at(PI::out_pos(p, i)) = w1[i];
-                __syncthreads();
+                __syncwarp();
 #pragma unroll
                 for (int i = 0; i < V; ++i) w1[i] = *at(PI::in_pos(p, i));
             }
@@ -374,7 +395,7 @@ k_z(Geo g, MemberDev *md, int stage)
         }
     }
     if constexpr (MODE == 1 || MODE == 4) {
-        __syncthreads();   // all threads reach the stores below after their loads
+        __syncwarp();   // all threads reach the stores below after their loads
     }
     forward_pair_store<N>(w0, p, r, tw, buf, B, B + g.sB, g.NZ, true);
     forward_pair_store<N>(w1, p, r, tw, buf, B + 2 * g.sB, nullptr, g.NZ, true);
@@ -438,62 +459,73 @@ __device__ __forceinline__ void block_sum_to(double *out, double (&vals)[NW], do
 }
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(kTile * PlanInfo<N>::P)
+__global__ void __launch_bounds__(kTile * PlanInfo<N>::P, 256 / (kTile * PlanInfo<N>::P) > 0 ? 2 : 1)
 k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
 {
     using PI = PlanInfo<N>;
     constexpr int P = PI::P, V = PI::V;
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *buf = sm + N;
+    float2 *tw = sm, *buf = sm + N, *tile = buf + N * kTile;   // tile: [3][NK][kTile]
     load_twiddles(tw, g.tw, N);
     const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
     const int m = blockIdx.y;
-    const int col = blockIdx.x * kTile + c;   // (ky, kz) flat
+    const int col0 = blockIdx.x * kTile;
+    const int col = col0 + c;                                  // (ky, kz) flat
     const int iy = col / g.NZp, kz = col % g.NZp;
     const bool valid = kz < g.NZ;
-    const int kyi = iy <= g.kc ? iy : iy - g.NK;
+    const int per = g.NK * kTile;
     const float2 *Ain = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
     auto at = [&](int pos) { return &buf[pos * kTile + c]; };
-    float2 X[3][V];
-#pragma unroll
+    // forward transforms of the three components; kept rows to the tile
+#pragma unroll 1
     for (int q = 0; q < 3; ++q) {
+        float2 v[V];
 #pragma unroll
         for (int i = 0; i < V; ++i)
-            X[q][i] = valid ? Ain[(long long)q * g.sA + (long long)PI::in_pos(p, i) * g.NZp] : make_float2(0.f, 0.f);
-        fft_line<N, true>(X[q], p, tw, at);
+            v[i] = valid ? Ain[(long long)q * g.sA + (long long)PI::in_pos(p, i) * g.NZp] : make_float2(0.f, 0.f);
+        fft_line<N, true>(v, p, tw, at);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const int kx = wnum(PI::out_pos(p, i), N);
+            if (kx >= -g.kc && kx <= g.kc) tile[q * per + (kx >= 0 ? kx : kx + g.NK) * kTile + c] = v[i];
+        }
     }
+    __syncthreads();
+
     const MemberDev &d = md[g.first + m];
     const float inv_n3 = 1.0f / ((float)N * (float)N * (float)N);
     const long long rowU = (long long)g.NK * g.NZp;
-    float2 *U = g.U + (long long)m * 3 * g.sU + col;
-    float2 *S = g.S + (long long)m * 3 * g.sU + col;
-    const float wgt = kz == 0 ? 1.f : 2.f;   // Hermitian multiplicity in the full spectrum
+    float2 *U = g.U + (long long)m * 3 * g.sU + col0;
+    float2 *S = g.S + (long long)m * 3 * g.sU + col0;
+    const int kyi = iy <= g.kc ? iy : iy - g.NK;
     float se = 0.f, sd = 0.f, sb = 0.f;
-    double dt = 0.0;
-    float alpha = 0.f, nu = 0.f;
+    float dtf = 0.f, alpha = 0.f, nu = 0.f;
     StageCoef co{};
     if constexpr (MODE == 0 || MODE == 1) {
-        dt = member_dt(d, N);
+        dtf = (float)member_dt(d, N);
         alpha = (float)d.alpha;
         nu = (float)d.nu;
         co = stage_coef(d.rk, stage);
     }
-    double *shell_smem = reinterpret_cast<double *>(buf);   // reused after the FFTs (MODE 2)
+    const int blo = d.band_lo2, bhi = d.band_hi2;
+    double *shell_smem = reinterpret_cast<double *>(buf);   // exchange buffer is free now (MODE 2)
     if constexpr (MODE == 2) {
-        __syncthreads();
         for (int s = threadIdx.x; s < g.shells; s += blockDim.x) shell_smem[s] = 0.0;
         __syncthreads();
     }
-#pragma unroll
-    for (int i = 0; i < V; ++i) {
-        const int kx = wnum(PI::out_pos(p, i), N);
-        if (!valid || kx < -g.kc || kx > g.kc) continue;
-        const int ix = kx >= 0 ? kx : kx + g.NK;
-        const long long off = ix * rowU;
-        const float fk[3] = {(float)kx, (float)kyi, (float)kz};
-        const int k2i = kx * kx + kyi * kyi + kz * kz;
+    // per kept mode of the tile: thread <-> (kx row, column), coalesced in the column
+    for (int idx = threadIdx.x; idx < per; idx += blockDim.x) {
+        const int ix = idx / kTile, cc = idx % kTile;
+        const int kzc = (col0 + cc) % g.NZp;
+        if (kzc >= g.NZ) continue;
+        const int kx = ix <= g.kc ? ix : ix - g.NK;
+        const float fk[3] = {(float)kx, (float)kyi, (float)kzc};
+        const int k2i = kx * kx + kyi * kyi + kzc * kzc;
         const float k2 = (float)k2i;
-        float2 n[3] = {cscale(X[0][i], inv_n3), cscale(X[1][i], inv_n3), cscale(X[2][i], inv_n3)};
+        const long long off = ix * rowU + cc;
+        float2 n[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) n[q] = cscale(tile[q * per + idx], inv_n3);
         if (MODE != 3) {
             // Leray projection P_ij = delta_ij - k_i k_j / k^2; k = 0 held at zero
             if (k2i == 0) {
@@ -506,19 +538,19 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
                 for (int q = 0; q < 3; ++q) n[q] = make_float2(n[q].x - fk[q] * dr, n[q].y - fk[q] * di);
             }
         }
+        const float wgt = kzc == 0 ? 1.f : 2.f;   // Hermitian multiplicity in the full spectrum
         if constexpr (MODE == 2 || MODE == 3) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) U[q * g.sU + off] = n[q];
             if constexpr (MODE == 2) {
-                const int s = (int)lrint(sqrt((double)k2i));
+                const int s = (int)lrintf(sqrtf(k2));
                 float a2 = 0.f;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) a2 += n[q].x * n[q].x + n[q].y * n[q].y;
                 atomicAdd(&shell_smem[s], 0.5 * (double)(wgt * a2));
             }
-            continue;
         } else {
-            const bool band = (double)k2i >= d.klo2 - 1e-9 && (double)k2i <= d.khi2 + 1e-9;
+            const bool band = k2i >= blo && k2i <= bhi;
             float2 us[3], un[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -529,9 +561,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
             if constexpr (MODE == 1) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) S[q * g.sU + off] = n[q];
-                continue;
             } else {
-                const float dtf = (float)dt;
                 const float ea = co.a != 0.f ? expf(-nu * k2 * co.ha * dtf) : 0.f;
                 const float eb = expf(-nu * k2 * co.hb * dtf);
                 float2 *dst = last_stage ? U : S;

@@ -26,6 +26,7 @@ bool supported_n(int N);
 int plan_threads(int N);
 int stats_blocks(int N);
 cudaError_t prepare_kernels(int N, int nq, int nt);
+int znl_ctas(int N);   // persistent grid of the z nonlinear pass (0 on error)
 
 // mode/arg per pass:
 //   IX: mode 0 (u, omega) or 1 (gradient), arg = read S instead of U

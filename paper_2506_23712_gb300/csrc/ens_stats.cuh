@@ -65,10 +65,10 @@ constexpr size_t smem_stats(int nq, int nt)
 }
 
 template <int N>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_z_stats(Geo g, HistDev h, const MemberDev *md)
 {
-    using PI = PlanInfo<N>;
+    using PI = WPlanInfo<N>;
     using RC = RowCfg<N>;
     constexpr int P = PI::P, V = PI::V, RZ = RC::RZ;
     extern __shared__ float2 sm[];
@@ -114,7 +114,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
             for (int i = 0; i < V; ++i)
                 v[q][i] = row_ok ? pair_at(B + (2 * q) * g.sB, B + (2 * q + 1) * g.sB, PI::in_pos(p, i), N, g.kc)
                                  : make_float2(0.f, 0.f);
-            fft_line<N, false>(v[q], p, tw, at);
+            fft_line_warp<N, false>(v[q], p, tw, at);
         }
         float sQ = 0.f, sR = 0.f, sE = 0.f, sW = 0.f, sQ2 = 0.f, sR2 = 0.f, sE2 = 0.f, sW2 = 0.f;
 #pragma unroll

@@ -1,0 +1,152 @@
+// ZNL: the z-direction pass of an RK stage, persistent and TMA-fed.
+//
+// Per (y, x) row of a member: the six half spectra (u, omega) along z are
+// taken to physical space as three complex lines (two real rows per complex
+// line, Hermitian extension), the rotational nonlinear term n = u x omega is
+// formed point by point together with max|u_i| (CFL step, Sec. IV) and a
+// non-finite check, and n goes straight back along z; the dealiased half
+// spectra of n overwrite fields 0..2 of the row in buffer B.
+//
+// Each warp owns a stream of row groups (32/P rows per group, P threads per
+// row) and double-buffers their inputs in shared memory: one lane issues
+// six 1D bulk copies (cp.async.bulk, TMA) per row into the idle buffer,
+// completion counted on that buffer's mbarrier, while the whole warp
+// transforms the other buffer.  Waits are bounded; a wait that gives up
+// flags the member (ENS_ETIMEOUT) and the warp stops.
+#pragma once
+
+#include "ens_kernels.cuh"
+#include "ens_tma.cuh"
+
+namespace ens {
+
+template <int N>
+struct ZCfg {
+    using PI = WPlanInfo<N>;
+    static constexpr int P = PI::P, V = PI::V, LPW = 32 / P;
+    static constexpr int WPB = 8;                          // warps per CTA
+    static constexpr int NZ = kc_of_n(N) + 1;
+    static constexpr int NZ2 = (NZ + 1) / 2 * 2;           // copied row length (16-byte multiple)
+    static constexpr int STAGE = LPW * 6 * NZ2;            // float2 per warp buffer
+    static constexpr int SROW = RowCfg<N>::SROW;
+    static constexpr size_t smem_bytes()
+    {
+        return sizeof(float2) * (size_t)N + sizeof(uint64_t) * 2 * WPB + sizeof(float2) * (size_t)WPB * 2 * STAGE +
+               sizeof(float2) * (size_t)WPB * LPW * SROW;
+    }
+};
+
+template <int N>
+__global__ void __launch_bounds__(256, ZCfg<N>::smem_bytes() <= 110 * 1024 ? 2 : 1)
+k_znl(Geo g, MemberDev *md, int stage_idx)
+{
+    using C = ZCfg<N>;
+    using PI = WPlanInfo<N>;
+    constexpr int P = C::P, V = C::V, LPW = C::LPW, NZ2 = C::NZ2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *tw = reinterpret_cast<float2 *>(smraw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tw + N);
+    float2 *stage = reinterpret_cast<float2 *>(bars + 2 * C::WPB);
+    float2 *rows = stage + C::WPB * 2 * C::STAGE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int line = lane / P, p = lane % P;
+    uint64_t *bar = bars + 2 * warp;
+    float2 *st = stage + warp * 2 * C::STAGE;
+    float2 *rowbuf = rows + warp * LPW * C::SROW;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    load_twiddles(tw, g.tw, N);   // block barrier also publishes the barrier init
+
+    const long long G = (long long)N * N / LPW;   // row groups per member
+    const long long T = G * g.members;
+    const long long W = (long long)gridDim.x * C::WPB;
+    long long grp = (long long)blockIdx.x * C::WPB + warp;
+    const uint32_t bytes = (uint32_t)(LPW * 6 * NZ2 * sizeof(float2));
+    auto issue = [&](long long gi, int b) {   // lane 0 only
+        const long long m = gi / G, lg = gi % G;
+        const float2 *src = g.B + m * kFields * g.sB + (lg * LPW) * g.NZp;
+        float2 *dst = st + b * C::STAGE;
+        mbar_arrive_expect_tx(&bar[b], bytes);
+#pragma unroll 1
+        for (int l = 0; l < LPW; ++l)
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+                bulk_g2s(dst + (l * 6 + f) * NZ2, src + f * g.sB + l * g.NZp, NZ2 * (uint32_t)sizeof(float2),
+                         &bar[b]);
+    };
+    if (lane == 0 && grp < T) issue(grp, 0);
+
+    auto at = [&](int pos) { return row_slot<N>(rowbuf, line, pos); };
+    float umax = 0.f;
+    bool finite = true;
+    long long cur_m = grp < T ? grp / G : 0;
+    auto flush = [&](long long m) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+        const unsigned bad = __ballot_sync(0xffffffffu, !finite);
+        if (lane == 0) {
+            atomicMax(&md[g.first + m].umax_bits[stage_idx], __float_as_uint(umax));
+            if (bad) atomicOr(&md[g.first + m].flags, kFlagNonFinite);
+        }
+        umax = 0.f;
+        finite = true;
+    };
+    bool timed_out = false;
+    int it = 0;
+    for (; grp < T; ++it, grp += W) {
+        const int b = it & 1;
+        const long long nxt = grp + W;
+        if (lane == 0 && nxt < T) {
+            fence_proxy_async_smem();   // this buffer's earlier reads precede the refill
+            issue(nxt, b ^ 1);
+        }
+        if (!mbar_wait_warp(&bar[b], (uint32_t)((it >> 1) & 1))) {
+            timed_out = true;
+            break;
+        }
+        const long long m = grp / G, lg = grp % G;
+        if (m != cur_m) {
+            flush(cur_m);
+            cur_m = m;
+        }
+        const long long rho = lg * LPW + line;
+        const float2 *X = st + b * C::STAGE + line * 6 * NZ2;
+        float2 a[V], bb[V], cc[V], w0[V], w1[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const int pos = PI::in_pos(p, i);
+            a[i] = pair_at(X, X + NZ2, pos, N, g.kc);
+            bb[i] = pair_at(X + 2 * NZ2, X + 3 * NZ2, pos, N, g.kc);
+            cc[i] = pair_at(X + 4 * NZ2, X + 5 * NZ2, pos, N, g.kc);
+        }
+        fft_line_warp<N, false>(a, p, tw, at);
+        fft_line_warp<N, false>(bb, p, tw, at);
+        fft_line_warp<N, false>(cc, p, tw, at);
+        // a = ux + i uy, bb = uz + i wx, cc = wy + i wz at positions out_pos
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const float ux = a[i].x, uy = a[i].y, uz = bb[i].x;
+            const float wx = bb[i].y, wy = cc[i].x, wz = cc[i].y;
+            umax = fmaxf(umax, fmaxf(fabsf(ux), fmaxf(fabsf(uy), fabsf(uz))));
+            finite = finite && isfinite(ux + uy + uz + wx + wy + wz);
+            w0[i] = make_float2(uy * wz - uz * wy, uz * wx - ux * wz);
+            w1[i] = make_float2(ux * wy - uy * wx, 0.f);
+        }
+        static_assert(PI::matched, "first and last radix must agree");
+        float2 *Bout = g.B + m * kFields * g.sB + rho * g.NZp;
+        forward_pair_store<N>(w0, p, line, tw, rowbuf, Bout, Bout + g.sB, g.NZ, true);
+        forward_pair_store<N>(w1, p, line, tw, rowbuf, Bout + 2 * g.sB, nullptr, g.NZ, true);
+        __syncwarp();   // all lanes are done with buffer b before it is refilled
+    }
+    if (grp > (long long)blockIdx.x * C::WPB + warp || timed_out) flush(cur_m);
+    if (timed_out) {
+        if (lane == 0) atomicOr(&md[g.first + cur_m].flags, kFlagTimeout);
+        // the refill of the other buffer may still be in flight: wait for it (bounded)
+        if (grp + W < T) mbar_wait_warp(&bar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+    }
+}
+
+}  // namespace ens
