@@ -318,6 +318,76 @@ __device__ __forceinline__ void exchange_warp(float2 *v, int p, At at)
     }
 }
 
+// Per-thread inter-pass twiddles of a warp-local plan, held in registers.
+// Pass s (radix R, after Ns points) multiplies slot t of butterfly b by
+// W_N^{t k N/(Ns R)}, k = (p + b P) mod Ns; the forward values are stored,
+// the inverse uses their conjugates.
+template <int N, int R, int Ns, int P>
+struct PassTw {
+    static constexpr int B = N / (R * P);
+    float2 w[B][R > 1 ? R - 1 : 1];
+    __device__ __forceinline__ void init(int p, const float2 *__restrict__ tw)
+    {
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int k = (p + b * P) % Ns;
+#pragma unroll
+            for (int t = 1; t < R; ++t) w[b][t - 1] = tw[t * k * (N / (Ns * R))];
+        }
+    }
+};
+
+template <int N, int R, int Ns, int P, bool FWD>
+__device__ __forceinline__ void pass_regs_tw(float2 *v, const PassTw<N, R, Ns, P> &T)
+{
+    constexpr int B = N / (R * P);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+#pragma unroll
+        for (int t = 1; t < R; ++t) {
+            float2 w = T.w[b][t - 1];
+            if (!FWD) w.y = -w.y;
+            v[b * R + t] = cmul(v[b * R + t], w);
+        }
+        Dft<R, FWD>::run(&v[b * R]);
+    }
+}
+
+template <int N>
+struct WarpTw {
+    using PI = WPlanInfo<N>;
+    static constexpr int P = PI::P, R0 = PI::R0, R1 = PI::R1, R2 = PI::R2, R3 = PI::R3;
+    PassTw<N, R1, R0, P> t1;
+    PassTw<N, (PI::NP >= 3 ? R2 : 2), R0 * R1, P> t2;
+    PassTw<N, (PI::NP >= 4 ? R3 : 2), R0 * R1 * R2, P> t3;
+    __device__ __forceinline__ void init(int p, const float2 *__restrict__ tw)
+    {
+        t1.init(p, tw);
+        if constexpr (PI::NP >= 3) t2.init(p, tw);
+        if constexpr (PI::NP >= 4) t3.init(p, tw);
+    }
+};
+
+// Warp-local line transform with register twiddles.
+template <int N, bool FWD, class At>
+__device__ __forceinline__ void fft_line_warp_tw(float2 *v, int p, const WarpTw<N> &T, At at)
+{
+    using PI = WPlanInfo<N>;
+    constexpr int P = PI::P;
+    constexpr int R0 = PI::R0, R1 = PI::R1, R2 = PI::R2, R3 = PI::R3;
+    pass_regs<N, R0, 1, P, FWD>(v, p, nullptr);
+    exchange_warp<N, R0, 1, R1, P>(v, p, at);
+    pass_regs_tw<N, R1, R0, P, FWD>(v, T.t1);
+    if constexpr (PI::NP >= 3) {
+        exchange_warp<N, R1, R0, R2, P>(v, p, at);
+        pass_regs_tw<N, R2, R0 * R1, P, FWD>(v, T.t2);
+    }
+    if constexpr (PI::NP >= 4) {
+        exchange_warp<N, R2, R0 * R1, R3, P>(v, p, at);
+        pass_regs_tw<N, R3, R0 * R1 * R2, P, FWD>(v, T.t3);
+    }
+}
+
 // Warp-local line transform; all 32 lanes of the warp must call it.
 template <int N, bool FWD, class At>
 __device__ __forceinline__ void fft_line_warp(float2 *v, int p, const float2 *__restrict__ tw, At at)

@@ -30,7 +30,7 @@ template <int N>
 struct RowCfg {
     static constexpr int P = WPlanInfo<N>::P;     // threads per row (warp-local lines)
     static constexpr int RZ = 256 / P;            // rows per 256-thread CTA
-    static constexpr int SROW = N + N / 16 + 1;   // padded shared row stride (float2)
+    static constexpr int SROW = N + N / 16 + N / 32 + 1;   // padded shared row stride (float2)
 };
 
 __host__ __device__ constexpr int threads_cols(int P) { return kTile * P; }
@@ -220,7 +220,9 @@ k_fwd_y(Geo g)
 template <int N>
 __device__ __forceinline__ float2 *row_slot(float2 *buf, int r, int pos)
 {
-    return &buf[r * RowCfg<N>::SROW + pos + (pos >> 4)];
+    // padding chosen (by simulating the bank mapping of the warp-local
+    // exchanges) so that the pass exchanges are close to conflict-free
+    return &buf[r * RowCfg<N>::SROW + pos + (pos >> 4) + (pos >> 5)];
 }
 
 // Hermitian-extended pair line a + i b at position pos from half spectra.

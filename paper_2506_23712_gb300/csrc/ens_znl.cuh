@@ -36,6 +36,29 @@ struct ZCfg {
     }
 };
 
+// forward transform of two real rows with register twiddles, then the half
+// spectra of both rows (kz < NZ) to dstA / dstB (dstB null: one real row)
+template <int N>
+__device__ __forceinline__ void forward_pair_store_tw(float2 *v, int p, int r, const WarpTw<N> &T, float2 *buf,
+                                                      float2 *dstA, float2 *dstB, int NZ)
+{
+    using PI = WPlanInfo<N>;
+    constexpr int V = PI::V, P = PI::P;
+    auto at = [&](int pos) { return row_slot<N>(buf, r, pos); };
+    fft_line_warp_tw<N, true>(v, p, T, at);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < V; ++i) *at(PI::out_pos(p, i)) = v[i];
+    __syncwarp();
+    for (int k = p; k < NZ; k += P) {
+        const float2 z = *at(k);
+        const float2 w = cconj(*at(k == 0 ? 0 : N - k));
+        // Xa = (Z_k + conj Z_{N-k}) / 2 ; Xb = (Z_k - conj Z_{N-k}) / (2i)
+        dstA[k] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y + w.y));
+        if (dstB) dstB[k] = make_float2(0.5f * (z.y - w.y), -0.5f * (z.x - w.x));
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(256, ZCfg<N>::smem_bytes() <= 110 * 1024 ? 2 : 1)
 k_znl(Geo g, MemberDev *md, int stage_idx)
@@ -59,6 +82,8 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         fence_mbar_init();
     }
     load_twiddles(tw, g.tw, N);   // block barrier also publishes the barrier init
+    WarpTw<N> TW;                 // this lane's inter-pass twiddles, for every row it transforms
+    TW.init(p, tw);
 
     const long long G = (long long)N * N / LPW;   // row groups per member
     const long long T = G * g.members;
@@ -122,9 +147,9 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
             bb[i] = pair_at(X + 2 * NZ2, X + 3 * NZ2, pos, N, g.kc);
             cc[i] = pair_at(X + 4 * NZ2, X + 5 * NZ2, pos, N, g.kc);
         }
-        fft_line_warp<N, false>(a, p, tw, at);
-        fft_line_warp<N, false>(bb, p, tw, at);
-        fft_line_warp<N, false>(cc, p, tw, at);
+        fft_line_warp_tw<N, false>(a, p, TW, at);
+        fft_line_warp_tw<N, false>(bb, p, TW, at);
+        fft_line_warp_tw<N, false>(cc, p, TW, at);
         // a = ux + i uy, bb = uz + i wx, cc = wy + i wz at positions out_pos
 #pragma unroll
         for (int i = 0; i < V; ++i) {
@@ -137,8 +162,8 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         }
         static_assert(PI::matched, "first and last radix must agree");
         float2 *Bout = g.B + m * kFields * g.sB + rho * g.NZp;
-        forward_pair_store<N>(w0, p, line, tw, rowbuf, Bout, Bout + g.sB, g.NZ, true);
-        forward_pair_store<N>(w1, p, line, tw, rowbuf, Bout + 2 * g.sB, nullptr, g.NZ, true);
+        forward_pair_store_tw<N>(w0, p, line, TW, rowbuf, Bout, Bout + g.sB, g.NZ);
+        forward_pair_store_tw<N>(w1, p, line, TW, rowbuf, Bout + 2 * g.sB, nullptr, g.NZ);
         __syncwarp();   // all lanes are done with buffer b before it is refilled
     }
     if (grp > (long long)blockIdx.x * C::WPB + warp || timed_out) flush(cur_m);
