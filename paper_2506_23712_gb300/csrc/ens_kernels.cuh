@@ -221,8 +221,11 @@ template <int N>
 __device__ __forceinline__ float2 *row_slot(float2 *buf, int r, int pos)
 {
     // padding chosen (by simulating the bank mapping of the warp-local
-    // exchanges) so that the pass exchanges are close to conflict-free
-    return &buf[r * RowCfg<N>::SROW + pos + (pos >> 4) + (pos >> 5)];
+    // exchanges) so that the pass exchanges are close to conflict-free:
+    // two-pass plans want one pad per 16 slots, three-pass plans one more
+    // per 32
+    if constexpr (WPlanInfo<N>::NP == 2) return &buf[r * RowCfg<N>::SROW + pos + (pos >> 4)];
+    else return &buf[r * RowCfg<N>::SROW + pos + (pos >> 4) + (pos >> 5)];
 }
 
 // Hermitian-extended pair line a + i b at position pos from half spectra.

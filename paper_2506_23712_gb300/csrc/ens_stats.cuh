@@ -65,7 +65,7 @@ constexpr size_t smem_stats(int nq, int nt)
 }
 
 template <int N>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 1)
 k_z_stats(Geo g, HistDev h, const MemberDev *md)
 {
     using PI = WPlanInfo<N>;
