@@ -64,6 +64,33 @@ def abc_flow(N: int, A: float = 1.0, B: float = 0.7, C: float = 0.4) -> np.ndarr
     return np.stack([A * np.sin(Z) + C * np.cos(Y), B * np.sin(X) + A * np.cos(Z), C * np.sin(Y) + B * np.cos(X)])
 
 
+def synthetic_member_counts(lams, nq, nt, npoints, seed):
+    """Member histograms drawn from smooth, lambda-dependent model densities
+    (multinomial samples of npoints per PDF kind), in the library's counts
+    layout [qr nq*nq | eps nt | enstrophy nt | 8 counters]; npoints is stored
+    at counter 6.  Used to exercise the lambda interpolant on inputs with a
+    known smooth lambda dependence."""
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    c = (np.arange(nq) + 0.5) / nq * 2 - 1
+    Qg, Rg = np.meshgrid(c, c, indexing="ij")
+    x = (np.arange(nt) + 0.5) / nt * 2 - 1
+    out = np.zeros((len(lams), nq * nq + 2 * nt + 8), dtype=np.uint64)
+    for i, lam in enumerate(lams):
+        s = 0.25 * math.exp(lam / 8.0)
+        pqr = np.exp(-(Qg ** 2 + (Rg - 0.2 * Qg) ** 2) / (2 * s * s)) * (1 + 0.3 * np.tanh(3 * (Rg + Qg)))
+        pe = np.exp(-(x - (-0.2 + 0.08 * lam)) ** 2 / (2 * (0.15 * math.exp(lam / 10.0)) ** 2))
+        pw = np.exp(-(x - (-0.1 + 0.1 * lam)) ** 2 / (2 * (0.18 * math.exp(lam / 10.0)) ** 2))
+        parts = []
+        for p in (pqr.ravel(), pe, pw):
+            p = p / p.sum()
+            parts.append(rng.multinomial(npoints, p))
+        out[i, :nq * nq] = parts[0]
+        out[i, nq * nq:nq * nq + nt] = parts[1]
+        out[i, nq * nq + nt:nq * nq + 2 * nt] = parts[2]
+        out[i, nq * nq + 2 * nt + 6] = npoints
+    return out
+
+
 # ---------------------------------------------------------------------------
 # workloads: lists of member parameter dicts (keys of ens_member_desc)
 # ---------------------------------------------------------------------------

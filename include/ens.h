@@ -251,6 +251,55 @@ ens_status ens_rhs(ens_ctx *ctx, int member, double *host_spec);
 ens_status ens_diagnostics(ens_ctx *ctx, ens_diag *out);
 ens_status ens_synchronize(ens_ctx *ctx);
 
+/* ---- learned lambda interpolant (surrogate) ------------------------------
+ * A 4-layer MLP (width 256, SiLU; BF16 weights, FP32 accumulation on the
+ * tcgen05 tensor cores, FP32 master weights, Adam) that maps (bin, lambda) to
+ * a logit; a softmax over the bins of each PDF kind gives the per-lambda
+ * densities of the joint Q-R histogram and of the two tail histograms.  It
+ * lets the lambda mixture of Sec. II (Eq. ensemble_hypothesis) and Sec. IV
+ * (Eq. gaussian_lambda_pdf) be evaluated on a fine lambda quadrature between
+ * the simulated members; the member quadrature (ens_mixture) remains the
+ * reference and judges its error.  The paper itself mixes member statistics
+ * directly; the interpolant is this library's addition.
+ *
+ * Row features of (bin, lambda): bin centre coordinates scaled to [-1, 1]
+ * (Q and R for the joint PDF, the log axis for the tails), lambda / 5, a
+ * one-hot PDF kind, and sin/cos(pi k s) of the three coordinates for
+ * k = 1..4 (31 features, padded to 64).  Targets: each member's in-range
+ * histogram of each kind normalised to unit sum; loss: mean over (member,
+ * kind) of the cross-entropy -sum_b p_b log q_b.  Parameters (FP32, this
+ * order): W1 [256][64], b1 [256], W2 [256][256], b2, W3 [256][256], b3,
+ * w4 [256], b4 [1].  Work runs on `stream`; calls returning host data
+ * synchronise it.  Device memory is allocated by the object. */
+typedef struct ens_surrogate ens_surrogate;
+ens_status ens_surrogate_create(uint64_t seed, void *stream, ens_surrogate **out);
+ens_status ens_surrogate_destroy(ens_surrogate *s);
+size_t ens_surrogate_param_count(void);
+ens_status ens_surrogate_get_params(ens_surrogate *s, float *host);
+ens_status ens_surrogate_set_params(ens_surrogate *s, const float *host);
+/* Loss and gradient (FP32, parameter order above) of the current parameters
+ * on n members' histograms (counts layout of ens_get_stats). */
+ens_status ens_surrogate_loss_grad(ens_surrogate *s, int n, const double *lambdas, const uint64_t *counts,
+                                   const ens_hist_spec *hist, double *loss, float *grad);
+/* `steps` full-batch Adam steps (learning rate lr) on the members'
+ * histograms; *final_loss is the loss of the last step's forward pass. */
+ens_status ens_surrogate_train(ens_surrogate *s, int n, const double *lambdas, const uint64_t *counts,
+                               const ens_hist_spec *hist, int steps, double lr, double *final_loss);
+/* Densities (bin probabilities) at n lambda values: probs [n][qr_bins^2 +
+ * 2 tail_bins], each kind summing to one. */
+ens_status ens_surrogate_density(ens_surrogate *s, int n, const double *lambdas, const ens_hist_spec *hist,
+                                 double *probs);
+/* Mixture over a midpoint lambda quadrature of nquad points on
+ * [lam_lo, lam_hi] with the masses of a Gaussian weight specification
+ * (ENS_W_GAUSS_PAPER or ENS_W_GAUSS), renormalised; fills pdf_qr, pdf_eps,
+ * pdf_ens of `out` (same units as ens_mixture). */
+ens_status ens_surrogate_mixture(ens_surrogate *s, const ens_hist_spec *hist, const ens_weight_spec *w,
+                                 double lam_lo, double lam_hi, int nquad, ens_mixture_out *out);
+/* Tensor-core GEMM check C = A B^T on host BF16 bit patterns: A [M][K],
+ * B [N][K], C [M][N] FP32; M % 128 == 0, N % 64 == 0, K % (64 ksplit) == 0,
+ * ksplit <= 32 splits K across CTAs (partials summed in a fixed order). */
+ens_status ens_tc_gemm_check(const uint16_t *A, const uint16_t *B, float *C, int M, int N, int K, int ksplit);
+
 /* ---- introspection / profiling ----------------------------------------- */
 
 /* Number of members, grid size of a member. */

@@ -96,6 +96,16 @@ SIGNATURES = [
     ("ens_run_pass", _i, [_vp, _i, _i]),
     ("ens_kernels_per_step", _i, [_vp]),
     ("ens_pass_bytes", _d, [_vp, _i, _i]),
+    ("ens_surrogate_create", _i, [ctypes.c_uint64, _vp, _P(_vp)]),
+    ("ens_surrogate_destroy", _i, [_vp]),
+    ("ens_surrogate_param_count", _sz, []),
+    ("ens_surrogate_get_params", _i, [_vp, _vp]),
+    ("ens_surrogate_set_params", _i, [_vp, _vp]),
+    ("ens_surrogate_loss_grad", _i, [_vp, _i, _vp, _vp, _P(HistSpec), _P(_d), _vp]),
+    ("ens_surrogate_train", _i, [_vp, _i, _vp, _vp, _P(HistSpec), _i, _d, _P(_d)]),
+    ("ens_surrogate_density", _i, [_vp, _i, _vp, _P(HistSpec), _vp]),
+    ("ens_surrogate_mixture", _i, [_vp, _P(HistSpec), _P(WeightSpec), _d, _d, _i, _P(MixtureOut)]),
+    ("ens_tc_gemm_check", _i, [_vp, _vp, _vp, _i, _i, _i, _i]),
 ]
 
 _lib = None
@@ -409,6 +419,86 @@ class Ensemble:
         if getattr(self, "ctx", None):
             ens_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# learned lambda interpolant (surrogate)
+# ---------------------------------------------------------------------------
+def ens_tc_gemm_check(A_bf16_bits, B_bf16_bits, ksplit=1):
+    """C = A B^T on the tensor cores; A [M][K], B [N][K] as uint16 BF16 bits."""
+    A = np.ascontiguousarray(A_bf16_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bf16_bits, dtype=np.uint16)
+    M, K = A.shape
+    N = B.shape[0]
+    C = np.zeros((M, N), dtype=np.float32)
+    _check(lib().ens_tc_gemm_check(_ptr(A), _ptr(B), _ptr(C), M, N, K, ksplit))
+    return C
+
+
+class Surrogate:
+    """Owner of an ens_surrogate (MLP over (bin, lambda) on the tensor cores)."""
+
+    def __init__(self, seed=0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libens needs a CUDA GPU; no CPU fallback exists")
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib().ens_surrogate_create(seed, _stream_ptr(self._stream), ctypes.byref(h)))
+        self.h = h
+        self.nparam = lib().ens_surrogate_param_count()
+
+    def params(self):
+        out = np.zeros(self.nparam, dtype=np.float32)
+        _check(lib().ens_surrogate_get_params(self.h, _ptr(out)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparam
+        _check(lib().ens_surrogate_set_params(self.h, _ptr(p)))
+
+    def loss_grad(self, lambdas, counts, hist):
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        counts = np.ascontiguousarray(counts, dtype=np.uint64)
+        g = np.zeros(self.nparam, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().ens_surrogate_loss_grad(self.h, lam.size, _ptr(lam), _ptr(counts), ctypes.byref(hist),
+                                             ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train(self, lambdas, counts, hist, steps, lr=1e-3):
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        counts = np.ascontiguousarray(counts, dtype=np.uint64)
+        loss = ctypes.c_double()
+        _check(lib().ens_surrogate_train(self.h, lam.size, _ptr(lam), _ptr(counts), ctypes.byref(hist), steps, lr,
+                                         ctypes.byref(loss)))
+        return loss.value
+
+    def density(self, lambdas, hist):
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        per = hist.qr_bins ** 2 + 2 * hist.tail_bins
+        out = np.zeros((lam.size, per), dtype=np.float64)
+        _check(lib().ens_surrogate_density(self.h, lam.size, _ptr(lam), ctypes.byref(hist), _ptr(out)))
+        return out
+
+    def mixture(self, hist, lam_lo, lam_hi, nquad=512, **weights):
+        ws, keep = _weight_spec(**weights)
+        out, bufs = _mixture_out(1, hist)
+        _check(lib().ens_surrogate_mixture(self.h, ctypes.byref(hist), ctypes.byref(ws), lam_lo, lam_hi, nquad,
+                                           ctypes.byref(out)))
+        return _mixture_result(out, bufs, hist)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ens_surrogate_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:
