@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-uneven", action="store_true")
     return p.parse_args()
 
 
@@ -232,6 +233,36 @@ def run_reference(args, members):
     print(json.dumps(line), flush=True)
 
 
+def measure_uneven(E, torch, steps=3):
+    """Uneven-size batch (24 x 128^3, 12 x 256^3, 4 x 384^3): all members in
+    one graph per step (one branch per grid size) vs member-by-member
+    launches of the same kernels."""
+    import ens_inputs as I
+    ms = [E.Member(N=d["N"], nu=d["nu"], lam=d["lam"], eps_bar=d["eps_bar"], k_lo=d["k_lo"], k_hi=d["k_hi"],
+                   dt=d["dt"], cfl=d["cfl"], dt_max=d["dt_max"], rk_order=d["rk_order"], seed=d["seed"],
+                   init_energy=d["init_energy"]) for d in I.uneven_batch()]
+    stream = torch.cuda.current_stream()
+    ens = E.Ensemble(ms, hist=E.hist_spec(nu_norm=ms[0].nu), stream=stream)
+    out = {"workload": "24 x 128^3 + 12 x 256^3 + 4 x 384^3, IF-RK3, CFL 0.2, k_max eta >= 1.5",
+           "members": len(ms), "steps": steps}
+    for mode in ("batched", "sequential"):
+        run = (lambda k: ens.step(k)) if mode == "batched" else (lambda k: E.ens_step_sequential(ens.ctx, k))
+        run(1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        out[mode] = {"member_steps_per_s": len(ms) * steps / sec, "ms_per_step": 1e3 * sec / steps}
+    out["batched_over_sequential"] = out["batched"]["member_steps_per_s"] / out["sequential"]["member_steps_per_s"]
+    flags = sum(1 for d in ens.diagnostics(raise_on_flag=False) if d["flags"])
+    out["flagged_members"] = flags
+    ens.close()
+    return out
+
+
 def traffic_for(kernel):
     """ncu DRAM bytes per launch of the kernel (profiles/traffic.json), or None
     if the kernel source changed since the capture."""
@@ -362,6 +393,12 @@ def main():
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(members[0])
 
+    state_gb = ens.state_bytes() / 1e9
+    ens.close()
+    uneven = None
+    if not args.no_uneven and rank == 0:
+        uneven = measure_uneven(E, torch)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -369,14 +406,13 @@ def main():
                 "config": {"workload": WORKLOAD, "members": n_mem, "N": args.N, "rk_order": 3,
                            "grid_point_updates_per_s": value * args.N ** 3,
                            "l2": "inputs larger than L2 (state %.1f GB, per-pass buffers %.0f GB)" % (
-                               ens.state_bytes() / 1e9, step_bytes / 1e9),
+                               state_gb, step_bytes / 1e9),
                            "parallelism": "replicas per GPU" if world > 1 else "single GPU",
                            "step_hbm_roofline_frac": round(step_frac, 4),
                            "flagged_members": flagged},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kps * args.steps,
-                "clocks": clk, "plain": plain, "passes": passes}
+                "clocks": clk, "plain": plain, "passes": passes, "uneven_batch": uneven}
         print(json.dumps(line), flush=True)
-    ens.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -172,6 +172,9 @@ const char *ens_status_string(ens_status s);
 ens_status ens_step(ens_ctx *ctx, int nsteps);
 /* Same, launching the kernels directly instead of replaying a graph. */
 ens_status ens_step_nograph(ens_ctx *ctx, int nsteps);
+/* Same results, launched the slow way for comparison: one member at a time,
+ * every pass of every member a separate launch on the context stream. */
+ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
 
 /* ---- statistics (Secs. V-VII) ---------------------------------------- */
 

@@ -45,6 +45,9 @@ struct ens_ctx {
     std::vector<int> member_group, member_local;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    std::vector<cudaStream_t> aux;        // one per group (index 0 unused)
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
     void *workspace = nullptr;
     bool owns = false;
     size_t ws_bytes = 0;
@@ -214,20 +217,50 @@ Geo single(const ens_ctx *ctx, int i)
     return g;
 }
 
+void record_group_stage(ens_ctx *ctx, const Geo &g, int st, int last, cudaStream_t s)
+{
+    launch_pass(Pass::IX, 0, g, ctx->md, nullptr, st, last, st > 0 ? 1 : 0, s);
+    launch_pass(Pass::IY, 0, g, ctx->md, nullptr, st, last, 6, s);
+    launch_pass(Pass::Z, 0, g, ctx->md, nullptr, st, last, 0, s);
+    launch_pass(Pass::FY, 0, g, ctx->md, nullptr, st, last, 0, s);
+    launch_pass(Pass::FX, 0, g, ctx->md, nullptr, st, last, 0, s);
+}
+
+// One step.  Groups of different grid size are independent until the
+// per-member stage reduction, so with several groups each group's pass chain
+// runs on its own stream (a parallel branch of the captured graph), joined
+// before the reduction of every stage.
 void record_step(ens_ctx *ctx, cudaStream_t s)
+{
+    const int nst = ctx->rk;
+    const int n = (int)ctx->desc.size();
+    const int ng = (int)ctx->groups.size();
+    for (int st = 0; st < nst; ++st) {
+        const int last = st == nst - 1;
+        if (ng == 1) {
+            record_group_stage(ctx, ctx->groups[0].geo, st, last, s);
+        } else {
+            cudaEventRecord(ctx->ev_fork, s);
+            for (int gi = 1; gi < ng; ++gi) {
+                cudaStreamWaitEvent(ctx->aux[gi], ctx->ev_fork, 0);
+                record_group_stage(ctx, ctx->groups[gi].geo, st, last, ctx->aux[gi]);
+                cudaEventRecord(ctx->ev_join[gi], ctx->aux[gi]);
+            }
+            record_group_stage(ctx, ctx->groups[0].geo, st, last, s);
+            for (int gi = 1; gi < ng; ++gi) cudaStreamWaitEvent(s, ctx->ev_join[gi], 0);
+        }
+        launch_finish(ctx->md, n, ctx->partial, ctx->partial_blocks, st, last, 0, s);
+    }
+}
+
+// Comparison mode: every member on its own, one after another, one stream.
+void record_step_sequential(ens_ctx *ctx, cudaStream_t s)
 {
     const int nst = ctx->rk;
     const int n = (int)ctx->desc.size();
     for (int st = 0; st < nst; ++st) {
         const int last = st == nst - 1;
-        for (auto &gr : ctx->groups) {
-            const Geo &g = gr.geo;
-            launch_pass(Pass::IX, 0, g, ctx->md, nullptr, st, last, st > 0 ? 1 : 0, s);
-            launch_pass(Pass::IY, 0, g, ctx->md, nullptr, st, last, 6, s);
-            launch_pass(Pass::Z, 0, g, ctx->md, nullptr, st, last, 0, s);
-            launch_pass(Pass::FY, 0, g, ctx->md, nullptr, st, last, 0, s);
-            launch_pass(Pass::FX, 0, g, ctx->md, nullptr, st, last, 0, s);
-        }
+        for (int i = 0; i < n; ++i) record_group_stage(ctx, single(ctx, i), st, last, s);
         launch_finish(ctx->md, n, ctx->partial, ctx->partial_blocks, st, last, 0, s);
     }
 }
@@ -318,6 +351,13 @@ static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, co
     }
     cudaStream_t st = ctx->stream;
     ENS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    ENS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    ctx->aux.assign(ctx->groups.size(), nullptr);
+    ctx->ev_join.assign(ctx->groups.size(), nullptr);
+    for (size_t gi = 1; gi < ctx->groups.size(); ++gi) {
+        ENS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[gi], cudaStreamNonBlocking));
+        ENS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join[gi], cudaEventDisableTiming));
+    }
     ENS_CUDA(ctx, cudaMemcpyAsync(ctx->md, md.data(), sizeof(MemberDev) * n, cudaMemcpyHostToDevice, st));
     ENS_CUDA(ctx, cudaMemsetAsync(ctx->partial, 0, sizeof(double) * n * ctx->partial_blocks * 4, st));
     const long long L = counts_len_of(h->qr_bins, h->tail_bins);
@@ -447,6 +487,11 @@ ens_status ens_destroy(ens_ctx *ctx)
     else cudaDeviceSynchronize();
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (auto st : ctx->aux)
+        if (st) cudaStreamDestroy(st);
+    for (auto ev : ctx->ev_join)
+        if (ev) cudaEventDestroy(ev);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->owns && ctx->workspace) cudaFree(ctx->workspace);
     delete ctx;
     return ENS_OK;
@@ -458,6 +503,16 @@ int ens_member_n(const ens_ctx *ctx, int i)
     return (ctx && i >= 0 && i < (int)ctx->desc.size()) ? ctx->desc[i].N : 0;
 }
 int ens_kernels_per_step(const ens_ctx *ctx) { return ctx ? ctx->rk * (5 * (int)ctx->groups.size() + 1) : 0; }
+
+ens_status ens_step_sequential(ens_ctx *ctx, int nsteps)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (nsteps < 0) return fail(ctx, ENS_EINVAL, "nsteps < 0");
+    for (int k = 0; k < nsteps; ++k) record_step_sequential(ctx, ctx->stream);
+    ENS_CUDA(ctx, cudaGetLastError());
+    return ENS_OK;
+}
 
 ens_status ens_step_nograph(ens_ctx *ctx, int nsteps)
 {

@@ -75,6 +75,7 @@ SIGNATURES = [
     ("ens_status_string", ctypes.c_char_p, [_i]),
     ("ens_step", _i, [_vp, _i]),
     ("ens_step_nograph", _i, [_vp, _i]),
+    ("ens_step_sequential", _i, [_vp, _i]),
     ("ens_gradient_stats", _i, [_vp, _i]),
     ("ens_get_stats", _i, [_vp, _vp, _vp]),
     ("ens_counts_len", _i, [_P(HistSpec)]),
@@ -171,6 +172,10 @@ def ens_step(ctx, nsteps=1):
 
 def ens_step_nograph(ctx, nsteps=1):
     _check(lib().ens_step_nograph(ctx, nsteps), ctx)
+
+
+def ens_step_sequential(ctx, nsteps=1):
+    _check(lib().ens_step_sequential(ctx, nsteps), ctx)
 
 
 def ens_gradient_stats(ctx, accumulate=True):

@@ -306,3 +306,21 @@ def test_nonfinite_member_is_reported(E):
     assert status == 4
     assert diags[1]["flags"] & 1 and not diags[0]["flags"] & 1
     ens.close()
+
+
+def test_uneven_groups_graph_branches_match_sequential(E):
+    """Members of three grid sizes: the graph with one branch per grid size,
+    direct launches, and member-by-member launches give identical fields."""
+    ms = [E.Member(N=n, nu=0.03, lam=0.2 * i - 0.5, k_lo=1, k_hi=2, dt=-1, cfl=0.2, rk_order=3, seed=40 + i)
+          for i, n in enumerate([16, 32, 64, 32, 16, 64])]
+    a, b, c = E.Ensemble(ms), E.Ensemble(ms), E.Ensemble(ms)
+    a.step(2, graph=True)
+    b.step(2, graph=False)
+    E.ens_step_sequential(c.ctx, 2)
+    for i in range(len(ms)):
+        fa = a.field(i)
+        assert np.array_equal(fa, b.field(i)) and np.array_equal(fa, c.field(i)), i
+    da, dc = a.diagnostics(), c.diagnostics()
+    assert [d["dt"] for d in da] == [d["dt"] for d in dc]
+    for e in (a, b, c):
+        e.close()
