@@ -104,43 +104,66 @@ k_inv_x(Geo g, int use_S)
 
     float2 *dst0 = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
     auto at = [&](int pos) { return &buf[pos * kTile + c]; };
-#pragma unroll 1
-    for (int f = 0; f < NF; ++f) {
-        float2 v[V];
+    // transform of component q of the tile, optionally times i kx (the x
+    // derivative: kx varies along this transform, so it is applied before it)
+    auto transform = [&](float2 *v, int q, bool dx) {
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const int kxi = wnum(PI::in_pos(p, i), N);
             const bool keep = kxi >= -g.kc && kxi <= g.kc;
             const int ix = kxi >= 0 ? kxi : kxi + g.NK;
-            const float kx = (float)kxi;
-            const float2 z = make_float2(0.f, 0.f);
-            const float2 a = keep ? tile[ix * kTile + c] : z;
-            const float2 b = keep ? tile[per + ix * kTile + c] : z;
-            const float2 d = keep ? tile[2 * per + ix * kTile + c] : z;
-            if (MODE == 0) {
-                if (f < 3) {
-                    v[i] = f == 0 ? a : (f == 1 ? b : d);
-                } else {
-                    // omega = i k x u: (k x u)_x = ky uz - kz uy, _y = kz ux - kx uz, _z = kx uy - ky ux
-                    float2 cr;
-                    if (f == 3) cr = make_float2(ky * d.x - kzf * b.x, ky * d.y - kzf * b.y);
-                    else if (f == 4) cr = make_float2(kzf * a.x - kx * d.x, kzf * a.y - kx * d.y);
-                    else cr = make_float2(kx * b.x - ky * a.x, kx * b.y - ky * a.y);
-                    v[i] = mul_i(cr);
-                }
-            } else {
-                // A_ij = i k_j u_i, f = 3 i + j
-                const float2 uc = f < 3 ? a : (f < 6 ? b : d);
-                const int cj = f % 3;
-                const float kj = cj == 0 ? kx : (cj == 1 ? ky : kzf);
-                v[i] = mul_i(cscale(uc, kj));
-            }
+            const float2 u = keep ? tile[q * per + ix * kTile + c] : make_float2(0.f, 0.f);
+            v[i] = dx ? mul_i(cscale(u, (float)kxi)) : u;
         }
         fft_line<N, false>(v, p, tw, at);
+    };
+    auto store = [&](const float2 *v, int f) {
         if (valid) {
             float2 *dst = dst0 + (long long)f * g.sA;
 #pragma unroll
             for (int i = 0; i < V; ++i) dst[(long long)PI::out_pos(p, i) * g.NZp] = v[i];
+        }
+    };
+    // ky and kz are constant along x, so their derivatives are applied after
+    // the transform: 5 transforms give u and omega, 6 give the 8 gradients
+    float2 Ua[V], Ub[V];
+    if constexpr (MODE == 0) {
+        // omega = i k x u: (k x u)_x = ky uz - kz uy, _y = kz ux - kx uz, _z = kx uy - ky ux
+        transform(Ua, 1, false);                                  // uy
+        store(Ua, 1);
+        transform(Ub, 2, false);                                  // uz
+        store(Ub, 2);
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+            Ua[i] = mul_i(make_float2(ky * Ub[i].x - kzf * Ua[i].x, ky * Ub[i].y - kzf * Ua[i].y));
+        store(Ua, 3);                                             // omega_x
+        transform(Ua, 0, false);                                  // ux
+        store(Ua, 0);
+        transform(Ub, 2, true);                                   // i kx uz
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+            Ub[i] = make_float2(-kzf * Ua[i].y - Ub[i].x, kzf * Ua[i].x - Ub[i].y);   // i kz ux - i kx uz
+        store(Ub, 4);                                             // omega_y
+        transform(Ub, 1, true);                                   // i kx uy
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+            Ub[i] = make_float2(Ub[i].x + ky * Ua[i].y, Ub[i].y - ky * Ua[i].x);      // i kx uy - i ky ux
+        store(Ub, 5);                                             // omega_z
+    } else {
+        // A_ij = i k_j u_i, f = 3 i + j (A_33 is not stored)
+#pragma unroll 1
+        for (int ci = 0; ci < 3; ++ci) {
+            transform(Ua, ci, false);
+#pragma unroll
+            for (int i = 0; i < V; ++i) Ub[i] = mul_i(cscale(Ua[i], ky));
+            store(Ub, 3 * ci + 1);
+            if (ci < 2) {
+#pragma unroll
+                for (int i = 0; i < V; ++i) Ub[i] = mul_i(cscale(Ua[i], kzf));
+                store(Ub, 3 * ci + 2);
+            }
+            transform(Ub, ci, true);
+            store(Ub, 3 * ci);
         }
     }
 }
@@ -481,18 +504,29 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
     const int per = g.NK * kTile;
     const float2 *Ain = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
     auto at = [&](int pos) { return &buf[pos * kTile + c]; };
-    // forward transforms of the three components; kept rows to the tile
+    // forward transforms of the three components; kept rows to the tile.
+    // The next component's inputs are loaded while this one is transformed.
+    float2 v[V], nxt[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+        v[i] = valid ? Ain[(long long)PI::in_pos(p, i) * g.NZp] : make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int q = 0; q < 3; ++q) {
-        float2 v[V];
+        if (q < 2) {
 #pragma unroll
-        for (int i = 0; i < V; ++i)
-            v[i] = valid ? Ain[(long long)q * g.sA + (long long)PI::in_pos(p, i) * g.NZp] : make_float2(0.f, 0.f);
+            for (int i = 0; i < V; ++i)
+                nxt[i] = valid ? Ain[(long long)(q + 1) * g.sA + (long long)PI::in_pos(p, i) * g.NZp]
+                               : make_float2(0.f, 0.f);
+        }
         fft_line<N, true>(v, p, tw, at);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const int kx = wnum(PI::out_pos(p, i), N);
             if (kx >= -g.kc && kx <= g.kc) tile[q * per + (kx >= 0 ? kx : kx + g.NK) * kTile + c] = v[i];
+        }
+        if (q < 2) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) v[i] = nxt[i];
         }
     }
     __syncthreads();
@@ -518,8 +552,29 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
         for (int s = threadIdx.x; s < g.shells; s += blockDim.x) shell_smem[s] = 0.0;
         __syncthreads();
     }
-    // per kept mode of the tile: thread <-> (kx row, column), coalesced in the column
-    for (int idx = threadIdx.x; idx < per; idx += blockDim.x) {
+    // per kept mode of the tile: thread <-> (kx row, column), coalesced in the
+    // column; the state reads of UB modes are issued together before use
+    constexpr int UB = 4;
+    for (int base = threadIdx.x; base < per; base += UB * blockDim.x) {
+        float2 unb[UB][3], usb[UB][3];
+        if constexpr (MODE == 0 || MODE == 1) {
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int idx = base + u * blockDim.x;
+                const int cc = idx % kTile;
+                const bool ok = idx < per && ((col0 + cc) % g.NZp) < g.NZ;
+                const long long off = (long long)(idx / kTile) * rowU + cc;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    unb[u][q] = ok ? U[q * g.sU + off] : make_float2(0.f, 0.f);
+                    usb[u][q] = (ok && stage != 0) ? S[q * g.sU + off] : unb[u][q];
+                }
+            }
+        }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx >= per) continue;
         const int ix = idx / kTile, cc = idx % kTile;
         const int kzc = (col0 + cc) % g.NZp;
         if (kzc >= g.NZ) continue;
@@ -559,8 +614,8 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
             float2 us[3], un[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                un[q] = U[q * g.sU + off];
-                us[q] = stage == 0 ? un[q] : S[q * g.sU + off];
+                un[q] = unb[u][q];
+                us[q] = usb[u][q];
                 if (band) n[q] = make_float2(n[q].x + alpha * us[q].x, n[q].y + alpha * us[q].y);
             }
             if constexpr (MODE == 1) {
@@ -584,6 +639,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
                 if (band) sb += 0.5f * wgt * a2;
             }
         }
+    }
     }
     if constexpr (MODE == 2) {
         __syncthreads();
