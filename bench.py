@@ -29,6 +29,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -52,6 +54,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-uneven", action="store_true")
+    p.add_argument("--no-surrogate", action="store_true")
     return p.parse_args()
 
 
@@ -233,6 +236,60 @@ def run_reference(args, members):
     print(json.dumps(line), flush=True)
 
 
+def hellinger(p, q):
+    p = np.asarray(p, dtype=np.float64).ravel()
+    q = np.asarray(q, dtype=np.float64).ravel()
+    p, q = p / p.sum(), q / q.sum()
+    return float(np.sqrt(max(0.0, 1.0 - np.sum(np.sqrt(p * q)))))
+
+
+def measure_surrogate(E, ens, descs, torch, steps=200):
+    """Learned lambda interpolant on this ensemble's own histograms: training
+    throughput, the tcgen05 hidden-layer GEMM against the BF16 peak, and the
+    512-point quadrature mixture against the member quadrature (Hellinger)."""
+    ens.gradient_stats(accumulate=False)
+    counts, _ = ens.stats()
+    h = ens.hist
+    lams = np.array([d.lam for d in descs])
+    per = h.qr_bins ** 2 + 2 * h.tail_bins
+    S = E.Surrogate(seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = S.train(lams, counts, h, steps, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    rows_q = 512 * per
+    gemm_ms = S.time_gemm(rows_q, iters=5)
+    tflops = 2.0 * pad128(rows_q) * 256 * 256 / (gemm_ms / 1e3) / 1e12
+    Z = 1.5 * math.log(261.0 / 63.0)
+    s = np.sort(np.unique(lams))
+    lo, hi = s[0] - 0.5 * (s[1] - s[0]), s[-1] + 0.5 * (s[-1] - s[-2])
+    ref = E.ens_mixture(ens.ctx, len(lams), h, kind=E.W_GAUSS_PAPER, c=0.023, Z=Z)
+    t0 = time.perf_counter()
+    sur = S.mixture(h, lo, hi, 512, kind=E.W_GAUSS_PAPER, c=0.023, Z=Z)
+    t_inf = time.perf_counter() - t0
+    S.close()
+    peak = measured_bf16()
+    return {"members": len(lams), "bins_per_member": per, "train_steps": steps, "train_s": t_train,
+            "train_rows_per_step": len(lams) * per, "final_loss": loss,
+            "quadrature_points": 512, "mixture_s": t_inf,
+            "hellinger_vs_member_quadrature": {k: hellinger(sur[k], ref[k]) for k in ("pdf_qr", "pdf_eps", "pdf_ens")},
+            "Z": Z, "roofline": {"bound": "tensor", "kernel": "k_gemm_tc<256>", "achieved": tflops, "peak": peak[0],
+                                  "unit": "TFLOP/s", "frac": tflops / peak[0], "peak_source": peak[1],
+                                  "shape": "%d x 256 x 256 BF16 -> FP32" % pad128(rows_q), "ms": gemm_ms}}
+
+
+def pad128(r):
+    return (r + 127) // 128 * 128
+
+
+def measured_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured bf16_tflops (burst cuBLAS)"
+    return 1900.0, "fallback"
+
+
 def measure_uneven(E, torch, steps=3):
     """Uneven-size batch (24 x 128^3, 12 x 256^3, 4 x 384^3): all members in
     one graph per step (one branch per grid size) vs member-by-member
@@ -393,6 +450,9 @@ def main():
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(members[0])
 
+    surrogate = None
+    if not args.no_surrogate and rank == 0:
+        surrogate = measure_surrogate(E, ens, descs, torch)
     state_gb = ens.state_bytes() / 1e9
     ens.close()
     uneven = None
@@ -411,7 +471,8 @@ def main():
                            "step_hbm_roofline_frac": round(step_frac, 4),
                            "flagged_members": flagged},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kps * args.steps,
-                "clocks": clk, "plain": plain, "passes": passes, "uneven_batch": uneven}
+                "clocks": clk, "plain": plain, "passes": passes, "uneven_batch": uneven,
+                "surrogate": surrogate}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

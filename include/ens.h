@@ -298,6 +298,9 @@ ens_status ens_surrogate_density(ens_surrogate *s, int n, const double *lambdas,
  * pdf_ens of `out` (same units as ens_mixture). */
 ens_status ens_surrogate_mixture(ens_surrogate *s, const ens_hist_spec *hist, const ens_weight_spec *w,
                                  double lam_lo, double lam_hi, int nquad, ens_mixture_out *out);
+/* Average device time (ms, CUDA events on the object's stream) of one
+ * hidden-layer GEMM of `rows` rows (rows x 256 x 256, BF16 in, FP32 out). */
+ens_status ens_surrogate_time_gemm(ens_surrogate *s, long long rows, int iters, double *ms);
 /* Tensor-core GEMM check C = A B^T on host BF16 bit patterns: A [M][K],
  * B [N][K], C [M][N] FP32; M % 128 == 0, N % 64 == 0, K % (64 ksplit) == 0,
  * ksplit <= 32 splits K across CTAs (partials summed in a fixed order). */

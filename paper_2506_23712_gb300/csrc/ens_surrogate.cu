@@ -840,6 +840,31 @@ ens_status ens_surrogate_mixture(ens_surrogate *S, const ens_hist_spec *h, const
     return ENS_OK;
 }
 
+// average time of the hidden-layer GEMM (rows x 256 x 256) on the object's
+// buffers, CUDA events on its stream (profiling)
+ens_status ens_surrogate_time_gemm(ens_surrogate *S, long long rows, int iters, double *ms)
+{
+    if (!S || rows <= 0 || iters < 1 || !ms) return ENS_EINVAL;
+    rows = pad128(rows);
+    if (!alloc_work(S, rows, 3)) return ENS_ENOMEM;
+    cudaMemsetAsync(S->H1, 0, sizeof(__nv_bfloat16) * rows * kHid, S->s);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    gemm(S->H1, kHid, S->W2b, kHid, S->Z2, kHid, (int)rows, kHid, kHid, 1, S->err, S->s);   // warm-up
+    cudaEventRecord(a, S->s);
+    for (int i = 0; i < iters; ++i) gemm(S->H1, kHid, S->W2b, kHid, S->Z2, kHid, (int)rows, kHid, kHid, 1, S->err, S->s);
+    cudaEventRecord(b, S->s);
+    float t = 0.f;
+    const cudaError_t e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return ENS_ECUDA;
+    *ms = t / iters;
+    return check_err(S);
+}
+
 // tensor-core GEMM check: C = A B^T for host BF16 bit patterns (tests)
 ens_status ens_tc_gemm_check(const uint16_t *A, const uint16_t *B, float *C, int M, int N, int K, int ksplit)
 {

@@ -106,6 +106,7 @@ SIGNATURES = [
     ("ens_surrogate_train", _i, [_vp, _i, _vp, _vp, _P(HistSpec), _i, _d, _P(_d)]),
     ("ens_surrogate_density", _i, [_vp, _i, _vp, _P(HistSpec), _vp]),
     ("ens_surrogate_mixture", _i, [_vp, _P(HistSpec), _P(WeightSpec), _d, _d, _i, _P(MixtureOut)]),
+    ("ens_surrogate_time_gemm", _i, [_vp, ctypes.c_longlong, _i, _P(_d)]),
     ("ens_tc_gemm_check", _i, [_vp, _vp, _vp, _i, _i, _i, _i]),
 ]
 
@@ -492,6 +493,11 @@ class Surrogate:
         out = np.zeros((lam.size, per), dtype=np.float64)
         _check(lib().ens_surrogate_density(self.h, lam.size, _ptr(lam), ctypes.byref(hist), _ptr(out)))
         return out
+
+    def time_gemm(self, rows, iters=10):
+        ms = ctypes.c_double()
+        _check(lib().ens_surrogate_time_gemm(self.h, rows, iters, ctypes.byref(ms)))
+        return ms.value
 
     def mixture(self, hist, lam_lo, lam_hi, nquad=512, **weights):
         ws, keep = _weight_spec(**weights)
