@@ -112,8 +112,9 @@ def lambda_pdf_from_K(K, lam_grid):
     dl = lam[1] - lam[0]
     s = 2.0 * math.pi * np.fft.fftfreq(n, d=dl)
     phi = np.exp(np.array([K(1j * si) for si in s], dtype=np.complex128))
-    # P(l) = 1/(2 pi) int ds exp(-i s l) phi(s)  ~  (1/(n dl)) sum_s exp(-i s l) phi(s)
-    P = np.real(np.exp(-1j * np.outer(lam - lam[0], s)) @ (phi * np.exp(-1j * s * lam[0]))) / (n * dl)
+    # P(l_j) = 1/(2 pi) int ds exp(-i s l_j) phi(s)
+    #        ~ (1/(n dl)) sum_k exp(-i s_k l_0) phi(s_k) exp(-2 pi i k j / n): a forward DFT
+    P = np.real(np.fft.fft(phi * np.exp(-1j * s * lam[0]))) / (n * dl)
     return P
 
 
@@ -251,3 +252,85 @@ def cost_ratio(R_ref, R_ens, n):
 def Z_from_Rlambda(R_ref, R_ens):
     """Sec. V, Eq. Rlambda_Z_relation: R_ref ~ exp(2Z/3) with the constant fixed at Z = 0."""
     return 1.5 * math.log(R_ref / R_ens)
+
+
+def fit_R0(lams, rlambda):
+    """Constant-C_eps fit over the members with lambda >= 0 (Sec. V): with
+    Re = C_eps^(-1/3) nu^-1 (eps L^4)^(1/3) (Eq. Re_definition) and
+    R_lambda^2 ~ Re, a member's R_lambda scales as exp(lambda/6); the fit
+    of ln R_lambda = ln R0 + lambda/6 gives R0, the central value."""
+    sel = [(l, r) for l, r in zip(lams, rlambda) if l >= 0.0]
+    return math.exp(sum(math.log(r) - l / 6.0 for l, r in sel) / len(sel))
+
+
+def scale_gap(lams, rlambda, R_ref):
+    """Z for a target R_lambda from the fitted central value."""
+    return Z_from_Rlambda(R_ref, fit_R0(lams, rlambda))
+
+
+# ---------------------------------------------------------------------------
+# general scaling exponents (Sec. III / Sec. VII): zeta families and weights
+# ---------------------------------------------------------------------------
+def zeta_logpoisson(p, beta=2.0 / 3.0, C0=2.0):
+    """Log-Poisson exponents zeta_p = p/9 + C0 (1 - beta^(p/3)) (a literature
+    parameterization the paper lists among the choices, Sec. III)."""
+    return p / 9.0 + C0 * (1.0 - beta ** (p / 3.0))
+
+
+def nelkin_rho(m, zeta):
+    """Gradient-moment exponent from the Nelkin relation rho_m = m - zeta_{m + rho_m}
+    (Sec. III, Eq. nelkin_rhom), solved by bisection."""
+    f = lambda r: r - m + zeta(m + r)
+    lo, hi = -10.0, 10.0
+    assert f(lo) < 0 < f(hi)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) < 0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def ratio_exponents(zeta):
+    """Predicted R_lambda exponents of skewness, flatness and hyper-flatness
+    (Sec. VII): 2 rho3 - 3 rho2, 2 rho4 - 4 rho2, 2 rho6 - 6 rho2."""
+    r = {m: nelkin_rho(m, zeta) for m in (2, 3, 4, 6)}
+    return 2 * r[3] - 3 * r[2], 2 * r[4] - 4 * r[2], 2 * r[6] - 6 * r[2]
+
+
+def weights_numeric(lams, K, Z, grid_lo=-30.0, grid_hi=30.0, n=8192):
+    """Member bin masses of the lambda distribution whose cumulant generating
+    function is K(t; Z) (Sec. III, Eq. cumulant_generating_function), by the
+    numerical inverse two-sided Laplace transform (Sec. VII) on a uniform
+    grid and trapezoid integration over each member's bin."""
+    grid = np.linspace(grid_lo, grid_hi, n, endpoint=False)
+    P = lambda_pdf_from_K(lambda t: K(t, Z), grid)
+    lo, hi, mult = lambda_bins(lams)
+    w = np.zeros(len(lams))
+    for i in range(len(lams)):
+        a, b = max(lo[i], grid_lo), min(hi[i], grid[-1])
+        if b <= a:
+            continue
+        xs = np.concatenate(([a], grid[(grid > a) & (grid < b)], [b]))
+        ys = np.interp(xs, grid, P)
+        w[i] = np.trapezoid(ys, xs) / mult[i]
+    return w
+
+
+def weights_logpoisson(lams, Z, beta=2.0 / 3.0, C0=2.0):
+    """Exact member masses for the log-Poisson exponents: K(t; Z) =
+    (t - zeta_3t) Z = (2t/3 - C0 (1 - beta^t)) Z is the cumulant generating
+    function of lambda = 2Z/3 + n ln(beta), n ~ Poisson(C0 Z)."""
+    lo, hi, mult = lambda_bins(lams)
+    mu = C0 * Z
+    w = np.zeros(len(lams))
+    logp = -mu
+    for k in range(0, 400):
+        if k > 0:
+            logp += math.log(mu) - math.log(k)
+        lam_k = 2.0 * Z / 3.0 + k * math.log(beta)
+        for i in range(len(lams)):
+            if lo[i] <= lam_k < hi[i]:
+                w[i] += math.exp(logp) / mult[i]
+    return w

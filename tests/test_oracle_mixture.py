@@ -149,3 +149,56 @@ def test_hellinger():
     p = np.array([0.5, 0.5, 0.0])
     assert M.hellinger(p, p) == 0.0
     assert M.hellinger(p, np.array([0.0, 0.0, 1.0])) == pytest.approx(1.0)
+
+
+def test_scale_gap_fit():
+    """Members on R_lambda = R0 exp(lambda/6) recover R0; the paper's
+    R_ens = 63, R_ref = 1300 give Z = 1.5 ln(1300/63)."""
+    lams = np.linspace(-3, 3, 13)
+    R = 63.0 * np.exp(lams / 6.0)
+    assert M.fit_R0(lams, R) == pytest.approx(63.0, rel=1e-12)
+    assert M.scale_gap(lams, R, 1300.0) == pytest.approx(1.5 * math.log(1300 / 63), rel=1e-12)
+    # only lambda >= 0 enters the fit
+    R2 = R.copy()
+    R2[lams < 0] *= 5.0
+    assert M.fit_R0(lams, R2) == pytest.approx(63.0, rel=1e-12)
+
+
+def test_nelkin_exponents_closed_forms():
+    """K41 (c = 0): rho_m = m/2; quadratic zeta: rho solves a quadratic."""
+    k41 = lambda p: p / 3.0
+    for m in (2, 3, 4, 6):
+        assert M.nelkin_rho(m, k41) == pytest.approx(m / 2.0, abs=1e-12)
+    c = 0.023
+    z = lambda p: M.zeta_quadratic(p, c)
+    for m in (2, 3, 4, 6):
+        # rho = m - (m+rho)/3 + c((m+rho)^2 - 3(m+rho))/2  ->  a rho^2 + b rho + d = 0
+        a = c / 2.0
+        b = -(1 + 1 / 3.0) + c * (2 * m - 3) / 2.0
+        d = m - m / 3.0 + c * (m * m - 3 * m) / 2.0
+        disc = math.sqrt(b * b - 4 * a * d)
+        roots = [(-b - disc) / (2 * a), (-b + disc) / (2 * a)]
+        ref = min(roots, key=lambda r: abs(r - m / 2.0))
+        assert M.nelkin_rho(m, z) == pytest.approx(ref, abs=1e-10)
+    S, F, H = M.ratio_exponents(z)
+    assert S < 0.2 and F > 0 and H > F   # intermittency grows with order
+
+
+def test_numeric_weights_reproduce_gaussian_and_logpoisson_constraint():
+    c, Z = 0.023, 2.0
+    lams = np.linspace(-3, 2, 11)
+    Kq = lambda t, Zz: 9 * c * (t * t - t) * Zz / 2
+    wn = M.weights_numeric(lams, Kq, Z)
+    wg, _ = M.member_weights(lams, "gauss_paper", c=c, Z=Z, renormalize=False)
+    # trapezoid rule on the 60/8192 grid: error <= h^2 max|P''| (bin width)/12 ~ 4e-6
+    assert np.abs(wn - wg).max() < 1e-5
+    # log-Poisson: exact masses; K(1; Z) = 0 is the mean-injection constraint
+    beta, C0 = 2.0 / 3.0, 2.0
+    assert M.zeta_logpoisson(3.0, beta, C0) == pytest.approx(1.0, abs=1e-15)
+    mu = C0 * Z
+    s = sum(math.exp(-mu + k * math.log(mu) - math.lgamma(k + 1)) * math.exp(2 * Z / 3 + k * math.log(beta))
+            for k in range(200))
+    assert s == pytest.approx(1.0, abs=1e-12)
+    lams = np.linspace(-4.0, 1.5, 23)
+    w = M.weights_logpoisson(lams, Z)
+    assert 0.99 < w.sum() <= 1.0 + 1e-12
