@@ -103,15 +103,20 @@ def truncated_gauss_params(c, Z):
     return 0.5 * (lo + hi), sigma, Z
 
 
-def lambda_pdf_from_K(K, lam_grid):
+def lambda_pdf_from_K(K, lam_grid, atom=None):
     """Numerical inverse two-sided Laplace transform (Sec. VII): evaluate
     exp(K(i s)) (the characteristic function) and Fourier-transform it.
-    K must accept complex arguments.  Returns P on lam_grid (uniform)."""
+    K must accept complex arguments.  Returns P on lam_grid (uniform).
+    atom = (position, mass): a point mass known in closed form, removed from
+    the characteristic function before the transform (so that it does not
+    ring across the grid); the returned P is then the continuous part."""
     lam = np.asarray(lam_grid, dtype=np.float64)
     n = lam.size
     dl = lam[1] - lam[0]
     s = 2.0 * math.pi * np.fft.fftfreq(n, d=dl)
     phi = np.exp(np.array([K(1j * si) for si in s], dtype=np.complex128))
+    if atom is not None:
+        phi = phi - atom[1] * np.exp(1j * s * atom[0])
     # P(l_j) = 1/(2 pi) int ds exp(-i s l_j) phi(s)
     #        ~ (1/(n dl)) sum_k exp(-i s_k l_0) phi(s_k) exp(-2 pi i k j / n): a forward DFT
     P = np.real(np.fft.fft(phi * np.exp(-1j * s * lam[0]))) / (n * dl)
@@ -272,9 +277,25 @@ def scale_gap(lams, rlambda, R_ref):
 # general scaling exponents (Sec. III / Sec. VII): zeta families and weights
 # ---------------------------------------------------------------------------
 def zeta_logpoisson(p, beta=2.0 / 3.0, C0=2.0):
-    """Log-Poisson exponents zeta_p = p/9 + C0 (1 - beta^(p/3)) (a literature
-    parameterization the paper lists among the choices, Sec. III)."""
+    """Log-Poisson exponents, one of the literature parameterizations the
+    paper points to (Sec. III): zeta_p = p/9 + C0 (1 - beta^(p/3))."""
     return p / 9.0 + C0 * (1.0 - beta ** (p / 3.0))
+
+
+def zeta_rational(p, beta=0.05):
+    """Saturating rational exponents zeta_p = (1 + 3 beta) p / (3 (1 + beta p))
+    (Yakhot's mean-field form; zeta_3 = 1, zeta_p -> (1 + 3 beta)/(3 beta)).
+    A saturating family of the kind the paper inverts numerically (Sec. VII,
+    choice of zeta_p; Appendix, saturation gives lambda_max(Z) = Z)."""
+    return (1.0 + 3.0 * beta) * p / (3.0 * (1.0 + beta * p))
+
+
+def saturation_atom(zeta_inf, Z):
+    """Saturating exponents, zeta_p -> zeta_inf: K(t; Z) - t Z = -zeta_3t Z
+    tends to -zeta_inf Z as t -> infinity, so P(lambda; Z) holds a point mass
+    exp(-zeta_inf Z) at lambda_max = Z (the Appendix's saturation argument
+    carried one step further).  Returns (position, mass)."""
+    return Z, math.exp(-zeta_inf * Z)
 
 
 def nelkin_rho(m, zeta):
@@ -299,22 +320,28 @@ def ratio_exponents(zeta):
     return 2 * r[3] - 3 * r[2], 2 * r[4] - 4 * r[2], 2 * r[6] - 6 * r[2]
 
 
-def weights_numeric(lams, K, Z, grid_lo=-30.0, grid_hi=30.0, n=8192):
+LAMBDA_GRID = (-30.0, 30.0, 65536)     # lo, hi (exclusive), points
+
+
+def weights_numeric(lams, K, Z, grid_lo=LAMBDA_GRID[0], grid_hi=LAMBDA_GRID[1], n=LAMBDA_GRID[2], atom=None):
     """Member bin masses of the lambda distribution whose cumulant generating
     function is K(t; Z) (Sec. III, Eq. cumulant_generating_function), by the
     numerical inverse two-sided Laplace transform (Sec. VII) on a uniform
-    grid and trapezoid integration over each member's bin."""
+    grid and trapezoid integration over each member's bin.  atom =
+    (position, mass) of a known point mass: removed before the transform and
+    added to the bin that holds it (lo <= position < hi)."""
     grid = np.linspace(grid_lo, grid_hi, n, endpoint=False)
-    P = lambda_pdf_from_K(lambda t: K(t, Z), grid)
+    P = lambda_pdf_from_K(lambda t: K(t, Z), grid, atom)
     lo, hi, mult = lambda_bins(lams)
     w = np.zeros(len(lams))
     for i in range(len(lams)):
         a, b = max(lo[i], grid_lo), min(hi[i], grid[-1])
-        if b <= a:
-            continue
-        xs = np.concatenate(([a], grid[(grid > a) & (grid < b)], [b]))
-        ys = np.interp(xs, grid, P)
-        w[i] = np.trapezoid(ys, xs) / mult[i]
+        if b > a:
+            xs = np.concatenate(([a], grid[(grid > a) & (grid < b)], [b]))
+            ys = np.interp(xs, grid, P)
+            w[i] = np.trapezoid(ys, xs) / mult[i]
+        if atom is not None and lo[i] <= atom[0] < hi[i]:
+            w[i] += atom[1] / mult[i]
     return w
 
 

@@ -5,7 +5,8 @@ convolution property P(.; 2Z) = P(.; Z) * P(.; Z) (Sec. III), the printed
 bin mass 3.1e-6 of the member at lambda = 3.93 for R_lambda = 1300 with
 ens256 (Sec. VII), the printed cost ratio 7.8e4 (Sec. VI), Z = 0 giving the
 central member (Sec. VII), the truncated Gaussian of the Appendix, and the
-numerical inverse Laplace transform (Sec. VII) reproducing the Gaussian.
+numerical inverse Laplace transform (Sec. VII) reproducing the Gaussian
+and, for saturating exponents, the exact compound-Poisson law below.
 """
 import json
 import math
@@ -190,8 +191,8 @@ def test_numeric_weights_reproduce_gaussian_and_logpoisson_constraint():
     Kq = lambda t, Zz: 9 * c * (t * t - t) * Zz / 2
     wn = M.weights_numeric(lams, Kq, Z)
     wg, _ = M.member_weights(lams, "gauss_paper", c=c, Z=Z, renormalize=False)
-    # trapezoid rule on the 60/8192 grid: error <= h^2 max|P''| (bin width)/12 ~ 4e-6
-    assert np.abs(wn - wg).max() < 1e-5
+    # trapezoid rule on the 60/65536 grid: error <= h^2 max|P''| (bin width)/12 ~ 7e-8
+    assert np.abs(wn - wg).max() < 2e-7
     # log-Poisson: exact masses; K(1; Z) = 0 is the mean-injection constraint
     beta, C0 = 2.0 / 3.0, 2.0
     assert M.zeta_logpoisson(3.0, beta, C0) == pytest.approx(1.0, abs=1e-15)
@@ -202,3 +203,47 @@ def test_numeric_weights_reproduce_gaussian_and_logpoisson_constraint():
     lams = np.linspace(-4.0, 1.5, 23)
     w = M.weights_logpoisson(lams, Z)
     assert 0.99 < w.sum() <= 1.0 + 1e-12
+
+
+def _rational_exact(lams, Z, beta):
+    """Exact bin masses for zeta_p = (1+3b)p/(3(1+bp)).  K(t; Z) = Z t +
+    A Z (1/(1 + 3 b t) - 1), A = (1+3b)/(3b), is the cumulant generating
+    function of lambda = Z - 3 b G, G ~ Gamma(N, 1), N ~ Poisson(A Z) (G = 0
+    for N = 0): a closed form independent of any transform."""
+    from scipy.special import gammainc
+    A = (1 + 3 * beta) / (3 * beta)
+    mu = A * Z
+    lo, hi, mult = M.lambda_bins(lams)
+    w = np.zeros(len(lams))
+    for i in range(len(lams)):
+        g_hi = (Z - lo[i]) / (3 * beta)       # lambda >= lo  <=>  G <= g_hi
+        g_lo = (Z - hi[i]) / (3 * beta)
+        s = math.exp(-mu) if lo[i] <= Z < hi[i] else 0.0
+        for N in range(1, int(mu + 40 * math.sqrt(mu) + 60)):
+            pN = math.exp(-mu + N * math.log(mu) - math.lgamma(N + 1))
+            F = lambda g: gammainc(N, g) if g > 0 else 0.0
+            s += pN * (F(g_hi) - F(g_lo))
+        w[i] = s / mult[i]
+    return w
+
+
+@pytest.mark.parametrize("Z", [0.5, 2.0, 4.5])
+def test_rational_numeric_inversion_matches_compound_poisson(Z):
+    beta = 0.05
+    A = (1 + 3 * beta) / (3 * beta)
+    zeta = lambda p: M.zeta_rational(p, beta)
+    assert zeta(3.0) == pytest.approx(1.0, abs=1e-15)
+    assert zeta(1e12) == pytest.approx(A, rel=1e-10)
+    lams = np.linspace(-3, 3, 64)
+    atom = M.saturation_atom(A, Z)
+    w = M.weights_numeric(lams, lambda t, Zz: (t - zeta(3 * t)) * Zz, Z, atom=atom)
+    ref = _rational_exact(lams, Z, beta)
+    # the continuous part jumps by J = e^{-AZ} A Z / (3 beta) at lambda = Z;
+    # its Gibbs residual in a bin mass stays below 2e-3 J dl
+    dl = 60.0 / 65536
+    J = math.exp(-A * Z) * A * Z / (3 * beta)
+    assert np.abs(w - ref).max() < max(2e-3 * J * dl, 1e-8)
+    # saturation: no mass above lambda_max = Z (Appendix)
+    grid = np.linspace(-30, 30, 65536, endpoint=False)
+    P = M.lambda_pdf_from_K(lambda t: (t - zeta(3 * t)) * Z, grid, atom)
+    assert abs(P[grid > Z + 0.05].sum() * dl) < max(2e-3 * J * dl, 1e-12)
