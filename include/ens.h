@@ -226,6 +226,72 @@ ens_status ens_mixture_host_noalloc(int n, const double *lambdas, const uint64_t
                                     const ens_hist_spec *hist, const ens_weight_spec *w, ens_mixture_out *out,
                                     void *stream);
 
+/* ---- scaling-exponent theory (Secs. III, V, VII) ----------------------- */
+
+/* Inertial-range exponent families zeta_p:
+ *   ENS_ZETA_QUADRATIC  zeta_p = p/3 - c (p^2 - 3p)/2 (Sec. IV, Eq.
+ *                       quadratic_scaling_exponents; Gaussian lambda); c >= 0
+ *   ENS_ZETA_LOGPOISSON zeta_p = p/9 + C0 (1 - beta^(p/3)) (a literature
+ *                       parameterization of the kind listed in Sec. III;
+ *                       beta = 2/3, C0 = 2 give zeta_3 = 1); 0 < beta < 1,
+ *                       C0 > 0
+ *   ENS_ZETA_RATIONAL   zeta_p = (1 + 3 beta) p / (3 (1 + beta p)) (Yakhot's
+ *                       saturating mean-field form, beta ~ 0.05; the kind of
+ *                       saturating exponents Sec. VII inverts numerically);
+ *                       beta > 0
+ * The cumulant generating function of lambda is K(t; Z) = (t - zeta_3t) Z
+ * (Sec. III, Eq. exponents_KZ_1). */
+typedef enum { ENS_ZETA_QUADRATIC = 0, ENS_ZETA_LOGPOISSON = 1, ENS_ZETA_RATIONAL = 2 } ens_zeta_kind;
+typedef struct {
+    int kind;
+    double c;     /* quadratic */
+    double beta;  /* log-Poisson and rational */
+    double C0;    /* log-Poisson */
+} ens_zeta_spec;
+
+/* Uniform lambda grid of the numerical inversion: ENS_LAMBDA_GRID points
+ * lambda_j = LO + j (HI - LO) / ENS_LAMBDA_GRID, j = 0 .. GRID-1. */
+#define ENS_LAMBDA_GRID 65536
+#define ENS_LAMBDA_GRID_LO (-30.0)
+#define ENS_LAMBDA_GRID_HI 30.0
+
+/* P(lambda; Z) on the grid above (host array of ENS_LAMBDA_GRID doubles) by
+ * the numerical inverse two-sided Laplace transform of exp K (Sec. VII):
+ * exp K(i s) sampled at the grid's conjugate frequencies, then an FP64 FFT
+ * on the device.  Saturating exponents (zeta_p -> zeta_inf) give P a point
+ * mass exp(-zeta_inf Z) at lambda_max = Z (Appendix, saturation): it is
+ * removed from exp K before the transform, and the returned P is the
+ * continuous part.  Quadratic and rational families (log-Poisson lambda is
+ * a lattice: ENS_EINVAL).  Z > 0.  Synchronises `stream` (NULL: legacy
+ * default stream). */
+ens_status ens_lambda_pdf(const ens_zeta_spec *zeta, double Z, double *pdf, void *stream);
+/* Member weights w_i (host arrays of n doubles) for the lambda distribution
+ * of `zeta` at scale gap Z > 0: the mass of P(lambda; Z) in each member's
+ * lambda bin (bin edges halfway between neighbouring distinct lambdas, the
+ * outer bins as wide as their inner half; a shared lambda value splits its
+ * bin's mass equally).  Quadratic and rational families: trapezoid
+ * integral of ens_lambda_pdf over the bin, bin ends interpolated linearly,
+ * clipped to the grid, plus the point mass at lambda = Z of the rational
+ * family in the bin that holds it (lo <= Z < hi).  Log-Poisson: exact, lambda = 2Z/3 + k ln(beta) with
+ * k ~ Poisson(C0 Z), k < 400.  Not renormalised; *covered (may be NULL) is
+ * their sum.  Pass the result to ens_mixture as ENS_W_USER weights.
+ * Synchronises `stream`.  ENS_EINVAL for non-finite inputs or parameters
+ * outside the family's range. */
+ens_status ens_lambda_weights(const ens_zeta_spec *zeta, double Z, int n, const double *lambdas, double *weights,
+                              double *covered, void *stream);
+/* Gradient-moment exponents rho_m = m - zeta_{m + rho_m} (Sec. III, Eq.
+ * nelkin_rhom) for nm orders m; FP64 bisection (host). */
+ens_status ens_nelkin_exponents(const ens_zeta_spec *zeta, int nm, const double *m, double *rho);
+/* Predicted R_lambda exponents of skewness, flatness and hyper-flatness of
+ * the gradient components (Sec. VII): 2rho3 - 3rho2, 2rho4 - 4rho2,
+ * 2rho6 - 6rho2; out holds 3 doubles. */
+ens_status ens_ratio_exponents(const ens_zeta_spec *zeta, double *out);
+/* Scale gap for a target R_lambda (Sec. V): fit ln R_lambda = ln R0 +
+ * lambda/6 over the members with lambda >= 0 (constant C_eps, Eq.
+ * Re_definition), then Z = 1.5 ln(R_ref / R0) (Eq. Rlambda_Z_relation).
+ * Host arithmetic; R0 may be NULL. */
+ens_status ens_scale_gap(int n, const double *lambdas, const double *rlambda, double R_ref, double *Z, double *R0);
+
 /* ---- state access ------------------------------------------------------ */
 
 /* Member spectral field <-> host full layout (FP64; converted from/to the

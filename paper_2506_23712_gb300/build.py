@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libens.so")
-SOURCES = ["ens_kernels.cu", "ens_api.cu", "ens_noalloc.cu", "ens_surrogate.cu"]
+SOURCES = ["ens_kernels.cu", "ens_api.cu", "ens_noalloc.cu", "ens_surrogate.cu", "ens_theory.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-diag-suppress", "177",
          "-I", os.path.join(ROOT, "include")]

@@ -64,6 +64,14 @@ class MixtureOut(ctypes.Structure):
                 ("ratios", ctypes.c_double * 5)]
 
 
+ENS_ZETA_QUADRATIC, ENS_ZETA_LOGPOISSON, ENS_ZETA_RATIONAL = 0, 1, 2
+ENS_LAMBDA_GRID, ENS_LAMBDA_GRID_LO, ENS_LAMBDA_GRID_HI = 65536, -30.0, 30.0
+
+
+class ZetaSpec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("c", ctypes.c_double), ("beta", ctypes.c_double), ("C0", ctypes.c_double)]
+
+
 # every symbol declared in include/ens.h: (name, restype, argtypes)
 _P = ctypes.POINTER
 _vp, _i, _d, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
@@ -82,6 +90,11 @@ SIGNATURES = [
     ("ens_mixture", _i, [_vp, _P(WeightSpec), _P(MixtureOut)]),
     ("ens_mixture_host", _i, [_i, _vp, _vp, _vp, _P(HistSpec), _P(WeightSpec), _P(MixtureOut), _vp]),
     ("ens_mixture_host_noalloc", _i, [_i, _vp, _vp, _vp, _P(HistSpec), _P(WeightSpec), _P(MixtureOut), _vp]),
+    ("ens_lambda_pdf", _i, [_P(ZetaSpec), _d, _vp, _vp]),
+    ("ens_lambda_weights", _i, [_P(ZetaSpec), _d, _i, _vp, _vp, _P(_d), _vp]),
+    ("ens_nelkin_exponents", _i, [_P(ZetaSpec), _i, _vp, _vp]),
+    ("ens_ratio_exponents", _i, [_P(ZetaSpec), _vp]),
+    ("ens_scale_gap", _i, [_i, _vp, _vp, _d, _P(_d), _P(_d)]),
     ("ens_get_field", _i, [_vp, _i, _vp]),
     ("ens_set_field", _i, [_vp, _i, _vp]),
     ("ens_state_bytes", _sz, [_vp]),
@@ -261,6 +274,67 @@ def ens_mixture_host_noalloc(lambdas, counts, moments, hist, stream_ptr=None, **
     _check(lib().ens_mixture_host_noalloc(n, _ptr(lam), _ptr(counts), _ptr(moments), ctypes.byref(hist),
                                           ctypes.byref(ws), ctypes.byref(out), stream_ptr))
     return _mixture_result(out, bufs, hist)
+
+
+def zeta_spec(kind="quadratic", c=0.023, beta=None, C0=2.0) -> ZetaSpec:
+    """zeta_p family: 'quadratic' (c), 'logpoisson' (beta, default 2/3; C0)
+    or 'rational' (beta, default 0.05)."""
+    z = ZetaSpec()
+    z.kind = {"quadratic": ENS_ZETA_QUADRATIC, "logpoisson": ENS_ZETA_LOGPOISSON,
+              "rational": ENS_ZETA_RATIONAL}[kind]
+    if beta is None:
+        beta = 0.05 if kind == "rational" else 2.0 / 3.0
+    z.c, z.beta, z.C0 = c, beta, C0
+    return z
+
+
+def lambda_grid() -> np.ndarray:
+    return ENS_LAMBDA_GRID_LO + np.arange(ENS_LAMBDA_GRID) * (
+        (ENS_LAMBDA_GRID_HI - ENS_LAMBDA_GRID_LO) / ENS_LAMBDA_GRID)
+
+
+def ens_lambda_pdf(zeta: ZetaSpec, Z: float, stream_ptr=None) -> np.ndarray:
+    out = np.empty(ENS_LAMBDA_GRID, dtype=np.float64)
+    if stream_ptr is None:
+        stream_ptr = _stream_ptr()
+    _check(lib().ens_lambda_pdf(ctypes.byref(zeta), Z, _ptr(out), stream_ptr))
+    return out
+
+
+def ens_lambda_weights(zeta: ZetaSpec, Z: float, lambdas, stream_ptr=None):
+    """(weights, covered) of the members for the lambda law of `zeta` at Z."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    w = np.empty(lam.size, dtype=np.float64)
+    cov = ctypes.c_double()
+    if stream_ptr is None:
+        stream_ptr = _stream_ptr()
+    _check(lib().ens_lambda_weights(ctypes.byref(zeta), Z, lam.size, _ptr(lam), _ptr(w), ctypes.byref(cov),
+                                    stream_ptr))
+    return w, cov.value
+
+
+def ens_nelkin_exponents(zeta: ZetaSpec, m) -> np.ndarray:
+    mm = np.ascontiguousarray(m, dtype=np.float64)
+    rho = np.empty(mm.size, dtype=np.float64)
+    _check(lib().ens_nelkin_exponents(ctypes.byref(zeta), mm.size, _ptr(mm), _ptr(rho)))
+    return rho
+
+
+def ens_ratio_exponents(zeta: ZetaSpec):
+    out = np.empty(3, dtype=np.float64)
+    _check(lib().ens_ratio_exponents(ctypes.byref(zeta), _ptr(out)))
+    return tuple(out)
+
+
+def ens_scale_gap(lambdas, rlambda, R_ref):
+    """(Z, R0) for a target R_lambda from the members' R_lambda."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    r = np.ascontiguousarray(rlambda, dtype=np.float64)
+    if r.size != lam.size:
+        raise ValueError("one R_lambda per member")
+    Z, R0 = ctypes.c_double(), ctypes.c_double()
+    _check(lib().ens_scale_gap(lam.size, _ptr(lam), _ptr(r), R_ref, ctypes.byref(Z), ctypes.byref(R0)))
+    return Z.value, R0.value
 
 
 def _full_shape(N):
