@@ -63,7 +63,7 @@ class _HistSpec(ctypes.Structure):
     _fields_ = [("qr_bins", ctypes.c_int), ("q_lim", ctypes.c_double), ("r_lim", ctypes.c_double),
                 ("tail_bins", ctypes.c_int), ("tail_lo", ctypes.c_double),
                 ("tail_hi", ctypes.c_double), ("eps_norm", ctypes.c_double),
-                ("nu_norm", ctypes.c_double)]
+                ("nu_norm", ctypes.c_double), ("grad_bins", ctypes.c_int), ("grad_lim", ctypes.c_double)]
 
 
 def lib():
@@ -135,14 +135,17 @@ class HistSpec:
     tail_hi: float = 8.0
     eps_norm: float = 0.1
     nu_norm: float = 0.02
+    grad_bins: int = 0
+    grad_lim: float = 40.0
 
     def _c(self) -> _HistSpec:
         return _HistSpec(self.qr_bins, self.q_lim, self.r_lim, self.tail_bins, self.tail_lo,
-                         self.tail_hi, self.eps_norm, self.nu_norm)
+                         self.tail_hi, self.eps_norm, self.nu_norm, self.grad_bins, self.grad_lim)
 
     @property
     def counts_len(self) -> int:
-        return self.qr_bins ** 2 + 2 * self.tail_bins + 8
+        g = 2 * self.grad_bins + 4 if self.grad_bins > 0 else 0
+        return self.qr_bins ** 2 + 2 * self.tail_bins + 8 + g
 
 
 # ---------------------------------------------------------------------------
@@ -268,5 +271,14 @@ def split_counts(counts: np.ndarray, h: HistSpec):
     qr = counts[: nq * nq].reshape(nq, nq)
     e = counts[nq * nq: nq * nq + nt]
     w = counts[nq * nq + nt: nq * nq + 2 * nt]
-    c = counts[nq * nq + 2 * nt:]
+    c = counts[nq * nq + 2 * nt: nq * nq + 2 * nt + 8]
     return qr, e, w, c
+
+
+def split_grad_counts(counts: np.ndarray, h: HistSpec):
+    """View the gradient-component part of a counts vector as (longitudinal
+    [ng], transverse [ng], counters [4]: long_under, long_over, trans_under,
+    trans_over)."""
+    off = h.qr_bins ** 2 + 2 * h.tail_bins + 8
+    ng = h.grad_bins
+    return counts[off: off + ng], counts[off + ng: off + 2 * ng], counts[off + 2 * ng: off + 2 * ng + 4]

@@ -203,6 +203,22 @@ def mix_counts(counts, weights, h):
     return qr, e, w
 
 
+def mix_gradient_pdfs(counts, weights, h):
+    """Mixed PDFs of the longitudinal and transverse gradient components
+    (Sec. VI, gradient PDFs; Sec. II, Eq. pdf_superposition, discretised) in
+    units of A/sqrt(q0): every grid point contributes 3 longitudinal and 6
+    transverse samples, so PDF(b) = sum_i w_i h_i(b) / (k n_i db), k = 3, 6."""
+    counts = np.asarray(counts, dtype=np.float64)
+    nq, nt, ng = h.qr_bins, h.tail_bins, h.grad_bins
+    off = nq * nq + 2 * nt
+    npts = counts[:, off + 6]
+    db = 2.0 * h.grad_lim / ng
+    w = np.asarray(weights, dtype=np.float64)[:, None]
+    lon = (w * counts[:, off + 8: off + 8 + ng] / npts[:, None]).sum(axis=0) / (3.0 * db)
+    tra = (w * counts[:, off + 8 + ng: off + 8 + 2 * ng] / npts[:, None]).sum(axis=0) / (6.0 * db)
+    return lon, tra
+
+
 def mix_moments(moments, npoints, weights):
     """<X^p>_mix = sum_i w_i <X^p>_i (Sec. II, Eq. ensemble_hypothesis with X a power)."""
     moments = np.asarray(moments, dtype=np.float64)

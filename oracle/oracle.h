@@ -99,11 +99,16 @@ typedef struct {
     double tail_hi;
     double eps_norm;  /* eps_bar of the normalisation */
     double nu_norm;   /* nu of the normalisation */
+    int grad_bins;    /* bins of each gradient-component histogram (0: none) */
+    double grad_lim;  /* A_ij / sqrt(q0) in [-grad_lim, grad_lim) */
 } or_hist_spec;
 
 /* Counts layout: [qr_bins^2 | tail_bins (dissipation) | tail_bins
  * (enstrophy) | 8 counters], counters = {qr_out, eps_under, eps_over,
- * ens_under, ens_over, nonfinite, npoints, 0}. */
+ * ens_under, ens_over, nonfinite, npoints, 0}; with grad_bins > 0 followed
+ * by [grad_bins (longitudinal A_11, A_22, A_33 pooled) | grad_bins
+ * (transverse A_ij, i != j, pooled) | 4 counters: long_under, long_over,
+ * trans_under, trans_over]. */
 int or_counts_len(const or_hist_spec *h);
 #define OR_NMOM 48
 /* Velocity-gradient fields A_ij = d_j u_i (9 physical fields, row-major ij). */

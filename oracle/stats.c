@@ -9,7 +9,10 @@
  * member whose mean dissipation equals eps_norm (the paper plots the QR-PDF
  * in units of <Tr S^2>, Sec. VI).  Q axis: Q/q0, R axis: R/q0^(3/2);
  * dissipation axis: eps/eps_norm; enstrophy axis: omega^2 nu_norm/eps_norm,
- * both on log10 bins.
+ * both on log10 bins.  Gradient components (Sec. VI, longitudinal and
+ * transverse gradient PDFs): A_ij / sqrt(q0) on a linear axis, the three
+ * longitudinal components pooled in one histogram and the six transverse
+ * ones in another (isotropy).
  * [R] Bin rule: the edges are formed in FP64 and rounded to FP32; a value is
  * rounded to FP32 and lands in bin b iff edge[b] <= value < edge[b+1].
  * Values below the first edge count as underflow, at or above the last edge
@@ -23,7 +26,10 @@
 #include <stdlib.h>
 #include <string.h>
 
-int or_counts_len(const or_hist_spec *h) { return h->qr_bins * h->qr_bins + 2 * h->tail_bins + 8; }
+int or_counts_len(const or_hist_spec *h)
+{
+    return h->qr_bins * h->qr_bins + 2 * h->tail_bins + 8 + (h->grad_bins > 0 ? 2 * h->grad_bins + 4 : 0);
+}
 
 static int wavenumber(int i, int N) { return i <= N / 2 ? i : i - N; }
 
@@ -116,6 +122,14 @@ void or_gradient_stats(const double *uh, int N, double nu, const or_hist_spec *h
     const double q0 = h->eps_norm / (2.0 * h->nu_norm);
     const double r0 = pow(q0, 1.5);
     uint64_t *qr = counts, *he = counts + nq * nq, *hw = he + nt, *ctr = hw + nt;
+    const int ng = h->grad_bins;
+    float *eg = NULL;
+    if (ng > 0) {
+        eg = (float *)malloc(sizeof(float) * (ng + 1));
+        linear_edges(-h->grad_lim, h->grad_lim, ng, eg);
+    }
+    uint64_t *hl = ctr + 8, *ht = hl + ng, *gctr = ht + ng;
+    const double g0 = sqrt(q0);
 
     for (long p = 0; p < n3; ++p) {
         const double vals[4] = {Q[p] / q0, R[p] / r0, eps[p] / h->eps_norm, ens[p] * h->nu_norm / h->eps_norm};
@@ -134,7 +148,17 @@ void or_gradient_stats(const double *uh, int N, double nu, const or_hist_spec *h
             else if (b >= nt) ctr[2 + 2 * t] += 1;
             else hist[b] += 1;
         }
+        /* gradient components: c = 3 i + j, longitudinal iff i == j */
+        for (int c = 0; ng > 0 && c < 9; ++c) {
+            const int lon = c % 4 == 0;
+            const int b = find_bin((float)(A[(long)c * n3 + p] / g0), eg, ng);
+            uint64_t *hist = lon ? hl : ht;
+            if (b < 0) gctr[lon ? 0 : 2] += 1;
+            else if (b >= ng) gctr[lon ? 1 : 3] += 1;
+            else hist[b] += 1;
+        }
     }
+    free(eg);
     /* moments: sum A_c^p, p in {2,3,4,6}, c row-major; then sums of
      * Q, R, eps, omega^2, Q^2, R^2, eps^2, omega^4 */
     for (long p = 0; p < n3; ++p) {

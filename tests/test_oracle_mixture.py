@@ -131,6 +131,31 @@ def test_mixture_of_counts():
     assert np.allclose(qr1.ravel(), counts[1, :16] / npts[1], rtol=1e-15)
 
 
+def test_gradient_pdf_mixture():
+    """Mixed gradient-component PDFs integrate to the mixed in-range
+    fractions (3 and 6 samples per point), and one member with weight 1
+    gives its own normalised histogram."""
+    h = O.HistSpec(qr_bins=2, tail_bins=2, grad_bins=5, grad_lim=2.5)
+    L = h.counts_len
+    off = 4 + 4
+    rng = np.random.default_rng(1)
+    counts = np.zeros((3, L), dtype=np.uint64)
+    npts = np.array([1000, 2000, 1500])
+    for i in range(3):
+        counts[i, off + 6] = npts[i]
+        counts[i, off + 8: off + 13] = rng.multinomial(3 * npts[i] - 7, np.ones(5) / 5)
+        counts[i, off + 13: off + 18] = rng.multinomial(6 * npts[i] - 11, np.ones(5) / 5)
+    w = np.array([0.2, 0.5, 0.3])
+    lon, tra = M.mix_gradient_pdfs(counts, w, h)
+    db = 1.0
+    frac_l = (w * counts[:, off + 8: off + 13].sum(axis=1) / (3 * npts)).sum()
+    frac_t = (w * counts[:, off + 13: off + 18].sum(axis=1) / (6 * npts)).sum()
+    assert lon.sum() * db == pytest.approx(frac_l, rel=1e-14)
+    assert tra.sum() * db == pytest.approx(frac_t, rel=1e-14)
+    l1, _ = M.mix_gradient_pdfs(counts[1:2], np.array([1.0]), h)
+    assert np.allclose(l1, counts[1, off + 8: off + 13] / (3.0 * npts[1]), rtol=1e-15)
+
+
 def test_moment_ratios_of_gaussian_components():
     """Gaussian gradient components: S = 0, F = 3, H = 15."""
     mixed = np.zeros(48)

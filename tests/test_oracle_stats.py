@@ -116,6 +116,35 @@ def test_histograms_against_brute_force():
     assert mom[43] == pytest.approx((ens ** 2).sum(), rel=1e-13)
 
 
+def test_gradient_component_histograms_against_brute_force():
+    """Longitudinal (A_11, A_22, A_33) and transverse (A_ij, i != j)
+    components pooled, in units of sqrt(q0), against independent binning;
+    every point contributes 3 + 6 samples."""
+    N = 8
+    m = O.Member(N=N, nu=0.05, seed=9, init_energy=3.0)
+    uh = O.initial_field(m)
+    h = O.HistSpec(qr_bins=8, q_lim=4.0, r_lim=4.0, tail_bins=16, tail_lo=-3.0, tail_hi=2.0,
+                   eps_norm=0.1, nu_norm=0.05, grad_bins=24, grad_lim=3.0)
+    assert h.counts_len == 64 + 32 + 8 + 48 + 4
+    counts, _ = O.gradient_stats(uh, m.nu, h)
+    lon, tra, gc = O.split_grad_counts(counts, h)
+    A = O.gradient(uh)
+    g0 = np.sqrt(h.eps_norm / (2 * h.nu_norm))
+    eg = np.array([np.float32(-3.0 + 6.0 * b / 24) for b in range(25)], dtype=np.float32)
+    for comps, hist, cu, co in (([(0, 0), (1, 1), (2, 2)], lon, gc[0], gc[1]),
+                                ([(0, 1), (0, 2), (1, 0), (1, 2), (2, 0), (2, 1)], tra, gc[2], gc[3])):
+        b = np.concatenate([brute_bins((A[i, j] / g0).ravel(), eg) for i, j in comps])
+        inr = (b >= 0) & (b < 24)
+        assert np.array_equal(hist.astype(np.int64), np.bincount(b[inr], minlength=24))
+        assert cu == np.count_nonzero(b < 0) and co == np.count_nonzero(b >= 24)
+        assert hist.sum() + cu + co == len(comps) * N ** 3
+    # the first part of the layout is unchanged by the gradient histograms
+    h0 = O.HistSpec(qr_bins=8, q_lim=4.0, r_lim=4.0, tail_bins=16, tail_lo=-3.0, tail_hi=2.0,
+                    eps_norm=0.1, nu_norm=0.05)
+    c0, _ = O.gradient_stats(uh, m.nu, h0)
+    assert np.array_equal(c0, counts[: h0.counts_len])
+
+
 def test_log_histogram_underflow_for_zero():
     """A field at rest has eps = omega^2 = 0: every point is underflow."""
     N = 4
