@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-uneven", action="store_true")
     p.add_argument("--no-surrogate", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="keep the default pass variants")
     return p.parse_args()
 
 
@@ -290,7 +291,7 @@ def measured_bf16():
     return 1900.0, "fallback"
 
 
-def measure_uneven(E, torch, steps=3):
+def measure_uneven(E, torch, steps=3, tune=True):
     """Uneven-size batch (24 x 128^3, 12 x 256^3, 4 x 384^3): all members in
     one graph per step (one branch per grid size) vs member-by-member
     launches of the same kernels."""
@@ -302,6 +303,8 @@ def measure_uneven(E, torch, steps=3):
     ens = E.Ensemble(ms, hist=E.hist_spec(nu_norm=ms[0].nu), stream=stream)
     out = {"workload": "24 x 128^3 + 12 x 256^3 + 4 x 384^3, IF-RK3, CFL 0.2, k_max eta >= 1.5",
            "members": len(ms), "steps": steps}
+    if tune:
+        out["tuning"] = ens.autotune(steps=2)
     for mode in ("batched", "sequential"):
         run = (lambda k: ens.step(k)) if mode == "batched" else (lambda k: E.ens_step_sequential(ens.ctx, k))
         run(1)
@@ -364,6 +367,9 @@ def main():
     stream = torch.cuda.current_stream()
     ens = E.Ensemble(descs, hist=hist, stream=stream)
     n_mem = len(descs)
+    # pass variants picked by the library's autotuner on these members (the
+    # member state is restored afterwards; untimed)
+    tuning = None if args.no_tune else ens.autotune(steps=2)
     kps = E.ens_kernels_per_step(ens.ctx)
 
     def barrier():
@@ -457,7 +463,7 @@ def main():
     ens.close()
     uneven = None
     if not args.no_uneven and rank == 0:
-        uneven = measure_uneven(E, torch)
+        uneven = measure_uneven(E, torch, tune=not args.no_tune)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -469,6 +475,7 @@ def main():
                                state_gb, step_bytes / 1e9),
                            "parallelism": "replicas per GPU" if world > 1 else "single GPU",
                            "step_hbm_roofline_frac": round(step_frac, 4),
+                           "tuning": tuning,
                            "flagged_members": flagged},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kps * args.steps,
                 "clocks": clk, "plain": plain, "passes": passes, "uneven_batch": uneven,

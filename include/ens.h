@@ -86,12 +86,20 @@ typedef struct {
     double tail_hi;
     double eps_norm;    /* normalising injection rate */
     double nu_norm;     /* normalising viscosity */
+    int grad_bins;      /* bins of each gradient-component histogram, 0..2048 (0: none) */
+    double grad_lim;    /* A_ij / sqrt(q0) in [-grad_lim, grad_lim) */
 } ens_hist_spec;
 
 /* Per-member counts vector layout (uint64):
  *   [qr_bins*qr_bins | tail_bins (dissipation) | tail_bins (enstrophy) |
  *    8 counters: qr_out, eps_under, eps_over, ens_under, ens_over,
  *                nonfinite, npoints, 0]
+ * and, with grad_bins > 0 (gradient-component PDFs, Sec. VI):
+ *   [grad_bins (longitudinal A_11, A_22, A_33 pooled) |
+ *    grad_bins (transverse A_ij, i != j, pooled) |
+ *    4 counters: long_under, long_over, trans_under, trans_over]
+ * (3 longitudinal and 6 transverse samples per finite grid point; the
+ * mixture divides by 3 n and 6 n.)  ens_counts_len gives the total.
  * Moments (48 doubles per member): sums over points of A_c^p for the nine
  * components c (row-major A_ij = d_j u_i) and p = 2, 3, 4, 6 (index 4c + k),
  * then sums of Q, R, eps, omega^2, Q^2, R^2, eps^2, omega^4, then 4 zeros. */
@@ -140,6 +148,8 @@ typedef struct {
     double *pdf_ens;     /* [tail_bins] PDF of log10(omega^2 nu_norm/eps_norm) */
     double *moments;     /* [ENS_NMOM] mixed per-point averages */
     double ratios[5];    /* S_long, F_long, F_trans, H_long, H_trans */
+    double *pdf_long;    /* [grad_bins] PDF of longitudinal A_ii / sqrt(q0) (may be NULL) */
+    double *pdf_trans;   /* [grad_bins] PDF of transverse A_ij / sqrt(q0), i != j (may be NULL) */
 } ens_mixture_out;
 
 /* ---- context ---------------------------------------------------------- */
@@ -175,6 +185,52 @@ ens_status ens_step_nograph(ens_ctx *ctx, int nsteps);
 /* Same results, launched the slow way for comparison: one member at a time,
  * every pass of every member a separate launch on the context stream. */
 ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
+
+/* ---- autotuning (no counterpart in the paper: launch shapes of this
+ * library's kernels) ------------------------------------------------------ */
+
+/* Per grid-size group: the variants of the stage passes.
+ *   tile_x, tile_y  columns per CTA of the x / y FFT passes (8 or 16);
+ *   z_variant       0: persistent TMA-pipelined z pass with z_ctas_per_sm
+ *                   CTAs per SM (1 .. the kernel's occupancy limit),
+ *                   1: one CTA per group of rows (z_ctas_per_sm unused
+ *                   but kept, and checked, for a switch back to 0).
+ * Every variant computes the same transforms; the FP64 energy sums of the
+ * update pass are accumulated over tile_x-dependent CTA partials, so
+ * changing tile_x changes their rounding order (fields agree to FP32
+ * rounding, not bit for bit). */
+#define ENS_MAX_GROUPS 8
+typedef struct {
+    int N;               /* grid size (read-only: must match the context) */
+    int tile_x, tile_y;
+    int z_variant;
+    int z_ctas_per_sm;
+} ens_group_tuning;
+typedef struct {
+    int groups;          /* number of grid-size groups (read-only) */
+    int parallel_groups; /* 1: groups as parallel graph branches; 0: one chain */
+    ens_group_tuning group[ENS_MAX_GROUPS];   /* ascending N */
+    double ms_per_step;  /* ens_autotune: mean step time of the winner, else 0 */
+    int trials;          /* ens_autotune: configurations timed */
+} ens_tuning;
+/* Current tuning (defaults at creation: tiles 16, persistent z pass at its
+ * occupancy limit, parallel groups). */
+ens_status ens_get_tuning(const ens_ctx *ctx, ens_tuning *out);
+/* Install a tuning (for instance one cached from an earlier ens_autotune on
+ * the same device and member set).  ENS_EINVAL (not sticky, previous tuning
+ * kept) if a field is out of range or the groups do not match.  Synchronises;
+ * the next ens_step captures a new graph. */
+ens_status ens_set_tuning(ens_ctx *ctx, const ens_tuning *t);
+/* Time the variants on this context's own members and install the fastest:
+ * coordinate descent over tile_x, tile_y, the z variant and its CTAs per SM
+ * for each group, then parallel_groups; each trial restores the member
+ * state from a device snapshot, runs one untimed step and times `steps`
+ * graph replays with CUDA events; a candidate wins only if it is more than
+ * 1% faster.  The member state is restored afterwards (the simulation does
+ * not advance).  Needs device memory for one copy of the spectral state
+ * (ENS_ENOMEM otherwise, context unchanged).  out (may be NULL) receives
+ * the installed tuning with ms_per_step and trials. */
+ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out);
 
 /* ---- statistics (Secs. V-VII) ---------------------------------------- */
 

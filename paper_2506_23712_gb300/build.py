@@ -19,6 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libens.so")
 SOURCES = ["ens_kernels.cu", "ens_api.cu", "ens_noalloc.cu", "ens_surrogate.cu", "ens_theory.cu"]
+# the FFT passes of each grid size compile in their own translation unit
+SIZED = "ens_sized.cu"
+SIZES = [16, 32, 64, 128, 256, 384, 512]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-diag-suppress", "177",
          "-I", os.path.join(ROOT, "include")]
@@ -51,9 +54,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(job):
+        src, defs, obj = job
+        obj = os.path.join(BUILD, obj)
+        cmd = [cc] + ARCH + FLAGS + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s" % (src, r.stderr))
@@ -61,8 +65,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    jobs = [(SIZED, ["-DENS_N=%d" % n], "ens_sized_%d.o" % n) for n in reversed(SIZES)]
+    jobs += [(src, [], src.replace(".cu", ".o")) for src in SOURCES]
+    with ThreadPoolExecutor(max_workers=min(len(jobs), max(2, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(compile_one, jobs))
     tmp = LIB + ".tmp"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)

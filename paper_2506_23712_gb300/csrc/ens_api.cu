@@ -63,6 +63,8 @@ struct ens_ctx {
     double *mix = nullptr;       // mixture scratch
     cudaGraphExec_t graph = nullptr;
     int rk = 3;
+    int sms = 0;                 // streaming multiprocessors of the device
+    int parallel_groups = 1;     // grid-size groups as parallel graph branches
     ens_status sticky = ENS_OK;
     std::string err;
 };
@@ -89,6 +91,20 @@ ens_status cuda_fail(ens_ctx *ctx, const char *what, cudaError_t e)
         if (_e != cudaSuccess) return cuda_fail(ctx, #call, _e); \
     } while (0)
 
+ens_status validate_hist(const ens_hist_spec *h, std::string &why)
+{
+    if (h->qr_bins < 1 || h->qr_bins > 256 || h->tail_bins < 1 || h->tail_bins > 4096) { why = "histogram bins out of range"; return ENS_EINVAL; }
+    if (h->grad_bins < 0 || h->grad_bins > 2048 || (h->grad_bins > 0 && !(h->grad_lim > 0 && std::isfinite(h->grad_lim)))) {
+        why = "gradient-component histogram: 0 <= grad_bins <= 2048 and grad_lim > 0";
+        return ENS_EINVAL;
+    }
+    if (!(h->q_lim > 0) || !(h->r_lim > 0) || !(h->tail_hi > h->tail_lo) || !(h->eps_norm > 0) || !(h->nu_norm > 0)) {
+        why = "invalid histogram ranges or normalisation";
+        return ENS_EINVAL;
+    }
+    return ENS_OK;
+}
+
 ens_status validate(const ens_member_desc *m, int n, const ens_hist_spec *h, std::string &why)
 {
     if (!m || n <= 0) { why = "no members"; return ENS_EINVAL; }
@@ -114,12 +130,7 @@ ens_status validate(const ens_member_desc *m, int n, const ens_hist_spec *h, std
         if (!(d.dt > 0.0) && !(d.cfl > 0.0)) { snprintf(buf, sizeof buf, "member %d: need dt > 0 or cfl > 0", i); why = buf; return ENS_EINVAL; }
         if (!(d.init_energy > 0.0)) { snprintf(buf, sizeof buf, "member %d: init_energy must be > 0", i); why = buf; return ENS_EINVAL; }
     }
-    if (h->qr_bins < 1 || h->qr_bins > 256 || h->tail_bins < 1 || h->tail_bins > 4096) { why = "histogram bins out of range"; return ENS_EINVAL; }
-    if (!(h->q_lim > 0) || !(h->r_lim > 0) || !(h->tail_hi > h->tail_lo) || !(h->eps_norm > 0) || !(h->nu_norm > 0)) {
-        why = "invalid histogram ranges or normalisation";
-        return ENS_EINVAL;
-    }
-    return ENS_OK;
+    return validate_hist(h, why);
 }
 
 // Group members by N (ascending), carve the workspace (base == nullptr: size only).
@@ -144,6 +155,8 @@ size_t carve(const ens_member_desc *m, int n, const ens_hist_spec *h, char *base
         g.NK = 2 * g.kc + 1;
         g.NZ = g.kc + 1;
         g.NZp = (g.NZ + kTile - 1) / kTile * kTile;
+        g.tile_x = g.tile_y = kTile;
+        g.z_mode = 0;
         g.members = (int)gr.members.size();
         g.first = first;
         first += g.members;
@@ -157,16 +170,16 @@ size_t carve(const ens_member_desc *m, int n, const ens_hist_spec *h, char *base
         g.B = ar.take<float2>((size_t)kFields * g.sB * g.members);
         g.shells = (int)std::ceil(std::sqrt(3.0) * g.kc) + 2;
         g.shell = ar.take<double>((size_t)g.shells * g.members);
-        PB = std::max(PB, g.NK * g.NZp / kTile);
+        PB = std::max(PB, g.NK * g.NZp / 8);   // narrowest column tile of the update pass
         MB = std::max(MB, stats_blocks(N));
         groups.push_back(gr);
     }
-    const long long L = counts_len_of(h->qr_bins, h->tail_bins);
+    const long long L = counts_len_of(h->qr_bins, h->tail_bins, h->grad_bins);
     double *partial = ar.take<double>((size_t)n * PB * 4);
     unsigned long long *counts = ar.take<unsigned long long>((size_t)n * L);
     double *moments = ar.take<double>((size_t)n * kNMom);
     double *mom_partial = ar.take<double>((size_t)n * MB * kNMom);
-    float *edges = ar.take<float>((size_t)2 * (h->qr_bins + 1) + h->tail_bins + 1);
+    float *edges = ar.take<float>((size_t)2 * (h->qr_bins + 1) + h->tail_bins + 1 + h->grad_bins + 1);
     // mixture scratch: lambdas, user weights, weights, covered, pdf, mixed moments, ratios
     double *mix = ar.take<double>((size_t)3 * n + 1 + L + kNMom + 8);
     if (ctx) {
@@ -237,8 +250,8 @@ void record_step(ens_ctx *ctx, cudaStream_t s)
     const int ng = (int)ctx->groups.size();
     for (int st = 0; st < nst; ++st) {
         const int last = st == nst - 1;
-        if (ng == 1) {
-            record_group_stage(ctx, ctx->groups[0].geo, st, last, s);
+        if (ng == 1 || !ctx->parallel_groups) {
+            for (int gi = 0; gi < ng; ++gi) record_group_stage(ctx, ctx->groups[gi].geo, st, last, s);
         } else {
             cudaEventRecord(ctx->ev_fork, s);
             for (int gi = 1; gi < ng; ++gi) {
@@ -346,10 +359,13 @@ static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, co
         x.seed = d.seed;
         x.init_energy = d.init_energy;
         const Geo &g = ctx->groups[x.group].geo;
-        x.nblk = g.NK * g.NZp / kTile;   // update-pass CTAs (>= sums-kernel CTAs)
+        x.nblk = g.NK * g.NZp / g.tile_x;   // update-pass CTAs (>= sums-kernel CTAs)
         x.dt = x.dt_fixed;
     }
     cudaStream_t st = ctx->stream;
+    int dev = 0;
+    ENS_CUDA(ctx, cudaGetDevice(&dev));
+    ENS_CUDA(ctx, cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev));
     ENS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     ENS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     ctx->aux.assign(ctx->groups.size(), nullptr);
@@ -360,7 +376,7 @@ static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, co
     }
     ENS_CUDA(ctx, cudaMemcpyAsync(ctx->md, md.data(), sizeof(MemberDev) * n, cudaMemcpyHostToDevice, st));
     ENS_CUDA(ctx, cudaMemsetAsync(ctx->partial, 0, sizeof(double) * n * ctx->partial_blocks * 4, st));
-    const long long L = counts_len_of(h->qr_bins, h->tail_bins);
+    const long long L = counts_len_of(h->qr_bins, h->tail_bins, h->grad_bins);
     ENS_CUDA(ctx, cudaMemsetAsync(ctx->counts, 0, sizeof(unsigned long long) * n * L, st));
     ENS_CUDA(ctx, cudaMemsetAsync(ctx->moments, 0, sizeof(double) * n * kNMom, st));
     // histogram edges and scalings
@@ -382,12 +398,19 @@ static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, co
     hd.edges_q = ctx->edges;
     hd.edges_r = ctx->edges + (h->qr_bins + 1);
     hd.edges_t = ctx->edges + 2 * (h->qr_bins + 1);
-    launch_edges(ctx->edges, ctx->edges + (h->qr_bins + 1), ctx->edges + 2 * (h->qr_bins + 1), h->qr_bins,
-                 h->tail_bins, h->q_lim, h->r_lim, h->tail_lo, h->tail_hi, st);
+    hd.ng = h->grad_bins;
+    hd.g_scale = (float)(1.0 / std::sqrt(q0));
+    hd.g_lo = (float)(-h->grad_lim);
+    hd.g_inv_w = h->grad_bins > 0 ? (float)(h->grad_bins / (2.0 * h->grad_lim)) : 0.f;
+    hd.edges_g = hd.edges_t + h->tail_bins + 1;
+    launch_edges(ctx->edges, ctx->edges + (h->qr_bins + 1), ctx->edges + 2 * (h->qr_bins + 1),
+                 const_cast<float *>(hd.edges_g), h->qr_bins, h->tail_bins, h->grad_bins, h->q_lim, h->r_lim,
+                 h->tail_lo, h->tail_hi, h->grad_lim, st);
     for (auto &gr : ctx->groups) {
-        ENS_CUDA(ctx, prepare_kernels(gr.geo.N, h->qr_bins, h->tail_bins));
-        gr.geo.z_ctas = znl_ctas(gr.geo.N);
-        if (gr.geo.z_ctas <= 0) return fail(ctx, ENS_ECUDA, "occupancy query of the z pass failed");
+        ENS_CUDA(ctx, prepare_kernels(gr.geo.N, h->qr_bins, h->tail_bins, h->grad_bins));
+        const int per_sm = znl_ctas_per_sm(gr.geo.N);
+        if (per_sm <= 0 || ctx->sms <= 0) return fail(ctx, ENS_ECUDA, "occupancy query of the z pass failed");
+        gr.geo.z_ctas = per_sm * ctx->sms;
         launch_twiddles(const_cast<float2 *>(gr.geo.tw), gr.geo.N, st);
         ENS_CUDA(ctx, cudaMemsetAsync(gr.geo.U, 0, sizeof(float2) * 3 * gr.geo.sU * gr.geo.members, st));
         ENS_CUDA(ctx, cudaMemsetAsync(gr.geo.S, 0, sizeof(float2) * 3 * gr.geo.sU * gr.geo.members, st));
@@ -423,7 +446,10 @@ const char *ens_last_error(const ens_ctx *ctx)
     return ctx->err.empty() ? "" : ctx->err.c_str();
 }
 
-int ens_counts_len(const ens_hist_spec *h) { return h ? (int)counts_len_of(h->qr_bins, h->tail_bins) : 0; }
+int ens_counts_len(const ens_hist_spec *h)
+{
+    return h ? (int)counts_len_of(h->qr_bins, h->tail_bins, h->grad_bins > 0 ? h->grad_bins : 0) : 0;
+}
 
 ens_status ens_query(const ens_member_desc *m, int n, const ens_hist_spec *h, size_t *bytes)
 {
@@ -648,11 +674,13 @@ static ens_status mixture_device(ens_ctx *ctx, int n, const double *d_lam, const
     MixPdfArgs pa{};
     pa.nq = h->qr_bins;
     pa.nt = h->tail_bins;
-    pa.counts_len = (int)counts_len_of(h->qr_bins, h->tail_bins);
+    pa.ng = h->grad_bins;
+    pa.counts_len = (int)counts_len_of(h->qr_bins, h->tail_bins, h->grad_bins);
     pa.dq = 2.0 * h->q_lim / h->qr_bins;
     pa.dr = 2.0 * h->r_lim / h->qr_bins;
     pa.dt = (h->tail_hi - h->tail_lo) / h->tail_bins;
-    const int nb = pa.counts_len - 8;
+    pa.dg = h->grad_bins > 0 ? 2.0 * h->grad_lim / h->grad_bins : 0.0;
+    const int nb = mix_pdf_len(pa);
     double *d_w = d_scratch, *d_cov = d_w + n, *d_pdf = d_cov + 1, *d_mm = d_pdf + nb, *d_rat = d_mm + kNMom;
     launch_mixture(d_lam, n, wa, d_counts, d_mom, pa, d_w, d_cov, d_pdf, d_mm, d_rat, st);
     cudaError_t e = cudaGetLastError();
@@ -668,6 +696,10 @@ static ens_status mixture_device(ens_ctx *ctx, int n, const double *d_lam, const
     if (out->pdf_qr) std::memcpy(out->pdf_qr, hp, sizeof(double) * nq2);
     if (out->pdf_eps) std::memcpy(out->pdf_eps, hp + nq2, sizeof(double) * h->tail_bins);
     if (out->pdf_ens) std::memcpy(out->pdf_ens, hp + nq2 + h->tail_bins, sizeof(double) * h->tail_bins);
+    if (h->grad_bins > 0 && out->pdf_long)
+        std::memcpy(out->pdf_long, hp + nq2 + 2 * h->tail_bins, sizeof(double) * h->grad_bins);
+    if (h->grad_bins > 0 && out->pdf_trans)
+        std::memcpy(out->pdf_trans, hp + nq2 + 2 * h->tail_bins + h->grad_bins, sizeof(double) * h->grad_bins);
     if (out->moments) std::memcpy(out->moments, hm, sizeof(double) * kNMom);
     for (int k = 0; k < 5; ++k) out->ratios[k] = hr[k];
     return ENS_OK;
@@ -718,8 +750,10 @@ ens_status ens_mixture_host(int n, const double *lambdas, const uint64_t *counts
 {
     if (n <= 0 || n > 1024 || !lambdas || !counts || !moments || !h || !out || !weight_spec_ok(w))
         return ENS_EINVAL;
+    std::string why;
+    if (validate_hist(h, why) != ENS_OK) return ENS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    const long long L = counts_len_of(h->qr_bins, h->tail_bins);
+    const long long L = counts_len_of(h->qr_bins, h->tail_bins, h->grad_bins);
     const size_t nd = (size_t)3 * n + 1 + L + kNMom + 8 + (size_t)n * kNMom;
     const size_t bytes = sizeof(double) * nd + sizeof(unsigned long long) * n * L;
     void *mem = nullptr;
@@ -893,6 +927,259 @@ ens_status ens_diagnostics(ens_ctx *ctx, ens_diag *out)
         if ((d.flags & kFlagTimeout) && flag == ENS_OK) flag = ENS_ETIMEOUT;
     }
     return flag;
+}
+
+}  // extern "C"
+
+// ---- autotuner ------------------------------------------------------------
+
+namespace {
+
+void tuning_of(const ens_ctx *ctx, ens_tuning *t)
+{
+    std::memset(t, 0, sizeof *t);
+    t->groups = (int)ctx->groups.size();
+    t->parallel_groups = ctx->parallel_groups;
+    for (size_t gi = 0; gi < ctx->groups.size() && gi < ENS_MAX_GROUPS; ++gi) {
+        const Geo &g = ctx->groups[gi].geo;
+        ens_group_tuning &o = t->group[gi];
+        o.N = g.N;
+        o.tile_x = g.tile_x;
+        o.tile_y = g.tile_y;
+        o.z_variant = g.z_mode;
+        o.z_ctas_per_sm = ctx->sms > 0 ? g.z_ctas / ctx->sms : 0;
+    }
+}
+
+ens_status tuning_valid(const ens_ctx *ctx, const ens_tuning *t, std::string &why)
+{
+    if (t->groups != (int)ctx->groups.size()) {
+        why = "tuning describes a different number of grid-size groups";
+        return ENS_EINVAL;
+    }
+    if (t->parallel_groups != 0 && t->parallel_groups != 1) {
+        why = "parallel_groups must be 0 or 1";
+        return ENS_EINVAL;
+    }
+    for (int gi = 0; gi < t->groups; ++gi) {
+        const ens_group_tuning &o = t->group[gi];
+        const int N = ctx->groups[gi].geo.N;
+        if (o.N != N) {
+            why = "tuning group " + std::to_string(gi) + " is for N = " + std::to_string(o.N) + ", not " +
+                  std::to_string(N);
+            return ENS_EINVAL;
+        }
+        if ((o.tile_x != 8 && o.tile_x != 16) || (o.tile_y != 8 && o.tile_y != 16)) {
+            why = "column tiles must be 8 or 16";
+            return ENS_EINVAL;
+        }
+        if (o.z_variant != 0 && o.z_variant != 1) {
+            why = "z_variant must be 0 or 1";
+            return ENS_EINVAL;
+        }
+        const int occ = znl_ctas_per_sm(N);
+        if (o.z_ctas_per_sm < 1 || o.z_ctas_per_sm > occ) {
+            why = "z_ctas_per_sm must lie in [1, " + std::to_string(occ) + "] for N = " + std::to_string(N);
+            return ENS_EINVAL;
+        }
+    }
+    return ENS_OK;
+}
+
+// Install a (validated) tuning: pass variants per group, the update pass's
+// partial-sum count per member, and a fresh graph at the next ens_step.
+ens_status apply_tuning(ens_ctx *ctx, const ens_tuning *t)
+{
+    ctx->parallel_groups = t->parallel_groups;
+    for (int gi = 0; gi < t->groups; ++gi) {
+        Geo &g = ctx->groups[gi].geo;
+        const ens_group_tuning &o = t->group[gi];
+        g.tile_x = o.tile_x;
+        g.tile_y = o.tile_y;
+        g.z_mode = o.z_variant;
+        g.z_ctas = o.z_ctas_per_sm * ctx->sms;
+        const int nblk = g.NK * g.NZp / g.tile_x;
+        std::vector<int> v(g.members, nblk);
+        // MemberDev::nblk of the group's members: one int per struct, strided
+        ENS_CUDA(ctx, cudaMemcpy2DAsync(&ctx->md[g.first].nblk, sizeof(MemberDev), v.data(), sizeof(int),
+                                        sizeof(int), g.members, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    // slots a narrower tile wrote before must not leak into the reduction
+    ENS_CUDA(ctx, cudaMemsetAsync(ctx->partial, 0,
+                                  sizeof(double) * ctx->desc.size() * ctx->partial_blocks * 4, ctx->stream));
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return ENS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ens_status ens_get_tuning(const ens_ctx *ctx, ens_tuning *out)
+{
+    if (!ctx || !out) return ENS_EINVAL;
+    tuning_of(ctx, out);
+    return ENS_OK;
+}
+
+ens_status ens_set_tuning(ens_ctx *ctx, const ens_tuning *t)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (!t) return fail(ctx, ENS_EINVAL, "null tuning");
+    std::string why;
+    if (tuning_valid(ctx, t, why) != ENS_OK) {
+        ctx->err = why;   // not sticky: the context keeps its previous tuning
+        return ENS_EINVAL;
+    }
+    return apply_tuning(ctx, t);
+}
+
+ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (steps < 1) return fail(ctx, ENS_EINVAL, "autotune needs at least one timed step per trial");
+    const int n = (int)ctx->desc.size();
+    cudaStream_t st = ctx->stream;
+    // snapshot of the member state: the spectral fields U (S is stage
+    // scratch, rewritten before it is read) and the per-member run state
+    size_t bytes = sizeof(MemberDev) * n;
+    for (auto &gr : ctx->groups) bytes += sizeof(float2) * 3 * gr.geo.sU * gr.geo.members;
+    char *snap = nullptr;
+    if (cudaMallocAsync(&snap, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "autotune: no device memory for the state snapshot (" + std::to_string(bytes) + " bytes)";
+        return ENS_ENOMEM;
+    }
+    auto copy_state = [&](bool save) -> cudaError_t {
+        size_t off = 0;
+        cudaError_t e = cudaSuccess;
+        for (auto &gr : ctx->groups) {
+            const size_t b = sizeof(float2) * 3 * gr.geo.sU * gr.geo.members;
+            e = save ? cudaMemcpyAsync(snap + off, gr.geo.U, b, cudaMemcpyDeviceToDevice, st)
+                     : cudaMemcpyAsync(gr.geo.U, snap + off, b, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return e;
+            off += b;
+        }
+        return save ? cudaMemcpyAsync(snap + off, ctx->md, sizeof(MemberDev) * n, cudaMemcpyDeviceToDevice, st)
+                    : cudaMemcpyAsync(ctx->md, snap + off, sizeof(MemberDev) * n, cudaMemcpyDeviceToDevice, st);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ens_tuning best, cand;
+    tuning_of(ctx, &best);
+    const ens_tuning start = best;
+    double best_ms = 0.0;
+    int trials = 0;
+    ens_status rs = ENS_OK;
+    auto fail_cuda = [&](const char *what, cudaError_t e) {
+        rs = cuda_fail(ctx, what, e);
+        return -1.0;
+    };
+    // one trial: install, restore the snapshot, one untimed step, then the
+    // mean of `steps` graph launches between two events
+    auto trial = [&](const ens_tuning &t) -> double {
+        if (apply_tuning(ctx, &t) != ENS_OK) {
+            rs = ctx->sticky != ENS_OK ? ctx->sticky : ENS_ECUDA;
+            return -1.0;
+        }
+        cudaError_t e = copy_state(false);
+        if (e != cudaSuccess) return fail_cuda("autotune restore", e);
+        if (ens_step(ctx, 1) != ENS_OK) {
+            rs = ctx->sticky;
+            return -1.0;
+        }
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) return fail_cuda("cudaEventRecord", e);
+        if (ens_step(ctx, steps) != ENS_OK) {
+            rs = ctx->sticky;
+            return -1.0;
+        }
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess) return fail_cuda("cudaEventRecord", e);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return fail_cuda("cudaEventSynchronize", e);
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return fail_cuda("cudaEventElapsedTime", e);
+        ++trials;
+        return ms / steps;
+    };
+    // a candidate replaces the incumbent only if it is faster by more than
+    // the timing noise of one trial
+    constexpr double kMargin = 0.01;
+    auto consider = [&](const ens_tuning &t) -> bool {
+        const double ms = trial(t);
+        if (ms < 0.0) return false;
+        if (ms < best_ms * (1.0 - kMargin)) {
+            best = t;
+            best_ms = ms;
+        }
+        return true;
+    };
+    cudaError_t e = copy_state(true);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        rs = cuda_fail(ctx, "autotune setup", e);
+    } else {
+        best_ms = trial(best);
+        if (best_ms < 0.0) rs = rs == ENS_OK ? ENS_ECUDA : rs;
+    }
+    // coordinate descent over the knobs, group by group
+    for (int gi = 0; rs == ENS_OK && gi < best.groups; ++gi) {
+        const int N = best.group[gi].N;
+        for (int tile : {16, 8}) {
+            cand = best;
+            if (cand.group[gi].tile_x == tile) continue;
+            cand.group[gi].tile_x = tile;
+            if (!consider(cand)) break;
+        }
+        for (int tile : {16, 8}) {
+            if (rs != ENS_OK) break;
+            cand = best;
+            if (cand.group[gi].tile_y == tile) continue;
+            cand.group[gi].tile_y = tile;
+            if (!consider(cand)) break;
+        }
+        const int occ = znl_ctas_per_sm(N);
+        for (int c = 1; rs == ENS_OK && c <= occ; ++c) {
+            cand = best;
+            if (cand.group[gi].z_variant == 0 && cand.group[gi].z_ctas_per_sm == c) continue;
+            cand.group[gi].z_variant = 0;
+            cand.group[gi].z_ctas_per_sm = c;
+            if (!consider(cand)) break;
+        }
+        if (rs == ENS_OK && best.group[gi].z_variant != 1) {
+            cand = best;
+            cand.group[gi].z_variant = 1;
+            consider(cand);
+        }
+    }
+    if (rs == ENS_OK && best.groups > 1) {
+        cand = best;
+        cand.parallel_groups = 1 - best.parallel_groups;
+        consider(cand);
+    }
+    // install the winner (or, after an error, the starting tuning) and put
+    // the state back as it was
+    const ens_tuning &fin = rs == ENS_OK ? best : start;
+    if (ctx->sticky == ENS_OK) {
+        apply_tuning(ctx, &fin);
+        e = copy_state(false);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess && rs == ENS_OK) rs = cuda_fail(ctx, "autotune restore", e);
+    }
+    cudaFreeAsync(snap, st);
+    cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) {
+        *out = fin;
+        out->ms_per_step = rs == ENS_OK ? best_ms : 0.0;
+        out->trials = trials;
+    }
+    return rs;
 }
 
 }  // extern "C"

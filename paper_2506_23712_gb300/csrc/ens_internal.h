@@ -6,7 +6,7 @@
 
 namespace ens {
 
-constexpr int kTile = 16;        // columns per CTA in the strided-axis passes
+constexpr int kTile = 16;        // column padding of the layouts; widest column tile of the strided-axis passes
 constexpr int kFields = 8;       // fields per member in the pass buffers
 constexpr int kNMom = 48;        // gradient moment sums per member
 constexpr int kStatsIters = 16;  // row groups per CTA in the statistics pass
@@ -53,6 +53,9 @@ struct Geo {
     unsigned long long *counts;  // statistics counts [member][counts_len]
     double *mom_partial;         // per-CTA moment partials [member][blocks][kNMom]
     int mom_blocks;
+    // tuning of the stage passes (chosen by the autotuner)
+    int tile_x, tile_y;          // columns per CTA of the x / y passes (8 or 16)
+    int z_mode;                  // 0: persistent TMA z pass, 1: one CTA per row group
     int z_ctas;                  // persistent CTAs of the z-direction nonlinear pass
 };
 
@@ -63,8 +66,15 @@ struct HistDev {
     float q_lo, q_inv_w, r_lo, r_inv_w;
     float t_lo, t_inv_w;         // log10 axis
     const float *edges_q, *edges_r, *edges_t;  // FP32 edges (nq+1, nq+1, nt+1)
+    int ng;                      // gradient-component bins (0: none)
+    float g_scale, g_lo, g_inv_w;  // 1/sqrt(q0); linear axis
+    const float *edges_g;        // FP32 edges (ng+1)
 };
 
-inline long long counts_len_of(int nq, int nt) { return (long long)nq * nq + 2LL * nt + 8; }
+// [nq*nq | nt | nt | 8 counters] then, with ng > 0, [ng | ng | 4 counters]
+inline long long counts_len_of(int nq, int nt, int ng)
+{
+    return (long long)nq * nq + 2LL * nt + 8 + (ng > 0 ? 2LL * ng + 4 : 0);
+}
 
 }  // namespace ens

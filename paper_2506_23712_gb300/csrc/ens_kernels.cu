@@ -1,5 +1,6 @@
 // Non-templated kernels (reductions, initial field, twiddles, edges, mixture)
-// and the per-N launch dispatch of the templated passes.
+// and the table of per-N pass launchers (each grid size compiles in its own
+// translation unit, ens_sized.cu).
 #include "ens_launch.h"
 #include "ens_stats.cuh"
 #include "ens_znl.cuh"
@@ -137,9 +138,10 @@ __global__ void k_twiddles(float2 *tw, int N)
     }
 }
 
-__global__ void k_edges(float *eq, float *er, float *et, int nq, int nt, double q_lim, double r_lim, double t_lo,
-                        double t_hi)
+__global__ void k_edges(float *eq, float *er, float *et, float *eg, int nq, int nt, int ng, double q_lim,
+                        double r_lim, double t_lo, double t_hi, double g_lim)
 {
+    for (int b = threadIdx.x; b <= ng; b += blockDim.x) eg[b] = (float)(-g_lim + 2.0 * g_lim * (double)b / (double)ng);
     for (int b = threadIdx.x; b <= nq; b += blockDim.x) {
         eq[b] = (float)(-q_lim + 2.0 * q_lim * (double)b / (double)nq);
         er[b] = (float)(-r_lim + 2.0 * r_lim * (double)b / (double)nq);
@@ -242,15 +244,20 @@ __global__ void k_mix_pdf(const unsigned long long *counts, const double *moment
                           MixPdfArgs a, double *pdf, double *mom_mix)
 {
     const int L = a.counts_len;
-    const int off_c = L - 8;
+    const int off_c = a.nq * a.nq + 2 * a.nt;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < off_c) {
+    if (b < mix_pdf_len(a)) {
+        // gradient bins follow the 8 counters; 3 longitudinal and 6
+        // transverse samples per grid point
+        const bool grad = b >= off_c;
+        const int src = grad ? b + 8 : b;
         double s = 0.0;
         for (int i = 0; i < n; ++i) {
             const double npts = (double)counts[(long long)i * L + off_c + 6];
-            if (npts > 0.0) s += w[i] * (double)counts[(long long)i * L + b] / npts;
+            if (npts > 0.0) s += w[i] * (double)counts[(long long)i * L + src] / npts;
         }
-        const double width = b < a.nq * a.nq ? a.dq * a.dr : a.dt;
+        double width = b < a.nq * a.nq ? a.dq * a.dr : a.dt;
+        if (grad) width = a.dg * (b < off_c + a.ng ? 3.0 : 6.0);
         pdf[b] = s / width;
     }
     if (blockIdx.x == 0 && threadIdx.x < kNMom) {
@@ -285,105 +292,6 @@ __global__ void k_mix_ratios(const double *mom_mix, double *ratios)
 // ---------------------------------------------------------------------------
 // launch dispatch
 // ---------------------------------------------------------------------------
-template <class K>
-static cudaError_t allow_smem(K kernel, size_t bytes)
-{
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <int N>
-static cudaError_t prepare_n(int nq, int nt)
-{
-    cudaError_t e = cudaSuccess;
-    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    chk(allow_smem(k_inv_x<N, 0>, smem_x<N>()));
-    chk(allow_smem(k_inv_x<N, 1>, smem_x<N>()));
-    chk(allow_smem(k_inv_y<N>, smem_cols<N>()));
-    chk(allow_smem(k_fwd_y<N>, smem_cols<N>()));
-    chk(allow_smem(k_fwd_x<N, 0>, smem_x<N>()));
-    chk(allow_smem(k_fwd_x<N, 1>, smem_x<N>()));
-    chk(allow_smem(k_fwd_x<N, 2>, smem_x<N>()));
-    chk(allow_smem(k_fwd_x<N, 3>, smem_x<N>()));
-    chk(allow_smem(k_z<N, 0>, smem_rows<N>()));
-    chk(allow_smem(k_z<N, 1>, smem_rows<N>()));
-    chk(allow_smem(k_z<N, 3>, smem_rows<N>()));
-    chk(allow_smem(k_z<N, 4>, smem_rows<N>()));
-    chk(allow_smem(k_z_stats<N>, smem_stats<N>(nq, nt)));
-    chk(allow_smem(k_znl<N>, ZCfg<N>::smem_bytes()));
-    return e;
-}
-
-// persistent grid of the z nonlinear pass: resident CTAs per SM x SMs
-template <int N>
-static int znl_ctas_n()
-{
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_znl<N>, 256, ZCfg<N>::smem_bytes()) !=
-        cudaSuccess)
-        return 0;
-    return std::max(1, per_sm) * sms;
-}
-
-template <int N>
-static void launch_n(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last,
-                     int arg, cudaStream_t s)
-{
-    constexpr int P = PlanInfo<N>::P;
-    constexpr int TC = kTile * P;
-    constexpr int RZ = RowCfg<N>::RZ;
-    constexpr int TZ = RZ * RowCfg<N>::P;   // 256 threads, warp-local rows
-    const int col_tiles_state = g.NK * g.NZp / kTile;
-    const int col_tiles_mid = N * g.NZp / kTile;
-    switch (pass) {
-    case Pass::IX: {
-        dim3 grid(col_tiles_state, g.members);
-        if (mode == 0) k_inv_x<N, 0><<<grid, TC, smem_x<N>(), s>>>(g, arg);
-        else k_inv_x<N, 1><<<grid, TC, smem_x<N>(), s>>>(g, arg);
-        break;
-    }
-    case Pass::IY: {
-        // arg = number of fields, mode = first field
-        dim3 grid(col_tiles_mid, arg, g.members);
-        k_inv_y<N><<<grid, TC, smem_cols<N>(), s>>>(g, mode);
-        break;
-    }
-    case Pass::Z: {
-        dim3 grid(N * N / RZ, g.members);
-        switch (mode) {
-        case 0: k_znl<N><<<g.z_ctas, 256, ZCfg<N>::smem_bytes(), s>>>(g, md, stage); break;
-        case 1: k_z<N, 1><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
-        case 3: k_z<N, 3><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
-        default: k_z<N, 4><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
-        }
-        break;
-    }
-    case Pass::FY: {
-        dim3 grid(col_tiles_mid, 3, g.members);
-        k_fwd_y<N><<<grid, TC, smem_cols<N>(), s>>>(g);
-        break;
-    }
-    case Pass::FX: {
-        dim3 grid(col_tiles_state, g.members);
-        switch (mode) {
-        case 0: k_fwd_x<N, 0><<<grid, TC, smem_x<N>(), s>>>(g, md, stage, last); break;
-        case 1: k_fwd_x<N, 1><<<grid, TC, smem_x<N>(), s>>>(g, md, stage, last); break;
-        case 2: k_fwd_x<N, 2><<<grid, TC, smem_x<N>(), s>>>(g, md, stage, last); break;
-        default: k_fwd_x<N, 3><<<grid, TC, smem_x<N>(), s>>>(g, md, stage, last); break;
-        }
-        break;
-    }
-    case Pass::ZSTAT: {
-        const long long rows = (long long)N * N;
-        dim3 grid((unsigned)((rows + (long long)RZ * kStatsIters - 1) / ((long long)RZ * kStatsIters)), g.members);
-        k_z_stats<N><<<grid, TZ, smem_stats<N>(h->nq, h->nt), s>>>(g, *h, md);
-        break;
-    }
-    }
-}
-
 #define ENS_SUPPORTED_N(X) X(16) X(32) X(64) X(128) X(256) X(384) X(512)
 
 bool supported_n(int N)
@@ -410,28 +318,30 @@ int stats_blocks(int N)
     return 0;
 }
 
-int znl_ctas(int N)
+const SizedOps *sized_ops(int N)
 {
-#define X(n) if (N == n) return znl_ctas_n<n>();
+#define X(n) if (N == n) return sized_ops_for<n>();
     ENS_SUPPORTED_N(X)
 #undef X
-    return 0;
+    return nullptr;
 }
 
-cudaError_t prepare_kernels(int N, int nq, int nt)
+cudaError_t prepare_kernels(int N, int nq, int nt, int ng)
 {
-#define X(n) if (N == n) return prepare_n<n>(nq, nt);
-    ENS_SUPPORTED_N(X)
-#undef X
-    return cudaErrorInvalidValue;
+    const SizedOps *o = sized_ops(N);
+    return o ? o->prepare(nq, nt, ng) : cudaErrorInvalidValue;
+}
+
+int znl_ctas_per_sm(int N)
+{
+    const SizedOps *o = sized_ops(N);
+    return o ? o->znl_ctas_per_sm() : 0;
 }
 
 void launch_pass(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last, int arg,
                  cudaStream_t s)
 {
-#define X(n) if (g.N == n) { launch_n<n>(pass, mode, g, md, h, stage, last, arg, s); return; }
-    ENS_SUPPORTED_N(X)
-#undef X
+    if (const SizedOps *o = sized_ops(g.N)) o->launch(pass, mode, g, md, h, stage, last, arg, s);
 }
 
 void launch_state_sums(const Geo &g, MemberDev *md, cudaStream_t s)
@@ -462,10 +372,10 @@ void launch_ic(const Geo &g, MemberDev *md, cudaStream_t s)
 
 void launch_twiddles(float2 *tw, int N, cudaStream_t s) { k_twiddles<<<(N + 255) / 256, 256, 0, s>>>(tw, N); }
 
-void launch_edges(float *eq, float *er, float *et, int nq, int nt, double q_lim, double r_lim, double t_lo,
-                  double t_hi, cudaStream_t s)
+void launch_edges(float *eq, float *er, float *et, float *eg, int nq, int nt, int ng, double q_lim, double r_lim,
+                  double t_lo, double t_hi, double g_lim, cudaStream_t s)
 {
-    k_edges<<<1, 256, 0, s>>>(eq, er, et, nq, nt, q_lim, r_lim, t_lo, t_hi);
+    k_edges<<<1, 256, 0, s>>>(eq, er, et, eg, nq, nt, ng, q_lim, r_lim, t_lo, t_hi, g_lim);
 }
 
 void launch_finish_stats(const double *mom_partial, int blocks, double *moments, int nmembers, int accumulate,
@@ -479,7 +389,7 @@ void launch_mixture(const double *lam, int n, const MixWeightArgs &wa, const uns
                     double *mom_mix, double *ratios, cudaStream_t s)
 {
     k_mix_weights<<<1, 1024, 0, s>>>(lam, n, wa, w, covered);
-    const int nb = pa.counts_len - 8;
+    const int nb = mix_pdf_len(pa);
     k_mix_pdf<<<(nb + 255) / 256, 256, 0, s>>>(counts, moments, w, n, pa, pdf, mom_mix);
     k_mix_ratios<<<1, 32, 0, s>>>(mom_mix, ratios);
 }

@@ -33,15 +33,24 @@ struct RowCfg {
     static constexpr int SROW = N + N / 16 + N / 32 + 1;   // padded shared row stride (float2)
 };
 
-__host__ __device__ constexpr int threads_cols(int P) { return kTile * P; }
+// Column-tile passes (x and y) take the tile width T (columns per CTA, a
+// divisor of kTile) as a template parameter: the autotuner picks it per grid
+// size.  Registers per thread stay the same for every T (128 at most where
+// the T = kTile variant asks for two CTAs per SM).
+template <int N, int T>
+struct ColCfg {
+    static_assert(kTile % T == 0, "tile width must divide the column padding");
+    static constexpr int threads = T * PlanInfo<N>::P;
+    static constexpr int min_blocks = (256 / (kTile * PlanInfo<N>::P) > 0 ? 2 : 1) * (kTile / T);
+};
 
 // Launch helpers (host): shared memory bytes per pass.
-template <int N>
-constexpr size_t smem_cols() { return sizeof(float2) * (size_t)(N + N * kTile); }
+template <int N, int T>
+constexpr size_t smem_cols() { return sizeof(float2) * (size_t)(N + N * T); }
 __host__ __device__ constexpr int kc_of_n(int N) { return (N + 2) / 3 - 1; }
-// x passes also stage the three components of a column tile: [3][NK][kTile]
-template <int N>
-constexpr size_t smem_x() { return smem_cols<N>() + sizeof(float2) * 3 * (2 * kc_of_n(N) + 1) * kTile; }
+// x passes also stage the three components of a column tile: [3][NK][T]
+template <int N, int T>
+constexpr size_t smem_x() { return smem_cols<N, T>() + sizeof(float2) * 3 * (2 * kc_of_n(N) + 1) * T; }
 template <int N>
 constexpr size_t smem_rows() { return sizeof(float2) * (size_t)(N + RowCfg<N>::RZ * RowCfg<N>::SROW); }
 
@@ -57,21 +66,21 @@ __device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restri
 // IX: inverse transform along x of fields built from the state.
 //   MODE 0: u_x, u_y, u_z, omega_x, omega_y, omega_z   (omega = i k x u)
 //   MODE 1: A_ij = i k_j u_i for ij = 11,12,13,21,22,23,31,32
-// grid (NK*NZp/kTile, members), block kTile*P.
+// grid (NK*NZp/T, members), block T*P.
 // ---------------------------------------------------------------------------
-template <int N, int MODE>
-__global__ void __launch_bounds__(kTile * PlanInfo<N>::P, 256 / (kTile * PlanInfo<N>::P) > 0 ? 2 : 1)
+template <int N, int MODE, int T>
+__global__ void __launch_bounds__(ColCfg<N, T>::threads, ColCfg<N, T>::min_blocks)
 k_inv_x(Geo g, int use_S)
 {
     using PI = PlanInfo<N>;
     constexpr int P = PI::P, V = PI::V;
     constexpr int NF = MODE == 0 ? 6 : 8;
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *buf = sm + N, *tile = buf + N * kTile;   // tile: [3][NK][kTile]
+    float2 *tw = sm, *buf = sm + N, *tile = buf + N * T;   // tile: [3][NK][T]
 
-    const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
+    const int c = threadIdx.x % T, p = threadIdx.x / T;
     const int m = blockIdx.y;
-    const int col0 = blockIdx.x * kTile;                    // a tile never straddles ky (NZp % kTile == 0)
+    const int col0 = blockIdx.x * T;                    // a tile never straddles ky (NZp % T == 0)
     const int col = col0 + c;
     const int iy = col / g.NZp, kz = col % g.NZp;
     const bool valid = kz < g.NZ;
@@ -80,7 +89,7 @@ k_inv_x(Geo g, int use_S)
     const long long rowU = (long long)g.NK * g.NZp;
     const float2 *X = (use_S ? g.S : g.U) + (long long)m * 3 * g.sU + col0;
     // coalesced staging of the three velocity components of this column tile
-    const int per = g.NK * kTile;
+    const int per = g.NK * T;
     constexpr int kBatch = 8;   // loads in flight per thread before the shared stores
     for (int base = threadIdx.x; base < 3 * per; base += kBatch * blockDim.x) {
         float2 tmp[kBatch];
@@ -90,7 +99,7 @@ k_inv_x(Geo g, int use_S)
             tmp[k] = make_float2(0.f, 0.f);
             if (idx < 3 * per) {
                 const int q = idx / per, rem = idx % per;
-                const int ix = rem / kTile, cc = rem % kTile;
+                const int ix = rem / T, cc = rem % T;
                 if (((col0 + cc) % g.NZp) < g.NZ) tmp[k] = X[q * g.sU + ix * rowU + cc];
             }
         }
@@ -103,7 +112,7 @@ k_inv_x(Geo g, int use_S)
     load_twiddles(tw, g.tw, N);   // block barrier: tile complete
 
     float2 *dst0 = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
-    auto at = [&](int pos) { return &buf[pos * kTile + c]; };
+    auto at = [&](int pos) { return &buf[pos * T + c]; };
     // transform of component q of the tile, optionally times i kx (the x
     // derivative: kx varies along this transform, so it is applied before it)
     auto transform = [&](float2 *v, int q, bool dx) {
@@ -112,7 +121,7 @@ k_inv_x(Geo g, int use_S)
             const int kxi = wnum(PI::in_pos(p, i), N);
             const bool keep = kxi >= -g.kc && kxi <= g.kc;
             const int ix = kxi >= 0 ? kxi : kxi + g.NK;
-            const float2 u = keep ? tile[q * per + ix * kTile + c] : make_float2(0.f, 0.f);
+            const float2 u = keep ? tile[q * per + ix * T + c] : make_float2(0.f, 0.f);
             v[i] = dx ? mul_i(cscale(u, (float)kxi)) : u;
         }
         fft_line<N, false>(v, p, tw, at);
@@ -170,10 +179,10 @@ k_inv_x(Geo g, int use_S)
 
 // ---------------------------------------------------------------------------
 // IY: inverse transform along y of buffer-A fields [f0, f0+nf) into B.
-// grid (N*NZp/kTile, nf, members).
+// grid (N*NZp/T, nf, members).
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kTile * PlanInfo<N>::P)
+template <int N, int T>
+__global__ void __launch_bounds__(ColCfg<N, T>::threads)
 k_inv_y(Geo g, int f0)
 {
     using PI = PlanInfo<N>;
@@ -181,9 +190,9 @@ k_inv_y(Geo g, int f0)
     extern __shared__ float2 sm[];
     float2 *tw = sm, *buf = sm + N;
     load_twiddles(tw, g.tw, N);
-    const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
+    const int c = threadIdx.x % T, p = threadIdx.x / T;
     const int f = f0 + blockIdx.y, m = blockIdx.z;
-    const int col = blockIdx.x * kTile + c;       // (x, kz) flat
+    const int col = blockIdx.x * T + c;       // (x, kz) flat
     const bool valid = (col % g.NZp) < g.NZ;
     const long long row = (long long)N * g.NZp;
     const float2 *src = g.A + ((long long)m * kFields + f) * g.sA + col;
@@ -196,7 +205,7 @@ k_inv_y(Geo g, int f0)
         const int iy = ky >= 0 ? ky : ky + g.NK;
         v[i] = keep ? src[iy * row] : make_float2(0.f, 0.f);
     }
-    fft_line<N, false>(v, p, tw, [&](int pos) { return &buf[pos * kTile + c]; });
+    fft_line<N, false>(v, p, tw, [&](int pos) { return &buf[pos * T + c]; });
     if (valid) {
 #pragma unroll
         for (int i = 0; i < V; ++i) dst[PI::out_pos(p, i) * row] = v[i];
@@ -205,10 +214,10 @@ k_inv_y(Geo g, int f0)
 
 // ---------------------------------------------------------------------------
 // FY: forward transform along y of B fields [0, nf) into A (kept ky only).
-// grid (N*NZp/kTile, nf, members).
+// grid (N*NZp/T, nf, members).
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kTile * PlanInfo<N>::P)
+template <int N, int T>
+__global__ void __launch_bounds__(ColCfg<N, T>::threads)
 k_fwd_y(Geo g)
 {
     using PI = PlanInfo<N>;
@@ -216,9 +225,9 @@ k_fwd_y(Geo g)
     extern __shared__ float2 sm[];
     float2 *tw = sm, *buf = sm + N;
     load_twiddles(tw, g.tw, N);
-    const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
+    const int c = threadIdx.x % T, p = threadIdx.x / T;
     const int f = blockIdx.y, m = blockIdx.z;
-    const int col = blockIdx.x * kTile + c;
+    const int col = blockIdx.x * T + c;
     const bool valid = (col % g.NZp) < g.NZ;
     const long long row = (long long)N * g.NZp;
     const float2 *src = g.B + ((long long)m * kFields + f) * g.sB + col;
@@ -226,7 +235,7 @@ k_fwd_y(Geo g)
     float2 v[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) v[i] = valid ? src[PI::in_pos(p, i) * row] : make_float2(0.f, 0.f);
-    fft_line<N, true>(v, p, tw, [&](int pos) { return &buf[pos * kTile + c]; });
+    fft_line<N, true>(v, p, tw, [&](int pos) { return &buf[pos * T + c]; });
     if (valid) {
 #pragma unroll
         for (int i = 0; i < V; ++i) {
@@ -436,7 +445,7 @@ k_z(Geo g, MemberDev *md, int stage)
 //   MODE 2: initial field: write the projected noise spectrum to U and
 //           accumulate shell energies
 //   MODE 3: write the normalised forward transform (no projection) to U
-// grid (NK*NZp/kTile, members), block kTile*P.
+// grid (NK*NZp/T, members), block T*P.
 // ---------------------------------------------------------------------------
 struct StageCoef {
     float a, ha, b, hb;   // out = a E(ha dt) u^n + b E(hb dt) (u^s + dt F)
@@ -486,24 +495,24 @@ __device__ __forceinline__ void block_sum_to(double *out, double (&vals)[NW], do
     }
 }
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(kTile * PlanInfo<N>::P, 256 / (kTile * PlanInfo<N>::P) > 0 ? 2 : 1)
+template <int N, int MODE, int T>
+__global__ void __launch_bounds__(ColCfg<N, T>::threads, ColCfg<N, T>::min_blocks)
 k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
 {
     using PI = PlanInfo<N>;
     constexpr int P = PI::P, V = PI::V;
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *buf = sm + N, *tile = buf + N * kTile;   // tile: [3][NK][kTile]
+    float2 *tw = sm, *buf = sm + N, *tile = buf + N * T;   // tile: [3][NK][T]
     load_twiddles(tw, g.tw, N);
-    const int c = threadIdx.x % kTile, p = threadIdx.x / kTile;
+    const int c = threadIdx.x % T, p = threadIdx.x / T;
     const int m = blockIdx.y;
-    const int col0 = blockIdx.x * kTile;
+    const int col0 = blockIdx.x * T;
     const int col = col0 + c;                                  // (ky, kz) flat
     const int iy = col / g.NZp, kz = col % g.NZp;
     const bool valid = kz < g.NZ;
-    const int per = g.NK * kTile;
+    const int per = g.NK * T;
     const float2 *Ain = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
-    auto at = [&](int pos) { return &buf[pos * kTile + c]; };
+    auto at = [&](int pos) { return &buf[pos * T + c]; };
     // forward transforms of the three components; kept rows to the tile.
     // The next component's inputs are loaded while this one is transformed.
     float2 v[V], nxt[V];
@@ -522,7 +531,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const int kx = wnum(PI::out_pos(p, i), N);
-            if (kx >= -g.kc && kx <= g.kc) tile[q * per + (kx >= 0 ? kx : kx + g.NK) * kTile + c] = v[i];
+            if (kx >= -g.kc && kx <= g.kc) tile[q * per + (kx >= 0 ? kx : kx + g.NK) * T + c] = v[i];
         }
         if (q < 2) {
 #pragma unroll
@@ -561,9 +570,9 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
 #pragma unroll
             for (int u = 0; u < UB; ++u) {
                 const int idx = base + u * blockDim.x;
-                const int cc = idx % kTile;
+                const int cc = idx % T;
                 const bool ok = idx < per && ((col0 + cc) % g.NZp) < g.NZ;
-                const long long off = (long long)(idx / kTile) * rowU + cc;
+                const long long off = (long long)(idx / T) * rowU + cc;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     unb[u][q] = ok ? U[q * g.sU + off] : make_float2(0.f, 0.f);
@@ -575,7 +584,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
     for (int u = 0; u < UB; ++u) {
         const int idx = base + u * blockDim.x;
         if (idx >= per) continue;
-        const int ix = idx / kTile, cc = idx % kTile;
+        const int ix = idx / T, cc = idx % T;
         const int kzc = (col0 + cc) % g.NZp;
         if (kzc >= g.NZ) continue;
         const int kx = ix <= g.kc ? ix : ix - g.NK;

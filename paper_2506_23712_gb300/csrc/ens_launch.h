@@ -18,15 +18,37 @@ struct MixWeightArgs {
 };
 
 struct MixPdfArgs {
-    int nq, nt, counts_len;
-    double dq, dr, dt;   // bin widths: Q/q0, R/q0^1.5, log10 tail axis
+    int nq, nt, ng, counts_len;
+    double dq, dr, dt, dg;   // bin widths: Q/q0, R/q0^1.5, log10 tail axis, A/sqrt(q0)
 };
+// mixed PDF values: [nq*nq | nt | nt | ng (longitudinal) | ng (transverse)]
+__host__ __device__ inline int mix_pdf_len(const MixPdfArgs &a) { return a.nq * a.nq + 2 * a.nt + 2 * a.ng; }
 
 bool supported_n(int N);
 int plan_threads(int N);
 int stats_blocks(int N);
-cudaError_t prepare_kernels(int N, int nq, int nt);
-int znl_ctas(int N);   // persistent grid of the z nonlinear pass (0 on error)
+cudaError_t prepare_kernels(int N, int nq, int nt, int ng);
+int znl_ctas_per_sm(int N);   // resident CTAs per SM of the persistent z pass (0 on error)
+
+// Pass launchers of one grid size (ens_sized.cu, one translation unit per N).
+struct SizedOps {
+    cudaError_t (*prepare)(int nq, int nt, int ng);
+    int (*znl_ctas_per_sm)();
+    void (*launch)(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last,
+                   int arg, cudaStream_t s);
+};
+template <int N>
+const SizedOps *sized_ops_for();
+#define ENS_DECLARE_SIZED(n) template <> const SizedOps *sized_ops_for<n>();
+ENS_DECLARE_SIZED(16)
+ENS_DECLARE_SIZED(32)
+ENS_DECLARE_SIZED(64)
+ENS_DECLARE_SIZED(128)
+ENS_DECLARE_SIZED(256)
+ENS_DECLARE_SIZED(384)
+ENS_DECLARE_SIZED(512)
+#undef ENS_DECLARE_SIZED
+const SizedOps *sized_ops(int N);   // nullptr for an unsupported size
 
 // mode/arg per pass:
 //   IX: mode 0 (u, omega) or 1 (gradient), arg = read S instead of U
@@ -35,6 +57,8 @@ int znl_ctas(int N);   // persistent grid of the z nonlinear pass (0 on error)
 //   FY: forward along y of fields 0..2
 //   FX: mode 0 RK update, 1 right-hand side, 2 initial field, 3 plain transform
 //   ZSTAT: statistics
+// The stage passes (IX mode 0, IY, FY, FX mode 0, Z mode 0) take their
+// variant from the group's tuning in g (tile_x, tile_y, z_mode, z_ctas).
 void launch_pass(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last, int arg,
                  cudaStream_t s);
 void launch_state_sums(const Geo &g, MemberDev *md, cudaStream_t s);
@@ -42,8 +66,8 @@ void launch_finish(MemberDev *md, int nmembers, const double *partial, int parti
                    int mode, cudaStream_t s);
 void launch_ic(const Geo &g, MemberDev *md, cudaStream_t s);
 void launch_twiddles(float2 *tw, int N, cudaStream_t s);
-void launch_edges(float *eq, float *er, float *et, int nq, int nt, double q_lim, double r_lim, double t_lo,
-                  double t_hi, cudaStream_t s);
+void launch_edges(float *eq, float *er, float *et, float *eg, int nq, int nt, int ng, double q_lim, double r_lim,
+                  double t_lo, double t_hi, double g_lim, cudaStream_t s);
 void launch_finish_stats(const double *mom_partial, int blocks, double *moments, int nmembers, int accumulate,
                          cudaStream_t s);
 void launch_mixture(const double *lam, int n, const MixWeightArgs &wa, const unsigned long long *counts,

@@ -80,7 +80,8 @@ extern "C" ens_status ens_mixture_host_noalloc(int n, const double *lambdas, con
     if (n <= 0 || !lambdas || !counts || !moments || !h || !out || !spec_ok(w)) return ENS_EINVAL;
     if (h->qr_bins < 1 || h->tail_bins < 1 || !(h->q_lim > 0) || !(h->r_lim > 0) || !(h->tail_hi > h->tail_lo))
         return ENS_EINVAL;
-    const long long L = counts_len_of(h->qr_bins, h->tail_bins);
+    if (h->grad_bins < 0 || (h->grad_bins > 0 && !(h->grad_lim > 0))) return ENS_EINVAL;
+    const long long L = counts_len_of(h->qr_bins, h->tail_bins, h->grad_bins);
     if (n > kMaxMembers || L > kMaxCounts) {
         fprintf(stderr,
                 "ens_mixture_host_noalloc: %d members x %lld counts exceed the fixed scratch "
@@ -122,10 +123,12 @@ extern "C" ens_status ens_mixture_host_noalloc(int n, const double *lambdas, con
     MixPdfArgs pa{};
     pa.nq = h->qr_bins;
     pa.nt = h->tail_bins;
+    pa.ng = h->grad_bins;
     pa.counts_len = (int)L;
     pa.dq = 2.0 * h->q_lim / h->qr_bins;
     pa.dr = 2.0 * h->r_lim / h->qr_bins;
     pa.dt = (h->tail_hi - h->tail_lo) / h->tail_bins;
+    pa.dg = h->grad_bins > 0 ? 2.0 * h->grad_lim / h->grad_bins : 0.0;
     launch_mixture(d_lam, n, wa, d_counts, d_mom, pa, d_w, d_cov, d_pdf, d_mm, d_rat, st);
     if (cudaGetLastError() != cudaSuccess) return ENS_ECUDA;
 
@@ -141,6 +144,12 @@ extern "C" ens_status ens_mixture_host_noalloc(int n, const double *lambdas, con
     if (e == cudaSuccess && out->pdf_ens)
         e = cudaMemcpyAsync(out->pdf_ens, d_pdf + nq2 + h->tail_bins, sizeof(double) * h->tail_bins,
                             cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && h->grad_bins > 0 && out->pdf_long)
+        e = cudaMemcpyAsync(out->pdf_long, d_pdf + nq2 + 2 * h->tail_bins, sizeof(double) * h->grad_bins,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && h->grad_bins > 0 && out->pdf_trans)
+        e = cudaMemcpyAsync(out->pdf_trans, d_pdf + nq2 + 2 * h->tail_bins + h->grad_bins,
+                            sizeof(double) * h->grad_bins, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && out->moments)
         e = cudaMemcpyAsync(out->moments, d_mm, sizeof(double) * kNMom, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ratios, d_rat, sizeof(double) * 5, cudaMemcpyDeviceToHost, st);

@@ -1,0 +1,146 @@
+// Pass launchers of one grid size N = ENS_N.  The build compiles this file
+// once per supported N (-DENS_N=16 ... 512), so the heavy template
+// instantiations of the FFT passes spread over parallel compiler jobs.
+#include "ens_launch.h"
+#include "ens_stats.cuh"
+#include "ens_znl.cuh"
+
+#ifndef ENS_N
+#error "compile with -DENS_N=<grid size>"
+#endif
+
+namespace ens {
+namespace {
+
+constexpr int N = ENS_N;
+
+template <class K>
+cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t prepare(int nq, int nt, int ng)
+{
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    chk(allow_smem(k_inv_x<N, 0, 16>, smem_x<N, 16>()));
+    chk(allow_smem(k_inv_x<N, 0, 8>, smem_x<N, 8>()));
+    chk(allow_smem(k_inv_x<N, 1, 16>, smem_x<N, 16>()));
+    chk(allow_smem(k_inv_y<N, 16>, smem_cols<N, 16>()));
+    chk(allow_smem(k_inv_y<N, 8>, smem_cols<N, 8>()));
+    chk(allow_smem(k_fwd_y<N, 16>, smem_cols<N, 16>()));
+    chk(allow_smem(k_fwd_y<N, 8>, smem_cols<N, 8>()));
+    chk(allow_smem(k_fwd_x<N, 0, 16>, smem_x<N, 16>()));
+    chk(allow_smem(k_fwd_x<N, 0, 8>, smem_x<N, 8>()));
+    chk(allow_smem(k_fwd_x<N, 1, 16>, smem_x<N, 16>()));
+    chk(allow_smem(k_fwd_x<N, 2, 16>, smem_x<N, 16>()));
+    chk(allow_smem(k_fwd_x<N, 3, 16>, smem_x<N, 16>()));
+    chk(allow_smem(k_z<N, 0>, smem_rows<N>()));
+    chk(allow_smem(k_z<N, 1>, smem_rows<N>()));
+    chk(allow_smem(k_z<N, 3>, smem_rows<N>()));
+    chk(allow_smem(k_z<N, 4>, smem_rows<N>()));
+    chk(allow_smem(k_z_stats<N>, smem_stats<N>(nq, nt, ng)));
+    chk(allow_smem(k_znl<N>, ZCfg<N>::smem_bytes()));
+    return e;
+}
+
+int znl_per_sm()
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_znl<N>, 256, ZCfg<N>::smem_bytes()) != cudaSuccess)
+        return 0;
+    return per_sm;
+}
+
+template <int T>
+void launch_cols(Pass pass, int mode, const Geo &g, MemberDev *md, int stage, int last, int arg, cudaStream_t s)
+{
+    constexpr int TC = ColCfg<N, T>::threads;
+    const dim3 grid_state(g.NK * g.NZp / T, g.members);
+    const int col_tiles_mid = N * g.NZp / T;
+    switch (pass) {
+    case Pass::IX:
+        if (mode == 0) k_inv_x<N, 0, T><<<grid_state, TC, smem_x<N, T>(), s>>>(g, arg);
+        break;
+    case Pass::IY:
+        // arg = number of fields, mode = first field
+        k_inv_y<N, T><<<dim3(col_tiles_mid, arg, g.members), TC, smem_cols<N, T>(), s>>>(g, mode);
+        break;
+    case Pass::FY:
+        k_fwd_y<N, T><<<dim3(col_tiles_mid, 3, g.members), TC, smem_cols<N, T>(), s>>>(g);
+        break;
+    case Pass::FX:
+        if (mode == 0) k_fwd_x<N, 0, T><<<grid_state, TC, smem_x<N, T>(), s>>>(g, md, stage, last);
+        break;
+    default: break;
+    }
+}
+
+void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last, int arg,
+            cudaStream_t s)
+{
+    constexpr int RZ = RowCfg<N>::RZ;
+    constexpr int TZ = RZ * RowCfg<N>::P;   // 256 threads, warp-local rows
+    constexpr int TC = ColCfg<N, 16>::threads;
+    const dim3 grid_state(g.NK * g.NZp / 16, g.members);
+    switch (pass) {
+    case Pass::IX:
+        if (mode == 0) {
+            if (g.tile_x == 8) launch_cols<8>(pass, mode, g, md, stage, last, arg, s);
+            else launch_cols<16>(pass, mode, g, md, stage, last, arg, s);
+        } else {
+            k_inv_x<N, 1, 16><<<grid_state, TC, smem_x<N, 16>(), s>>>(g, arg);
+        }
+        break;
+    case Pass::IY:
+    case Pass::FY:
+        if (g.tile_y == 8) launch_cols<8>(pass, mode, g, md, stage, last, arg, s);
+        else launch_cols<16>(pass, mode, g, md, stage, last, arg, s);
+        break;
+    case Pass::Z: {
+        const dim3 grid(N * N / RZ, g.members);
+        switch (mode) {
+        case 0:
+            if (g.z_mode == 1) k_z<N, 0><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage);
+            else k_znl<N><<<g.z_ctas, 256, ZCfg<N>::smem_bytes(), s>>>(g, md, stage);
+            break;
+        case 1: k_z<N, 1><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
+        case 3: k_z<N, 3><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
+        default: k_z<N, 4><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
+        }
+        break;
+    }
+    case Pass::FX:
+        switch (mode) {
+        case 0:
+            if (g.tile_x == 8) launch_cols<8>(pass, mode, g, md, stage, last, arg, s);
+            else launch_cols<16>(pass, mode, g, md, stage, last, arg, s);
+            break;
+        case 1: k_fwd_x<N, 1, 16><<<grid_state, TC, smem_x<N, 16>(), s>>>(g, md, stage, last); break;
+        case 2: k_fwd_x<N, 2, 16><<<grid_state, TC, smem_x<N, 16>(), s>>>(g, md, stage, last); break;
+        default: k_fwd_x<N, 3, 16><<<grid_state, TC, smem_x<N, 16>(), s>>>(g, md, stage, last); break;
+        }
+        break;
+    case Pass::ZSTAT: {
+        const long long rows = (long long)N * N;
+        const dim3 grid((unsigned)((rows + (long long)RZ * kStatsIters - 1) / ((long long)RZ * kStatsIters)),
+                        g.members);
+        k_z_stats<N><<<grid, TZ, smem_stats<N>(h->nq, h->nt, h->ng), s>>>(g, *h, md);
+        break;
+    }
+    }
+}
+
+const SizedOps kOps = {prepare, znl_per_sm, launch};
+
+}  // namespace
+
+template <>
+const SizedOps *sized_ops_for<ENS_N>()
+{
+    return &kOps;
+}
+
+}  // namespace ens

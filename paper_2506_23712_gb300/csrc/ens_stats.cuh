@@ -5,8 +5,10 @@
 // B); A_33 = -A_11 - A_22 by incompressibility.  Per grid point:
 //   Q = -1/2 Tr A^2, R = -1/3 Tr A^3            (Sec. V)
 //   eps = 2 nu Tr S^2, omega^2 = |omega|^2       (Sec. VI)
-// binned into the joint Q-R histogram (units q0 = eps_norm / (2 nu_norm)) and
-// log10 histograms of eps/eps_norm and omega^2 nu_norm/eps_norm.  Bin rule:
+// binned into the joint Q-R histogram (units q0 = eps_norm / (2 nu_norm)),
+// log10 histograms of eps/eps_norm and omega^2 nu_norm/eps_norm and, when
+// requested, linear histograms of the gradient components A_ij / sqrt(q0)
+// (longitudinal and transverse pooled separately, Sec. VI).  Bin rule:
 // bin b iff edge[b] <= x < edge[b+1] on FP32 edges (estimate from the affine
 // or log10 map, then corrected against the edge table, so the decision is
 // exactly the edge comparison).  Counts go to per-CTA shared-memory
@@ -58,10 +60,10 @@ __device__ __forceinline__ float warp_sum(float v)
 }
 
 template <int N>
-constexpr size_t smem_stats(int nq, int nt)
+constexpr size_t smem_stats(int nq, int nt, int ng)
 {
-    return smem_rows<N>() + sizeof(unsigned) * ((size_t)nq * nq + 2 * nt + 8) +
-           sizeof(float) * (2 * (nq + 1) + nt + 1) + sizeof(double) * 8 * kNMom + 64;
+    return smem_rows<N>() + sizeof(unsigned) * (size_t)counts_len_of(nq, nt, ng) +
+           sizeof(float) * (2 * (nq + 1) + nt + 1 + ng + 1) + sizeof(double) * 8 * kNMom + 64;
 }
 
 template <int N>
@@ -78,14 +80,16 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     float *eq = reinterpret_cast<float *>(hist + L);
     float *er = eq + (h.nq + 1);
     float *et = er + (h.nq + 1);
+    float *eg = et + (h.nt + 1);
     double *wmom = reinterpret_cast<double *>(
-        (reinterpret_cast<uintptr_t>(et + h.nt + 1) + 15) & ~(uintptr_t)15);
+        (reinterpret_cast<uintptr_t>(eg + h.ng + 1) + 15) & ~(uintptr_t)15);
     for (int i = threadIdx.x; i < L; i += blockDim.x) hist[i] = 0u;
     for (int i = threadIdx.x; i <= h.nq; i += blockDim.x) {
         eq[i] = h.edges_q[i];
         er[i] = h.edges_r[i];
     }
     for (int i = threadIdx.x; i <= h.nt; i += blockDim.x) et[i] = h.edges_t[i];
+    for (int i = threadIdx.x; i <= h.ng && h.ng > 0; i += blockDim.x) eg[i] = h.edges_g[i];
     for (int i = threadIdx.x; i < 8 * kNMom; i += blockDim.x) wmom[i] = 0.0;
     load_twiddles(tw, g.tw, N);
 
@@ -96,6 +100,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     const long long nrows = (long long)N * N;
     auto at = [&](int pos) { return row_slot<N>(buf, r, pos); };
     const int off_e = h.nq * h.nq, off_w = off_e + h.nt, off_c = off_w + h.nt;
+    const int off_gl = off_c + 8, off_gt = off_gl + h.ng, off_gc = off_gt + h.ng;
     int valid_rows = 0;
 
 #pragma unroll 1
@@ -162,6 +167,22 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
             warp_count(hist, kq);
             warp_count(hist, ke);
             warp_count(hist, kw);
+            if (h.ng > 0) {
+                // gradient components (longitudinal c = 0, 4, 8 pooled; the
+                // six transverse ones pooled), finite points only
+#pragma unroll
+                for (int c = 0; c < 9; ++c) {
+                    int kg = -1;
+                    if (row_ok && finite) {
+                        const float x = A[c / 3][c % 3] * h.g_scale;
+                        const int bg = bin_lin(x, h.g_lo, h.g_inv_w, eg, h.ng);
+                        const bool lon = c % 4 == 0;
+                        kg = bg < 0 ? off_gc + (lon ? 0 : 2)
+                                    : (bg >= h.ng ? off_gc + (lon ? 1 : 3) : (lon ? off_gl : off_gt) + bg);
+                    }
+                    warp_count(hist, kg);
+                }
+            }
         }
         // moments: sums of A_c^p (p = 2, 3, 4, 6) and of the invariants
         const float inv_vals[8] = {sQ, sR, sE, sW, sQ2, sR2, sE2, sW2};

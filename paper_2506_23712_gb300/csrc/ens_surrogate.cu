@@ -598,7 +598,7 @@ void make_targets(int n, const uint64_t *counts, const ens_hist_spec *h, std::ve
 {
     const int nq = h->qr_bins, nt = h->tail_bins;
     const int per = nq * nq + 2 * nt;
-    const long long L = (long long)nq * nq + 2LL * nt + 8;
+    const long long L = counts_len_of(nq, nt, h->grad_bins);
     t.assign((size_t)n * per, 0.f);
     for (int i = 0; i < n; ++i) {
         const uint64_t *c = counts + (size_t)i * L;

@@ -44,7 +44,8 @@ class MemberDesc(ctypes.Structure):
 class HistSpec(ctypes.Structure):
     _fields_ = [("qr_bins", ctypes.c_int), ("q_lim", ctypes.c_double), ("r_lim", ctypes.c_double),
                 ("tail_bins", ctypes.c_int), ("tail_lo", ctypes.c_double), ("tail_hi", ctypes.c_double),
-                ("eps_norm", ctypes.c_double), ("nu_norm", ctypes.c_double)]
+                ("eps_norm", ctypes.c_double), ("nu_norm", ctypes.c_double), ("grad_bins", ctypes.c_int),
+                ("grad_lim", ctypes.c_double)]
 
 
 class Diag(ctypes.Structure):
@@ -61,7 +62,8 @@ class MixtureOut(ctypes.Structure):
     _fields_ = [("weights", ctypes.POINTER(ctypes.c_double)), ("covered", ctypes.c_double),
                 ("pdf_qr", ctypes.POINTER(ctypes.c_double)), ("pdf_eps", ctypes.POINTER(ctypes.c_double)),
                 ("pdf_ens", ctypes.POINTER(ctypes.c_double)), ("moments", ctypes.POINTER(ctypes.c_double)),
-                ("ratios", ctypes.c_double * 5)]
+                ("ratios", ctypes.c_double * 5), ("pdf_long", ctypes.POINTER(ctypes.c_double)),
+                ("pdf_trans", ctypes.POINTER(ctypes.c_double))]
 
 
 ENS_ZETA_QUADRATIC, ENS_ZETA_LOGPOISSON, ENS_ZETA_RATIONAL = 0, 1, 2
@@ -70,6 +72,20 @@ ENS_LAMBDA_GRID, ENS_LAMBDA_GRID_LO, ENS_LAMBDA_GRID_HI = 65536, -30.0, 30.0
 
 class ZetaSpec(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("c", ctypes.c_double), ("beta", ctypes.c_double), ("C0", ctypes.c_double)]
+
+
+ENS_MAX_GROUPS = 8
+
+
+class GroupTuning(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("z_variant", ctypes.c_int), ("z_ctas_per_sm", ctypes.c_int)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int), ("parallel_groups", ctypes.c_int),
+                ("group", GroupTuning * ENS_MAX_GROUPS), ("ms_per_step", ctypes.c_double),
+                ("trials", ctypes.c_int)]
 
 
 # every symbol declared in include/ens.h: (name, restype, argtypes)
@@ -84,6 +100,9 @@ SIGNATURES = [
     ("ens_step", _i, [_vp, _i]),
     ("ens_step_nograph", _i, [_vp, _i]),
     ("ens_step_sequential", _i, [_vp, _i]),
+    ("ens_get_tuning", _i, [_vp, _P(Tuning)]),
+    ("ens_set_tuning", _i, [_vp, _P(Tuning)]),
+    ("ens_autotune", _i, [_vp, _i, _P(Tuning)]),
     ("ens_gradient_stats", _i, [_vp, _i]),
     ("ens_get_stats", _i, [_vp, _vp, _vp]),
     ("ens_counts_len", _i, [_P(HistSpec)]),
@@ -192,6 +211,37 @@ def ens_step_sequential(ctx, nsteps=1):
     _check(lib().ens_step_sequential(ctx, nsteps), ctx)
 
 
+_GROUP_KEYS = ("N", "tile_x", "tile_y", "z_variant", "z_ctas_per_sm")
+
+
+def _tuning_dict(t: Tuning) -> dict:
+    return {"parallel_groups": t.parallel_groups,
+            "groups": [{k: getattr(t.group[i], k) for k in _GROUP_KEYS} for i in range(t.groups)],
+            "ms_per_step": t.ms_per_step, "trials": t.trials}
+
+
+def ens_get_tuning(ctx) -> dict:
+    t = Tuning()
+    _check(lib().ens_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return _tuning_dict(t)
+
+
+def ens_set_tuning(ctx, tuning: dict):
+    t = Tuning()
+    t.groups = len(tuning["groups"])
+    t.parallel_groups = int(tuning["parallel_groups"])
+    for i, g in enumerate(tuning["groups"]):
+        for k in _GROUP_KEYS:
+            setattr(t.group[i], k, int(g[k]))
+    _check(lib().ens_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def ens_autotune(ctx, steps=3) -> dict:
+    t = Tuning()
+    _check(lib().ens_autotune(ctx, steps, ctypes.byref(t)), ctx)
+    return _tuning_dict(t)
+
+
 def ens_gradient_stats(ctx, accumulate=True):
     _check(lib().ens_gradient_stats(ctx, int(bool(accumulate))), ctx)
 
@@ -220,6 +270,9 @@ def _mixture_out(n, hist):
     nq, nt = hist.qr_bins, hist.tail_bins
     bufs = {"weights": np.zeros(n), "pdf_qr": np.zeros(nq * nq), "pdf_eps": np.zeros(nt),
             "pdf_ens": np.zeros(nt), "moments": np.zeros(ENS_NMOM)}
+    if hist.grad_bins > 0:
+        bufs["pdf_long"] = np.zeros(hist.grad_bins)
+        bufs["pdf_trans"] = np.zeros(hist.grad_bins)
     out = MixtureOut()
     for k, v in bufs.items():
         setattr(out, k, v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
@@ -230,6 +283,7 @@ def _mixture_result(out, bufs, hist):
     nq = hist.qr_bins
     return {"weights": bufs["weights"], "covered": out.covered, "pdf_qr": bufs["pdf_qr"].reshape(nq, nq),
             "pdf_eps": bufs["pdf_eps"], "pdf_ens": bufs["pdf_ens"], "moments": bufs["moments"],
+            "pdf_long": bufs.get("pdf_long"), "pdf_trans": bufs.get("pdf_trans"),
             "ratios": dict(zip(("S_long", "F_long", "F_trans", "H_long", "H_trans"), list(out.ratios)))}
 
 
@@ -433,8 +487,8 @@ class Member:
 
 
 def hist_spec(qr_bins=64, q_lim=10.0, r_lim=10.0, tail_bins=256, tail_lo=-8.0, tail_hi=8.0, eps_norm=0.1,
-              nu_norm=0.01) -> HistSpec:
-    return HistSpec(qr_bins, q_lim, r_lim, tail_bins, tail_lo, tail_hi, eps_norm, nu_norm)
+              nu_norm=0.01, grad_bins=0, grad_lim=40.0) -> HistSpec:
+    return HistSpec(qr_bins, q_lim, r_lim, tail_bins, tail_lo, tail_hi, eps_norm, nu_norm, grad_bins, grad_lim)
 
 
 class Ensemble:
@@ -461,6 +515,46 @@ class Ensemble:
 
     def step(self, nsteps=1, graph=True):
         (ens_step if graph else ens_step_nograph)(self.ctx, nsteps)
+
+    def tuning(self) -> dict:
+        return ens_get_tuning(self.ctx)
+
+    def set_tuning(self, tuning: dict):
+        ens_set_tuning(self.ctx, tuning)
+
+    def tuning_key(self) -> str:
+        """Cache key of a tuning: device name, RK order and the member count
+        per grid size."""
+        import torch
+        sizes = {}
+        for m in self.members:
+            sizes[m.N] = sizes.get(m.N, 0) + 1
+        return "%s|rk%d|%s" % (torch.cuda.get_device_name(), self.members[0].rk_order,
+                                ",".join("%dx%d" % (c, n) for n, c in sorted(sizes.items())))
+
+    def autotune(self, steps=3, cache: Optional[str] = None) -> dict:
+        """Install the fastest pass variants for this ensemble.  With a cache
+        path (a JSON file), a tuning stored under this ensemble's key is
+        installed without timing anything; otherwise the library times the
+        variants (ens_autotune) and the result is stored there."""
+        import json
+        import os
+        key = self.tuning_key()
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                self.set_tuning(table[key])
+                return dict(table[key], cached=True)
+        t = ens_autotune(self.ctx, steps)
+        if cache:
+            table[key] = t
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(t, cached=False)
 
     def gradient_stats(self, accumulate=True):
         ens_gradient_stats(self.ctx, accumulate)

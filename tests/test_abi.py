@@ -60,6 +60,8 @@ def test_query_validates_on_host(lib):
 
 def test_counts_len(lib):
     assert E.ens_counts_len(E.hist_spec(qr_bins=64, tail_bins=256)) == 64 * 64 + 512 + 8
+    # gradient-component histograms append 2 x grad_bins + 4 counters
+    assert E.ens_counts_len(E.hist_spec(qr_bins=64, tail_bins=256, grad_bins=100)) == 64 * 64 + 512 + 8 + 204
 
 
 def test_binding_refuses_without_gpu():

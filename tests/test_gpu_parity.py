@@ -211,6 +211,54 @@ def test_statistics_match_oracle(E):
     ens.close()
 
 
+def test_gradient_component_histograms_match_oracle(E):
+    """Longitudinal / transverse gradient-component histograms (Sec. VI
+    gradient PDFs) on the oracle's state: 2% in every bin above 1000 counts,
+    3 and 6 samples per point, the rest of the layout unchanged; their
+    mixture equals the oracle mixture of the same counts."""
+    m = config0(E, init_energy=2.0)
+    N = m.N
+    kw = dict(qr_bins=16, q_lim=10.0, r_lim=10.0, tail_bins=64, tail_lo=-8, tail_hi=8, eps_norm=0.1, nu_norm=0.02)
+    h = E.hist_spec(grad_bins=128, grad_lim=8.0, **kw)
+    oh = O.HistSpec(grad_bins=128, grad_lim=8.0, **kw)
+    assert E.ens_counts_len(h) == oh.counts_len
+    ens = E.Ensemble([m], hist=h)
+    ens.step(2)
+    om = oracle_member(m)
+    uh = O.initial_field(om)
+    assert O.step(om, uh, 2)[0] == 0
+    ens.gradient_stats(accumulate=False)
+    counts, mom = ens.stats()
+    rc, _ = O.gradient_stats(uh, m.nu, oh)
+    c, r = counts[0].astype(np.int64), rc.astype(np.int64)
+    off = 16 * 16 + 128 + 8
+    assert c[off - 2] == N ** 3
+    for lo, hi, k in ((off, off + 128, 3), (off + 128, off + 256, 6)):
+        g = c[lo:hi].sum() + c[off + 256 + (0 if k == 3 else 2)] + c[off + 256 + (1 if k == 3 else 3)]
+        assert g == k * N ** 3
+        big = r[lo:hi] > 1000
+        assert big.sum() >= 20
+        assert np.all(np.abs(c[lo:hi][big] - r[lo:hi][big]) <= 0.02 * r[lo:hi][big])
+    # the QR / tail part is the one a context without gradient bins produces
+    h0 = E.hist_spec(**kw)
+    ens0 = E.Ensemble([m], hist=h0)
+    ens0.step(2)
+    ens0.gradient_stats(accumulate=False)
+    c0, _ = ens0.stats()
+    assert np.array_equal(c0[0], counts[0][: len(c0[0])])
+    ens0.close()
+    # mixture of the gradient PDFs (one member, weight 1)
+    got = ens.mixture(kind=E.W_USER, user=[1.0], renormalize=False)
+    lon, tra = OM.mix_gradient_pdfs(counts, [1.0], oh)
+    assert np.allclose(got["pdf_long"], lon, rtol=1e-12, atol=1e-15)
+    assert np.allclose(got["pdf_trans"], tra, rtol=1e-12, atol=1e-15)
+    got = E.ens_mixture_host([0.0], counts, mom, h, kind=E.W_USER, user=[1.0], renormalize=False)
+    assert np.allclose(got["pdf_long"], lon, rtol=1e-12, atol=1e-15)
+    got = E.ens_mixture_host_noalloc([0.0], counts, mom, h, kind=E.W_USER, user=[1.0], renormalize=False)
+    assert np.allclose(got["pdf_trans"], tra, rtol=1e-12, atol=1e-15)
+    ens.close()
+
+
 def test_mixture_matches_oracle(E):
     lams = [-1.0, -0.3, 0.4, 1.1]
     ms = [E.Member(N=16, nu=0.05, lam=l, k_lo=1, k_hi=2, dt=0.01, rk_order=2, seed=i) for i, l in enumerate(lams)]
