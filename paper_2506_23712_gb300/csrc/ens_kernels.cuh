@@ -25,12 +25,44 @@
 
 namespace ens {
 
+// Geometry of a grid size, known at compile time (the host's Geo carries the
+// same values: kc = ceil(N/3) - 1, NK = 2 kc + 1, NZ = kc + 1, NZp = NZ
+// rounded up to kTile), so index arithmetic folds into constants.
+template <int N>
+struct Dims {
+    static constexpr int KC = (N + 2) / 3 - 1;
+    static constexpr int NK = 2 * KC + 1;
+    static constexpr int NZ = KC + 1;
+    static constexpr int NZP = (NZ + kTile - 1) / kTile * kTile;
+    static constexpr long long SU = (long long)NK * NK * NZP;   // per state component
+    static constexpr long long SA = (long long)NK * N * NZP;    // per buffer-A field
+    static constexpr long long SB = (long long)N * N * NZP;     // per buffer-B field
+};
+
+// Shared-memory slot of position pos of a warp-local line.  For the large
+// sizes an XOR swizzle permutes the 16 slots of every 16-aligned block by a
+// 4-bit mask of that block (table packed into two 64-bit words), chosen by an
+// offline search over every access pattern of the line transforms (the pass
+// exchanges, the output stores, the Hermitian unpacking reads) so that each
+// half-warp request of 8-byte words meets 16 distinct bank pairs; the small
+// sizes keep an additive padding.
+template <int N>
+struct RowSwz {
+    static constexpr bool on = false;
+    static constexpr unsigned long long lo = 0, hi = 0;
+};
+template <> struct RowSwz<128> { static constexpr bool on = true; static constexpr unsigned long long lo = 0x7ed43a90ull, hi = 0; };
+template <> struct RowSwz<256> { static constexpr bool on = true; static constexpr unsigned long long lo = 0x01ab45effe54ba10ull, hi = 0; };
+template <> struct RowSwz<384> { static constexpr bool on = true; static constexpr unsigned long long lo = 0xf906c1a7af41872dull, hi = 0xd42bc2b5ull; };
+template <> struct RowSwz<512> { static constexpr bool on = true; static constexpr unsigned long long lo = 0xf01695843ea7bd2cull, hi = 0xcc22bb3311504988ull; };
+
 // rows handled per CTA by the z-direction passes
 template <int N>
 struct RowCfg {
     static constexpr int P = WPlanInfo<N>::P;     // threads per row (warp-local lines)
     static constexpr int RZ = 256 / P;            // rows per 256-thread CTA
-    static constexpr int SROW = N + N / 16 + N / 32 + 1;   // padded shared row stride (float2)
+    // shared row stride (float2): swizzled rows are dense, padded rows are not
+    static constexpr int SROW = RowSwz<N>::on ? N : N + N / 16 + N / 32 + 1;
 };
 
 // Column-tile passes (x and y) take the tile width T (columns per CTA, a
@@ -82,14 +114,15 @@ k_inv_x(Geo g, int use_S)
     const int m = blockIdx.y;
     const int col0 = blockIdx.x * T;                    // a tile never straddles ky (NZp % T == 0)
     const int col = col0 + c;
-    const int iy = col / g.NZp, kz = col % g.NZp;
-    const bool valid = kz < g.NZ;
-    const float ky = (float)(iy <= g.kc ? iy : iy - g.NK);
+    const int iy = col / Dims<N>::NZP, kz = col % Dims<N>::NZP;
+    const int kz0 = col0 % Dims<N>::NZP;                  // first kz of the tile
+    const bool valid = kz < Dims<N>::NZ;
+    const float ky = (float)(iy <= Dims<N>::KC ? iy : iy - Dims<N>::NK);
     const float kzf = (float)kz;
-    const long long rowU = (long long)g.NK * g.NZp;
-    const float2 *X = (use_S ? g.S : g.U) + (long long)m * 3 * g.sU + col0;
+    const long long rowU = (long long)Dims<N>::NK * Dims<N>::NZP;
+    const float2 *X = (use_S ? g.S : g.U) + (long long)m * 3 * Dims<N>::SU + col0;
     // coalesced staging of the three velocity components of this column tile
-    const int per = g.NK * T;
+    constexpr int per = Dims<N>::NK * T;
     constexpr int kBatch = 8;   // loads in flight per thread before the shared stores
     for (int base = threadIdx.x; base < 3 * per; base += kBatch * blockDim.x) {
         float2 tmp[kBatch];
@@ -100,7 +133,7 @@ k_inv_x(Geo g, int use_S)
             if (idx < 3 * per) {
                 const int q = idx / per, rem = idx % per;
                 const int ix = rem / T, cc = rem % T;
-                if (((col0 + cc) % g.NZp) < g.NZ) tmp[k] = X[q * g.sU + ix * rowU + cc];
+                if (kz0 + cc < Dims<N>::NZ) tmp[k] = X[q * Dims<N>::SU + ix * rowU + cc];
             }
         }
 #pragma unroll
@@ -111,7 +144,7 @@ k_inv_x(Geo g, int use_S)
     }
     load_twiddles(tw, g.tw, N);   // block barrier: tile complete
 
-    float2 *dst0 = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
+    float2 *dst0 = g.A + (long long)m * kFields * Dims<N>::SA + ((long long)iy * N) * Dims<N>::NZP + kz;
     auto at = [&](int pos) { return &buf[pos * T + c]; };
     // transform of component q of the tile, optionally times i kx (the x
     // derivative: kx varies along this transform, so it is applied before it)
@@ -119,8 +152,8 @@ k_inv_x(Geo g, int use_S)
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const int kxi = wnum(PI::in_pos(p, i), N);
-            const bool keep = kxi >= -g.kc && kxi <= g.kc;
-            const int ix = kxi >= 0 ? kxi : kxi + g.NK;
+            const bool keep = kxi >= -Dims<N>::KC && kxi <= Dims<N>::KC;
+            const int ix = kxi >= 0 ? kxi : kxi + Dims<N>::NK;
             const float2 u = keep ? tile[q * per + ix * T + c] : make_float2(0.f, 0.f);
             v[i] = dx ? mul_i(cscale(u, (float)kxi)) : u;
         }
@@ -128,9 +161,9 @@ k_inv_x(Geo g, int use_S)
     };
     auto store = [&](const float2 *v, int f) {
         if (valid) {
-            float2 *dst = dst0 + (long long)f * g.sA;
+            float2 *dst = dst0 + (long long)f * Dims<N>::SA;
 #pragma unroll
-            for (int i = 0; i < V; ++i) dst[(long long)PI::out_pos(p, i) * g.NZp] = v[i];
+            for (int i = 0; i < V; ++i) dst[(long long)PI::out_pos(p, i) * Dims<N>::NZP] = v[i];
         }
     };
     // ky and kz are constant along x, so their derivatives are applied after
@@ -193,16 +226,16 @@ k_inv_y(Geo g, int f0)
     const int c = threadIdx.x % T, p = threadIdx.x / T;
     const int f = f0 + blockIdx.y, m = blockIdx.z;
     const int col = blockIdx.x * T + c;       // (x, kz) flat
-    const bool valid = (col % g.NZp) < g.NZ;
-    const long long row = (long long)N * g.NZp;
-    const float2 *src = g.A + ((long long)m * kFields + f) * g.sA + col;
-    float2 *dst = g.B + ((long long)m * kFields + f) * g.sB + col;
+    const bool valid = (col % Dims<N>::NZP) < Dims<N>::NZ;
+    const long long row = (long long)N * Dims<N>::NZP;
+    const float2 *src = g.A + ((long long)m * kFields + f) * Dims<N>::SA + col;
+    float2 *dst = g.B + ((long long)m * kFields + f) * Dims<N>::SB + col;
     float2 v[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) {
         const int ky = wnum(PI::in_pos(p, i), N);
-        const bool keep = valid && ky >= -g.kc && ky <= g.kc;
-        const int iy = ky >= 0 ? ky : ky + g.NK;
+        const bool keep = valid && ky >= -Dims<N>::KC && ky <= Dims<N>::KC;
+        const int iy = ky >= 0 ? ky : ky + Dims<N>::NK;
         v[i] = keep ? src[iy * row] : make_float2(0.f, 0.f);
     }
     fft_line<N, false>(v, p, tw, [&](int pos) { return &buf[pos * T + c]; });
@@ -228,10 +261,10 @@ k_fwd_y(Geo g)
     const int c = threadIdx.x % T, p = threadIdx.x / T;
     const int f = blockIdx.y, m = blockIdx.z;
     const int col = blockIdx.x * T + c;
-    const bool valid = (col % g.NZp) < g.NZ;
-    const long long row = (long long)N * g.NZp;
-    const float2 *src = g.B + ((long long)m * kFields + f) * g.sB + col;
-    float2 *dst = g.A + ((long long)m * kFields + f) * g.sA + col;
+    const bool valid = (col % Dims<N>::NZP) < Dims<N>::NZ;
+    const long long row = (long long)N * Dims<N>::NZP;
+    const float2 *src = g.B + ((long long)m * kFields + f) * Dims<N>::SB + col;
+    float2 *dst = g.A + ((long long)m * kFields + f) * Dims<N>::SA + col;
     float2 v[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) v[i] = valid ? src[PI::in_pos(p, i) * row] : make_float2(0.f, 0.f);
@@ -240,7 +273,7 @@ k_fwd_y(Geo g)
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const int ky = wnum(PI::out_pos(p, i), N);
-            if (ky >= -g.kc && ky <= g.kc) dst[(ky >= 0 ? ky : ky + g.NK) * row] = v[i];
+            if (ky >= -Dims<N>::KC && ky <= Dims<N>::KC) dst[(ky >= 0 ? ky : ky + Dims<N>::NK) * row] = v[i];
         }
     }
 }
@@ -252,10 +285,14 @@ k_fwd_y(Geo g)
 template <int N>
 __device__ __forceinline__ float2 *row_slot(float2 *buf, int r, int pos)
 {
-    // padding chosen (by simulating the bank mapping of the warp-local
-    // exchanges) so that the pass exchanges are close to conflict-free:
-    // two-pass plans want one pad per 16 slots, three-pass plans one more
-    // per 32
+    using SW = RowSwz<N>;
+    if constexpr (SW::on) {
+        const int blk = pos >> 4;
+        const unsigned long long w = (N <= 256 || blk < 16) ? SW::lo : SW::hi;
+        return &buf[r * RowCfg<N>::SROW + (pos ^ (int)((w >> ((blk & 15) * 4)) & 15ull))];
+    }
+    // small sizes: one pad per 16 slots (two-pass plans), one more per 32
+    // (three-pass plans)
     if constexpr (WPlanInfo<N>::NP == 2) return &buf[r * RowCfg<N>::SROW + pos + (pos >> 4)];
     else return &buf[r * RowCfg<N>::SROW + pos + (pos >> 4) + (pos >> 5)];
 }
@@ -339,7 +376,7 @@ k_z(Geo g, MemberDev *md, int stage)
     const int m = blockIdx.y;
     const long long rho = (long long)blockIdx.x * RZ + r;   // row = y*N + x
     const int yy = (int)(rho / N), xx = (int)(rho % N);
-    float2 *B = g.B + (long long)m * kFields * g.sB + rho * g.NZp;
+    float2 *B = g.B + (long long)m * kFields * Dims<N>::SB + rho * Dims<N>::NZP;
     auto at = [&](int pos) { return row_slot<N>(buf, r, pos); };
 
     float2 w0[V], w1[V];   // forward inputs in first-pass order
@@ -347,21 +384,21 @@ k_z(Geo g, MemberDev *md, int stage)
         float2 a[V], b[V], cc[V];
         // all loads first (memory-level parallelism), then the transforms
 #pragma unroll
-        for (int i = 0; i < V; ++i) a[i] = pair_at(B, B + g.sB, PI::in_pos(p, i), N, g.kc);
+        for (int i = 0; i < V; ++i) a[i] = pair_at(B, B + Dims<N>::SB, PI::in_pos(p, i), N, Dims<N>::KC);
         if constexpr (MODE == 3) {
 #pragma unroll
-            for (int i = 0; i < V; ++i) b[i] = pair_at(B + 2 * g.sB, B + 2 * g.sB, PI::in_pos(p, i), N, g.kc);
+            for (int i = 0; i < V; ++i) b[i] = pair_at(B + 2 * Dims<N>::SB, B + 2 * Dims<N>::SB, PI::in_pos(p, i), N, Dims<N>::KC);
         } else {
 #pragma unroll
-            for (int i = 0; i < V; ++i) b[i] = pair_at(B + 2 * g.sB, B + 3 * g.sB, PI::in_pos(p, i), N, g.kc);
+            for (int i = 0; i < V; ++i) b[i] = pair_at(B + 2 * Dims<N>::SB, B + 3 * Dims<N>::SB, PI::in_pos(p, i), N, Dims<N>::KC);
 #pragma unroll
-            for (int i = 0; i < V; ++i) cc[i] = pair_at(B + 4 * g.sB, B + 5 * g.sB, PI::in_pos(p, i), N, g.kc);
+            for (int i = 0; i < V; ++i) cc[i] = pair_at(B + 4 * Dims<N>::SB, B + 5 * Dims<N>::SB, PI::in_pos(p, i), N, Dims<N>::KC);
         }
         fft_line_warp<N, false>(a, p, tw, at);
         fft_line_warp<N, false>(b, p, tw, at);
         if constexpr (MODE == 3) {
             // physical u_c(x, y, z) into A viewed as floats [member][3][x][y][z]
-            float *out = reinterpret_cast<float *>(g.A + (long long)m * kFields * g.sA);
+            float *out = reinterpret_cast<float *>(g.A + (long long)m * kFields * Dims<N>::SA);
             const long long n3 = (long long)N * N * N;
             const long long base = ((long long)xx * N + yy) * N;
 #pragma unroll
@@ -421,7 +458,7 @@ k_z(Geo g, MemberDev *md, int stage)
             w1[i] = make_float2(white_noise(seed, 2 * n3 + idx), 0.f);
         }
     } else if constexpr (MODE == 4) {
-        const float *in = reinterpret_cast<const float *>(g.A + (long long)m * kFields * g.sA);
+        const float *in = reinterpret_cast<const float *>(g.A + (long long)m * kFields * Dims<N>::SA);
         const long long n3 = (long long)N * N * N;
         const long long base = ((long long)xx * N + yy) * N;
 #pragma unroll
@@ -434,8 +471,8 @@ k_z(Geo g, MemberDev *md, int stage)
     if constexpr (MODE == 1 || MODE == 4) {
         __syncwarp();   // all threads reach the stores below after their loads
     }
-    forward_pair_store<N>(w0, p, r, tw, buf, B, B + g.sB, g.NZ, true);
-    forward_pair_store<N>(w1, p, r, tw, buf, B + 2 * g.sB, nullptr, g.NZ, true);
+    forward_pair_store<N>(w0, p, r, tw, buf, B, B + Dims<N>::SB, Dims<N>::NZ, true);
+    forward_pair_store<N>(w1, p, r, tw, buf, B + 2 * Dims<N>::SB, nullptr, Dims<N>::NZ, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -508,30 +545,31 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
     const int m = blockIdx.y;
     const int col0 = blockIdx.x * T;
     const int col = col0 + c;                                  // (ky, kz) flat
-    const int iy = col / g.NZp, kz = col % g.NZp;
-    const bool valid = kz < g.NZ;
-    const int per = g.NK * T;
-    const float2 *Ain = g.A + (long long)m * kFields * g.sA + ((long long)iy * N) * g.NZp + kz;
+    const int iy = col / Dims<N>::NZP, kz = col % Dims<N>::NZP;
+    const int kz0 = col0 % Dims<N>::NZP;                  // first kz of the tile
+    const bool valid = kz < Dims<N>::NZ;
+    constexpr int per = Dims<N>::NK * T;
+    const float2 *Ain = g.A + (long long)m * kFields * Dims<N>::SA + ((long long)iy * N) * Dims<N>::NZP + kz;
     auto at = [&](int pos) { return &buf[pos * T + c]; };
     // forward transforms of the three components; kept rows to the tile.
     // The next component's inputs are loaded while this one is transformed.
     float2 v[V], nxt[V];
 #pragma unroll
     for (int i = 0; i < V; ++i)
-        v[i] = valid ? Ain[(long long)PI::in_pos(p, i) * g.NZp] : make_float2(0.f, 0.f);
+        v[i] = valid ? Ain[(long long)PI::in_pos(p, i) * Dims<N>::NZP] : make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int q = 0; q < 3; ++q) {
         if (q < 2) {
 #pragma unroll
             for (int i = 0; i < V; ++i)
-                nxt[i] = valid ? Ain[(long long)(q + 1) * g.sA + (long long)PI::in_pos(p, i) * g.NZp]
+                nxt[i] = valid ? Ain[(long long)(q + 1) * Dims<N>::SA + (long long)PI::in_pos(p, i) * Dims<N>::NZP]
                                : make_float2(0.f, 0.f);
         }
         fft_line<N, true>(v, p, tw, at);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const int kx = wnum(PI::out_pos(p, i), N);
-            if (kx >= -g.kc && kx <= g.kc) tile[q * per + (kx >= 0 ? kx : kx + g.NK) * T + c] = v[i];
+            if (kx >= -Dims<N>::KC && kx <= Dims<N>::KC) tile[q * per + (kx >= 0 ? kx : kx + Dims<N>::NK) * T + c] = v[i];
         }
         if (q < 2) {
 #pragma unroll
@@ -542,10 +580,10 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
 
     const MemberDev &d = md[g.first + m];
     const float inv_n3 = 1.0f / ((float)N * (float)N * (float)N);
-    const long long rowU = (long long)g.NK * g.NZp;
-    float2 *U = g.U + (long long)m * 3 * g.sU + col0;
-    float2 *S = g.S + (long long)m * 3 * g.sU + col0;
-    const int kyi = iy <= g.kc ? iy : iy - g.NK;
+    const long long rowU = (long long)Dims<N>::NK * Dims<N>::NZP;
+    float2 *U = g.U + (long long)m * 3 * Dims<N>::SU + col0;
+    float2 *S = g.S + (long long)m * 3 * Dims<N>::SU + col0;
+    const int kyi = iy <= Dims<N>::KC ? iy : iy - Dims<N>::NK;
     float se = 0.f, sd = 0.f, sb = 0.f;
     float dtf = 0.f, alpha = 0.f, nu = 0.f;
     StageCoef co{};
@@ -571,12 +609,12 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
             for (int u = 0; u < UB; ++u) {
                 const int idx = base + u * blockDim.x;
                 const int cc = idx % T;
-                const bool ok = idx < per && ((col0 + cc) % g.NZp) < g.NZ;
+                const bool ok = idx < per && kz0 + cc < Dims<N>::NZ;
                 const long long off = (long long)(idx / T) * rowU + cc;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    unb[u][q] = ok ? U[q * g.sU + off] : make_float2(0.f, 0.f);
-                    usb[u][q] = (ok && stage != 0) ? S[q * g.sU + off] : unb[u][q];
+                    unb[u][q] = ok ? U[q * Dims<N>::SU + off] : make_float2(0.f, 0.f);
+                    usb[u][q] = (ok && stage != 0) ? S[q * Dims<N>::SU + off] : unb[u][q];
                 }
             }
         }
@@ -585,9 +623,9 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
         const int idx = base + u * blockDim.x;
         if (idx >= per) continue;
         const int ix = idx / T, cc = idx % T;
-        const int kzc = (col0 + cc) % g.NZp;
-        if (kzc >= g.NZ) continue;
-        const int kx = ix <= g.kc ? ix : ix - g.NK;
+        const int kzc = kz0 + cc;
+        if (kzc >= Dims<N>::NZ) continue;
+        const int kx = ix <= Dims<N>::KC ? ix : ix - Dims<N>::NK;
         const float fk[3] = {(float)kx, (float)kyi, (float)kzc};
         const int k2i = kx * kx + kyi * kyi + kzc * kzc;
         const float k2 = (float)k2i;
@@ -610,7 +648,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
         const float wgt = kzc == 0 ? 1.f : 2.f;   // Hermitian multiplicity in the full spectrum
         if constexpr (MODE == 2 || MODE == 3) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) U[q * g.sU + off] = n[q];
+            for (int q = 0; q < 3; ++q) U[q * Dims<N>::SU + off] = n[q];
             if constexpr (MODE == 2) {
                 const int s = (int)lrintf(sqrtf(k2));
                 float a2 = 0.f;
@@ -629,7 +667,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
             }
             if constexpr (MODE == 1) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) S[q * g.sU + off] = n[q];
+                for (int q = 0; q < 3; ++q) S[q * Dims<N>::SU + off] = n[q];
             } else {
                 const float ea = co.a != 0.f ? expf(-nu * k2 * co.ha * dtf) : 0.f;
                 const float eb = expf(-nu * k2 * co.hb * dtf);
@@ -640,7 +678,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
                     const float rx = us[q].x + dtf * n[q].x, ry = us[q].y + dtf * n[q].y;
                     const float ox = co.a * ea * un[q].x + co.b * eb * rx;
                     const float oy = co.a * ea * un[q].y + co.b * eb * ry;
-                    dst[q * g.sU + off] = make_float2(ox, oy);
+                    dst[q * Dims<N>::SU + off] = make_float2(ox, oy);
                     a2 += ox * ox + oy * oy;
                 }
                 se += 0.5f * wgt * a2;

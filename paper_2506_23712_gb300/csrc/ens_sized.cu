@@ -5,6 +5,8 @@
 #include "ens_stats.cuh"
 #include "ens_znl.cuh"
 
+#include <cstdio>
+
 #ifndef ENS_N
 #error "compile with -DENS_N=<grid size>"
 #endif
@@ -81,6 +83,13 @@ void launch_cols(Pass pass, int mode, const Geo &g, MemberDev *md, int stage, in
 void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last, int arg,
             cudaStream_t s)
 {
+    // the kernels take the geometry from Dims<N>; a Geo built otherwise is a bug
+    using D = Dims<N>;
+    if (g.N != N || g.kc != D::KC || g.NK != D::NK || g.NZ != D::NZ || g.NZp != D::NZP || g.sU != D::SU ||
+        g.sA != D::SA || g.sB != D::SB) {
+        fprintf(stderr, "libens: geometry of N=%d does not match its compiled layout\n", N);
+        return;
+    }
     constexpr int RZ = RowCfg<N>::RZ;
     constexpr int TZ = RZ * RowCfg<N>::P;   // 256 threads, warp-local rows
     constexpr int TC = ColCfg<N, 16>::threads;

@@ -111,13 +111,13 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
             const long long first_row = ((long long)blockIdx.x * kStatsIters + it) * RZ;
             valid_rows += (int)max(0LL, min((long long)RZ, nrows - first_row));
         }
-        const float2 *B = g.B + (long long)m * kFields * g.sB + (row_ok ? rho : 0) * g.NZp;
+        const float2 *B = g.B + (long long)m * kFields * Dims<N>::SB + (row_ok ? rho : 0) * Dims<N>::NZP;
         float2 v[4][V];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
 #pragma unroll
             for (int i = 0; i < V; ++i)
-                v[q][i] = row_ok ? pair_at(B + (2 * q) * g.sB, B + (2 * q + 1) * g.sB, PI::in_pos(p, i), N, g.kc)
+                v[q][i] = row_ok ? pair_at(B + (2 * q) * Dims<N>::SB, B + (2 * q + 1) * Dims<N>::SB, PI::in_pos(p, i), N, Dims<N>::KC)
                                  : make_float2(0.f, 0.f);
             fft_line_warp<N, false>(v[q], p, tw, at);
         }

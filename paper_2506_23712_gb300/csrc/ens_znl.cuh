@@ -92,14 +92,14 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
     const uint32_t bytes = (uint32_t)(LPW * 6 * NZ2 * sizeof(float2));
     auto issue = [&](long long gi, int b) {   // lane 0 only
         const long long m = gi / G, lg = gi % G;
-        const float2 *src = g.B + m * kFields * g.sB + (lg * LPW) * g.NZp;
+        const float2 *src = g.B + m * kFields * Dims<N>::SB + (lg * LPW) * Dims<N>::NZP;
         float2 *dst = st + b * C::STAGE;
         mbar_arrive_expect_tx(&bar[b], bytes);
 #pragma unroll 1
         for (int l = 0; l < LPW; ++l)
 #pragma unroll
             for (int f = 0; f < 6; ++f)
-                bulk_g2s(dst + (l * 6 + f) * NZ2, src + f * g.sB + l * g.NZp, NZ2 * (uint32_t)sizeof(float2),
+                bulk_g2s(dst + (l * 6 + f) * NZ2, src + f * Dims<N>::SB + l * Dims<N>::NZP, NZ2 * (uint32_t)sizeof(float2),
                          &bar[b]);
     };
     if (lane == 0 && grp < T) issue(grp, 0);
@@ -143,9 +143,9 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const int pos = PI::in_pos(p, i);
-            a[i] = pair_at(X, X + NZ2, pos, N, g.kc);
-            bb[i] = pair_at(X + 2 * NZ2, X + 3 * NZ2, pos, N, g.kc);
-            cc[i] = pair_at(X + 4 * NZ2, X + 5 * NZ2, pos, N, g.kc);
+            a[i] = pair_at(X, X + NZ2, pos, N, Dims<N>::KC);
+            bb[i] = pair_at(X + 2 * NZ2, X + 3 * NZ2, pos, N, Dims<N>::KC);
+            cc[i] = pair_at(X + 4 * NZ2, X + 5 * NZ2, pos, N, Dims<N>::KC);
         }
         fft_line_warp_tw<N, false>(a, p, TW, at);
         fft_line_warp_tw<N, false>(bb, p, TW, at);
@@ -161,9 +161,9 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
             w1[i] = make_float2(ux * wy - uy * wx, 0.f);
         }
         static_assert(PI::matched, "first and last radix must agree");
-        float2 *Bout = g.B + m * kFields * g.sB + rho * g.NZp;
-        forward_pair_store_tw<N>(w0, p, line, TW, rowbuf, Bout, Bout + g.sB, g.NZ);
-        forward_pair_store_tw<N>(w1, p, line, TW, rowbuf, Bout + 2 * g.sB, nullptr, g.NZ);
+        float2 *Bout = g.B + m * kFields * Dims<N>::SB + rho * Dims<N>::NZP;
+        forward_pair_store_tw<N>(w0, p, line, TW, rowbuf, Bout, Bout + Dims<N>::SB, Dims<N>::NZ);
+        forward_pair_store_tw<N>(w1, p, line, TW, rowbuf, Bout + 2 * Dims<N>::SB, nullptr, Dims<N>::NZ);
         __syncwarp();   // all lanes are done with buffer b before it is refilled
     }
     if (grp > (long long)blockIdx.x * C::WPB + warp || timed_out) flush(cur_m);

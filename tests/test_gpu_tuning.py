@@ -115,6 +115,26 @@ def test_invalid_tuning_rejected_and_context_usable(E):
     ens.close()
 
 
+def test_narrow_tiles_keep_energy_sums_over_several_steps(E):
+    """tile_x = 8 doubles the update pass's CTA partials of the FP64 energy
+    sums; after three steps the forcing amplitude (from E_B) still gives the
+    exact injected power and the fields follow the oracle."""
+    ms = members(E)
+    ens = E.Ensemble(ms)
+    t = ens.tuning()
+    for g in t["groups"]:
+        g["tile_x"] = 8
+    ens.set_tuning(t)
+    ens.step(3)
+    for i, (m, d) in enumerate(zip(ms, ens.diagnostics())):
+        assert d["P"] == pytest.approx(np.exp(m.lam) * m.eps_bar, rel=1e-5)
+        om = oracle_member(m)
+        uh = O.initial_field(om)
+        O.step(om, uh, 3)
+        assert rel(ens.field(i), uh) < 1e-4
+    ens.close()
+
+
 def test_autotune_preserves_state_and_caches(E, tmp_path):
     ms = members(E)
     ens = E.Ensemble(ms)
