@@ -44,8 +44,9 @@ struct Dims {
 // 4-bit mask of that block (table packed into two 64-bit words), chosen by an
 // offline search over every access pattern of the line transforms (the pass
 // exchanges, the output stores, the Hermitian unpacking reads) so that each
-// half-warp request of 8-byte words meets 16 distinct bank pairs; the small
-// sizes keep an additive padding.
+// half-warp request of 8-byte words meets 16 distinct bank pairs
+// (paper_2506_23712_gb300/swizzle_search.py reproduces the tables); the
+// small sizes keep an additive padding.
 template <int N>
 struct RowSwz {
     static constexpr bool on = false;
