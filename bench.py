@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-uneven", action="store_true")
     p.add_argument("--no-surrogate", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep the default pass variants")
+    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-resolution / 512^3 measurements")
     return p.parse_args()
 
 
@@ -323,6 +324,43 @@ def measure_uneven(E, torch, steps=3, tune=True):
     return out
 
 
+def measure_mixed(E, torch, steps=3, tune=True):
+    """Mixed-resolution ensemble (the 64 x 256^3 members, those at lambda >=
+    3.2 on 512^3 grids) and the single 512^3 reference-run shape, each timed
+    over a few graph replays after one untimed step."""
+    import ens_inputs as I
+
+    def mk(ds):
+        return [E.Member(N=d["N"], nu=d["nu"], lam=d["lam"], eps_bar=d["eps_bar"], k_lo=d["k_lo"],
+                         k_hi=d["k_hi"], dt=d["dt"], cfl=d["cfl"], dt_max=d["dt_max"], rk_order=d["rk_order"],
+                         seed=d["seed"], init_energy=d["init_energy"]) for d in ds]
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, ds in (("mixed_resolution", I.mixed_resolution()), ("reference_512", I.reference_512())):
+        ms = mk(ds)
+        ens = E.Ensemble(ms, hist=E.hist_spec(nu_norm=ms[0].nu), stream=stream)
+        rec = {"members": len(ms), "grids": {str(n): sum(1 for m in ms if m.N == n) for n in sorted({m.N for m in ms})}}
+        if tune:
+            rec["tuning"] = ens.autotune(steps=2)
+        ens.step(1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.step(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        pts = sum(m.N ** 3 for m in ms)
+        rec.update(steps=steps, ms_per_step=1e3 * sec / steps, member_steps_per_s=len(ms) * steps / sec,
+                   grid_point_updates_per_s=pts * steps / sec,
+                   flagged_members=sum(1 for d in ens.diagnostics(raise_on_flag=False) if d["flags"]))
+        ens.close()
+        out[name] = rec
+    out["reference_512"]["note"] = ("throughput of the reference-run shape only: a statistically "
+                                    "stationary 512^3 reference needs ~10^5 steps")
+    return out
+
+
 def traffic_for(kernel):
     """ncu DRAM bytes per launch of the kernel (profiles/traffic.json), or None
     if the kernel source changed since the capture."""
@@ -464,6 +502,9 @@ def main():
     uneven = None
     if not args.no_uneven and rank == 0:
         uneven = measure_uneven(E, torch, tune=not args.no_tune)
+    mixed = None
+    if not args.no_mixed and rank == 0:
+        mixed = measure_mixed(E, torch, tune=not args.no_tune)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -478,7 +519,7 @@ def main():
                            "tuning": tuning,
                            "flagged_members": flagged},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kps * args.steps,
-                "clocks": clk, "plain": plain, "passes": passes, "uneven_batch": uneven,
+                "clocks": clk, "plain": plain, "passes": passes, "uneven_batch": uneven, "mixed_resolution": mixed,
                 "surrogate": surrogate}
         print(json.dumps(line), flush=True)
     if world > 1:

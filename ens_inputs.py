@@ -116,6 +116,24 @@ def ensemble_256(n=64, N=256):
                  rk_order=3, seed=1000 + i, init_energy=0.5) for i, l in enumerate(lams)]
 
 
+def mixed_resolution(n=64, lam_min=3.2, N_hi=512):
+    """ensemble_256 with every member at lambda >= lam_min replaced by the
+    same member on an N_hi grid (twice the small-scale resolution), as the
+    paper does for its extreme-gradient predictions (Sec. VI)."""
+    out = ensemble_256(n)
+    for d in out:
+        if d["lam"] >= lam_min:
+            d["N"] = N_hi
+    return out
+
+
+def reference_512():
+    """One 512^3 member at nu = 0.0015 forced at 1 <= |k| <= 2 with injection
+    rate 0.1 (lambda = 0): the single-reference-run shape."""
+    return [dict(N=512, nu=0.0015, lam=0.0, eps_bar=0.1, k_lo=1.0, k_hi=2.0, dt=-1.0, cfl=0.2, dt_max=0.0,
+                 rk_order=3, seed=77, init_energy=0.5)]
+
+
 def uneven_batch(counts=((128, 24), (256, 12), (384, 4))):
     out = []
     seed = 0

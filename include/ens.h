@@ -348,6 +348,24 @@ ens_status ens_ratio_exponents(const ens_zeta_spec *zeta, double *out);
  * Host arithmetic; R0 may be NULL. */
 ens_status ens_scale_gap(int n, const double *lambdas, const double *rlambda, double R_ref, double *Z, double *R0);
 
+/* ---- checkpoint / resume ------------------------------------------------ */
+
+/* Write the whole ensemble to a file: member descriptions, the spectral
+ * state (FP32 compact layout), every member's run state (time, step count,
+ * dt, energy sums, forcing amplitude, CFL maxima, flags), the accumulated
+ * histogram counts and moment sums, and an FNV-1a checksum of all of it.
+ * Written to path.tmp and renamed, so an interrupted save leaves no partial
+ * file under path.  The format is this library's (host byte order; not an
+ * interchange format).  Synchronises. */
+ens_status ens_save(ens_ctx *ctx, const char *path);
+/* Resume from ens_save's file into a context created with the same members
+ * (every ens_member_desc field equal), histogram specification and RK
+ * order: continuing from the loaded state gives the same fields, bit for
+ * bit, as continuing the saved context (under the same tuning).  ENS_EINVAL
+ * (not sticky; context unchanged) for a missing, foreign, truncated or
+ * corrupted file, with the reason in ens_last_error.  Synchronises. */
+ens_status ens_load(ens_ctx *ctx, const char *path);
+
 /* ---- state access ------------------------------------------------------ */
 
 /* Member spectral field <-> host full layout (FP64; converted from/to the

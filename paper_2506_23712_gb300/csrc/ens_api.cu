@@ -986,6 +986,20 @@ ens_status tuning_valid(const ens_ctx *ctx, const ens_tuning *t, std::string &wh
     return ENS_OK;
 }
 
+// MemberDev::nblk of every member (one int per struct, strided) from its
+// group's current update-pass tile; synchronises
+ens_status sync_nblk(ens_ctx *ctx)
+{
+    for (auto &gr : ctx->groups) {
+        const Geo &g = gr.geo;
+        std::vector<int> v(g.members, g.NK * g.NZp / g.tile_x);
+        ENS_CUDA(ctx, cudaMemcpy2DAsync(&ctx->md[g.first].nblk, sizeof(MemberDev), v.data(), sizeof(int),
+                                        sizeof(int), g.members, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ENS_OK;
+}
+
 // Install a (validated) tuning: pass variants per group, the update pass's
 // partial-sum count per member, and a fresh graph at the next ens_step.
 ens_status apply_tuning(ens_ctx *ctx, const ens_tuning *t)
@@ -998,12 +1012,9 @@ ens_status apply_tuning(ens_ctx *ctx, const ens_tuning *t)
         g.tile_y = o.tile_y;
         g.z_mode = o.z_variant;
         g.z_ctas = o.z_ctas_per_sm * ctx->sms;
-        const int nblk = g.NK * g.NZp / g.tile_x;
-        std::vector<int> v(g.members, nblk);
-        // MemberDev::nblk of the group's members: one int per struct, strided
-        ENS_CUDA(ctx, cudaMemcpy2DAsync(&ctx->md[g.first].nblk, sizeof(MemberDev), v.data(), sizeof(int),
-                                        sizeof(int), g.members, cudaMemcpyHostToDevice, ctx->stream));
     }
+    const ens_status ns = sync_nblk(ctx);
+    if (ns != ENS_OK) return ns;
     // slots a narrower tile wrote before must not leak into the reduction
     ENS_CUDA(ctx, cudaMemsetAsync(ctx->partial, 0,
                                   sizeof(double) * ctx->desc.size() * ctx->partial_blocks * 4, ctx->stream));
@@ -1082,13 +1093,15 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
     };
     // one trial: install, restore the snapshot, one untimed step, then the
     // mean of `steps` graph launches between two events
+    // (the snapshot holds the per-member partial-sum counts of the starting
+    // tuning, so the state is restored first and the tuning installed after)
     auto trial = [&](const ens_tuning &t) -> double {
+        cudaError_t e = copy_state(false);
+        if (e != cudaSuccess) return fail_cuda("autotune restore", e);
         if (apply_tuning(ctx, &t) != ENS_OK) {
             rs = ctx->sticky != ENS_OK ? ctx->sticky : ENS_ECUDA;
             return -1.0;
         }
-        cudaError_t e = copy_state(false);
-        if (e != cudaSuccess) return fail_cuda("autotune restore", e);
         if (ens_step(ctx, 1) != ENS_OK) {
             rs = ctx->sticky;
             return -1.0;
@@ -1165,10 +1178,10 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
     // the state back as it was
     const ens_tuning &fin = rs == ENS_OK ? best : start;
     if (ctx->sticky == ENS_OK) {
-        apply_tuning(ctx, &fin);
         e = copy_state(false);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess && rs == ENS_OK) rs = cuda_fail(ctx, "autotune restore", e);
+        if (e == cudaSuccess) apply_tuning(ctx, &fin);
     }
     cudaFreeAsync(snap, st);
     cudaStreamSynchronize(st);
@@ -1180,6 +1193,158 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
         out->trials = trials;
     }
     return rs;
+}
+
+}  // extern "C"
+
+// ---- checkpoint / resume ------------------------------------------------------
+
+namespace {
+
+constexpr char kCkptMagic[8] = {'E', 'N', 'S', 'C', 'K', 'P', 'T', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, members, rk, counts_len;
+    uint64_t state_bytes, md_bytes, payload_hash;
+    ens_hist_spec hist;
+};
+
+// FNV-1a over the payload, to refuse a truncated or altered file
+uint64_t fnv1a(uint64_t h, const void *data, size_t n)
+{
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+bool same_desc(const ens_member_desc &a, const ens_member_desc &b)
+{
+    return a.N == b.N && a.rk_order == b.rk_order && a.nu == b.nu && a.lambda == b.lambda &&
+           a.eps_bar == b.eps_bar && a.k_lo == b.k_lo && a.k_hi == b.k_hi && a.dt == b.dt && a.cfl == b.cfl &&
+           a.dt_max == b.dt_max && a.seed == b.seed && a.init_energy == b.init_energy;
+}
+
+bool same_hist(const ens_hist_spec &a, const ens_hist_spec &b)
+{
+    return a.qr_bins == b.qr_bins && a.q_lim == b.q_lim && a.r_lim == b.r_lim && a.tail_bins == b.tail_bins &&
+           a.tail_lo == b.tail_lo && a.tail_hi == b.tail_hi && a.eps_norm == b.eps_norm && a.nu_norm == b.nu_norm &&
+           a.grad_bins == b.grad_bins && (a.grad_bins == 0 || a.grad_lim == b.grad_lim);
+}
+
+}  // namespace
+
+extern "C" {
+
+ens_status ens_save(ens_ctx *ctx, const char *path)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (!path) return fail(ctx, ENS_EINVAL, "null path");
+    const int n = (int)ctx->desc.size();
+    const size_t L = (size_t)counts_len_of(ctx->hist.qr_bins, ctx->hist.tail_bins, ctx->hist.grad_bins);
+    const size_t sb = ens_state_bytes(ctx), mb = sizeof(MemberDev) * n;
+    std::vector<char> state(sb), md(mb);
+    std::vector<unsigned long long> counts(n * L);
+    std::vector<double> mom((size_t)n * kNMom);
+    s = ens_get_state(ctx, state.data(), sb);
+    if (s != ENS_OK) return s;
+    ENS_CUDA(ctx, cudaMemcpyAsync(md.data(), ctx->md, mb, cudaMemcpyDeviceToHost, ctx->stream));
+    ENS_CUDA(ctx, cudaMemcpyAsync(counts.data(), ctx->counts, sizeof(unsigned long long) * counts.size(),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    ENS_CUDA(ctx, cudaMemcpyAsync(mom.data(), ctx->moments, sizeof(double) * mom.size(), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.members = (uint32_t)n;
+    h.rk = (uint32_t)ctx->rk;
+    h.counts_len = (uint32_t)L;
+    h.state_bytes = sb;
+    h.md_bytes = mb;
+    h.hist = ctx->hist;
+    uint64_t hash = 0xcbf29ce484222325ull;
+    hash = fnv1a(hash, ctx->desc.data(), sizeof(ens_member_desc) * n);
+    hash = fnv1a(hash, state.data(), sb);
+    hash = fnv1a(hash, md.data(), mb);
+    hash = fnv1a(hash, counts.data(), sizeof(unsigned long long) * counts.size());
+    hash = fnv1a(hash, mom.data(), sizeof(double) * mom.size());
+    h.payload_hash = hash;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail(ctx, ENS_EINVAL, std::string("cannot open ") + tmp + " for writing");
+    bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 &&
+              std::fwrite(ctx->desc.data(), sizeof(ens_member_desc), n, f) == (size_t)n &&
+              std::fwrite(state.data(), 1, sb, f) == sb && std::fwrite(md.data(), 1, mb, f) == mb &&
+              std::fwrite(counts.data(), sizeof(unsigned long long), counts.size(), f) == counts.size() &&
+              std::fwrite(mom.data(), sizeof(double), mom.size(), f) == mom.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return fail(ctx, ENS_EINVAL, std::string("writing the checkpoint ") + path + " failed");
+    }
+    return ENS_OK;
+}
+
+ens_status ens_load(ens_ctx *ctx, const char *path)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (!path) return fail(ctx, ENS_EINVAL, "null path");
+    auto refuse = [&](const std::string &why) {
+        ctx->err = std::string("ens_load: ") + path + ": " + why;   // not sticky: the state is untouched
+        return ENS_EINVAL;
+    };
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return refuse("cannot open");
+    const int n = (int)ctx->desc.size();
+    const size_t L = (size_t)counts_len_of(ctx->hist.qr_bins, ctx->hist.tail_bins, ctx->hist.grad_bins);
+    const size_t sb = ens_state_bytes(ctx), mb = sizeof(MemberDev) * n;
+    CkptHeader h{};
+    std::vector<ens_member_desc> desc(n);
+    std::vector<char> state(sb), md(mb);
+    std::vector<unsigned long long> counts(n * L);
+    std::vector<double> mom((size_t)n * kNMom);
+    bool ok = std::fread(&h, sizeof h, 1, f) == 1 && std::memcmp(h.magic, kCkptMagic, 8) == 0 && h.version == 1;
+    if (ok) ok = h.members == (uint32_t)n && h.rk == (uint32_t)ctx->rk && h.counts_len == (uint32_t)L &&
+                 h.state_bytes == sb && h.md_bytes == mb && same_hist(h.hist, ctx->hist);
+    if (!ok) {
+        std::fclose(f);
+        return refuse("not a checkpoint of an ensemble with these members and histograms");
+    }
+    ok = std::fread(desc.data(), sizeof(ens_member_desc), n, f) == (size_t)n &&
+         std::fread(state.data(), 1, sb, f) == sb && std::fread(md.data(), 1, mb, f) == mb &&
+         std::fread(counts.data(), sizeof(unsigned long long), counts.size(), f) == counts.size() &&
+         std::fread(mom.data(), sizeof(double), mom.size(), f) == mom.size();
+    std::fclose(f);
+    if (!ok) return refuse("truncated");
+    for (int i = 0; i < n; ++i)
+        if (!same_desc(desc[i], ctx->desc[i])) return refuse("member " + std::to_string(i) + " differs");
+    uint64_t hash = 0xcbf29ce484222325ull;
+    hash = fnv1a(hash, desc.data(), sizeof(ens_member_desc) * n);
+    hash = fnv1a(hash, state.data(), sb);
+    hash = fnv1a(hash, md.data(), mb);
+    hash = fnv1a(hash, counts.data(), sizeof(unsigned long long) * counts.size());
+    hash = fnv1a(hash, mom.data(), sizeof(double) * mom.size());
+    if (hash != h.payload_hash) return refuse("checksum mismatch");
+    // the member run state, spectral state and statistics as saved; the
+    // partial-sum counts follow this context's tuning
+    const char *p = state.data();
+    for (auto &gr : ctx->groups) {
+        const size_t b = sizeof(float2) * 3 * gr.geo.sU * gr.geo.members;
+        ENS_CUDA(ctx, cudaMemcpyAsync(gr.geo.U, p, b, cudaMemcpyHostToDevice, ctx->stream));
+        p += b;
+    }
+    ENS_CUDA(ctx, cudaMemcpyAsync(ctx->md, md.data(), mb, cudaMemcpyHostToDevice, ctx->stream));
+    ENS_CUDA(ctx, cudaMemcpyAsync(ctx->counts, counts.data(), sizeof(unsigned long long) * counts.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    ENS_CUDA(ctx, cudaMemcpyAsync(ctx->moments, mom.data(), sizeof(double) * mom.size(), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    return sync_nblk(ctx);
 }
 
 }  // extern "C"

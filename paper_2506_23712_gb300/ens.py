@@ -114,6 +114,8 @@ SIGNATURES = [
     ("ens_nelkin_exponents", _i, [_P(ZetaSpec), _i, _vp, _vp]),
     ("ens_ratio_exponents", _i, [_P(ZetaSpec), _vp]),
     ("ens_scale_gap", _i, [_i, _vp, _vp, _d, _P(_d), _P(_d)]),
+    ("ens_save", _i, [_vp, ctypes.c_char_p]),
+    ("ens_load", _i, [_vp, ctypes.c_char_p]),
     ("ens_get_field", _i, [_vp, _i, _vp]),
     ("ens_set_field", _i, [_vp, _i, _vp]),
     ("ens_state_bytes", _sz, [_vp]),
@@ -391,6 +393,14 @@ def ens_scale_gap(lambdas, rlambda, R_ref):
     return Z.value, R0.value
 
 
+def ens_save(ctx, path: str):
+    _check(lib().ens_save(ctx, path.encode()), ctx)
+
+
+def ens_load(ctx, path: str):
+    _check(lib().ens_load(ctx, path.encode()), ctx)
+
+
 def _full_shape(N):
     return (3, N, N, N // 2 + 1)
 
@@ -515,6 +525,12 @@ class Ensemble:
 
     def step(self, nsteps=1, graph=True):
         (ens_step if graph else ens_step_nograph)(self.ctx, nsteps)
+
+    def save(self, path: str):
+        ens_save(self.ctx, path)
+
+    def load(self, path: str):
+        ens_load(self.ctx, path)
 
     def tuning(self) -> dict:
         return ens_get_tuning(self.ctx)
