@@ -245,7 +245,7 @@ def hellinger(p, q):
     return float(np.sqrt(max(0.0, 1.0 - np.sum(np.sqrt(p * q)))))
 
 
-def measure_surrogate(E, ens, descs, torch, steps=200):
+def measure_surrogate(E, ens, descs, torch, steps=400):
     """Learned lambda interpolant on this ensemble's own histograms: training
     throughput, the tcgen05 hidden-layer GEMM against the BF16 peak, and the
     512-point quadrature mixture against the member quadrature (Hellinger)."""
@@ -257,7 +257,7 @@ def measure_surrogate(E, ens, descs, torch, steps=200):
     S = E.Surrogate(seed=0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    loss = S.train(lams, counts, h, steps, lr=2e-3)
+    loss = S.train(lams, counts, h, steps, lr=4e-3)
     t_train = time.perf_counter() - t0
     rows_q = 512 * per
     gemm_ms = S.time_gemm(rows_q, iters=5)
