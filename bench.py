@@ -261,7 +261,11 @@ def measure_surrogate(E, ens, descs, torch, steps=400):
     t_train = time.perf_counter() - t0
     rows_q = 512 * per
     gemm_ms = S.time_gemm(rows_q, iters=5)
-    tflops = 2.0 * pad128(rows_q) * 256 * 256 / (gemm_ms / 1e3) / 1e12
+    gemm_tflops = 2.0 * pad128(rows_q) * 256 * 256 / (gemm_ms / 1e3) / 1e12
+    # fused inference (features -> 3 tcgen05 layers -> head) over the 512-point quadrature
+    infer_ms = S.time_infer(h, 512, iters=5)
+    infer_flops = 2.0 * rows_q * (64 * 256 + 2 * 256 * 256 + 256)
+    tflops = infer_flops / (infer_ms / 1e3) / 1e12
     Z = 1.5 * math.log(261.0 / 63.0)
     s = np.sort(np.unique(lams))
     lo, hi = s[0] - 0.5 * (s[1] - s[0]), s[-1] + 0.5 * (s[-1] - s[-2])
@@ -275,9 +279,12 @@ def measure_surrogate(E, ens, descs, torch, steps=400):
             "train_rows_per_step": len(lams) * per, "final_loss": loss,
             "quadrature_points": 512, "mixture_s": t_inf,
             "hellinger_vs_member_quadrature": {k: hellinger(sur[k], ref[k]) for k in ("pdf_qr", "pdf_eps", "pdf_ens")},
-            "Z": Z, "roofline": {"bound": "tensor", "kernel": "k_gemm_tc<256>", "achieved": tflops, "peak": peak[0],
+            "Z": Z, "roofline": {"bound": "tensor", "kernel": "k_mlp_infer", "achieved": tflops, "peak": peak[0],
                                   "unit": "TFLOP/s", "frac": tflops / peak[0], "peak_source": peak[1],
-                                  "shape": "%d x 256 x 256 BF16 -> FP32" % pad128(rows_q), "ms": gemm_ms}}
+                                  "rows": rows_q, "flops_per_launch": infer_flops, "ms": infer_ms},
+            "layer_gemm": {"kernel": "k_gemm_tc<256>", "shape": "%d x 256 x 256 BF16 -> FP32" % pad128(rows_q),
+                           "ms": gemm_ms, "TFLOPs": gemm_tflops,
+                           "note": "training-path layer GEMM; FP32 output makes it HBM-bound (86 flop/B)"}}
 
 
 def pad128(r):

@@ -191,6 +191,10 @@ ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
 
 /* Per grid-size group: the variants of the stage passes.
  *   tile_x, tile_y  columns per CTA of the x / y FFT passes (8 or 16);
+ *   plan_x          FFT plan of the x passes: 0 the default radix plan,
+ *                   1 (N = 128, 256, 512 only) a plan with twice the
+ *                   threads per line and a tighter register budget
+ *                   (128: 8x2x8, 256: 8x4x8, 512: 8x8x8 on 64 threads);
  *   z_variant       0: persistent TMA-pipelined z pass with z_ctas_per_sm
  *                   CTAs per SM (1 .. the kernel's occupancy limit),
  *                   1: one CTA per group of rows (z_ctas_per_sm unused
@@ -205,6 +209,7 @@ typedef struct {
     int tile_x, tile_y;
     int z_variant;
     int z_ctas_per_sm;
+    int plan_x;
 } ens_group_tuning;
 typedef struct {
     int groups;          /* number of grid-size groups (read-only) */
@@ -222,8 +227,8 @@ ens_status ens_get_tuning(const ens_ctx *ctx, ens_tuning *out);
  * the next ens_step captures a new graph. */
 ens_status ens_set_tuning(ens_ctx *ctx, const ens_tuning *t);
 /* Time the variants on this context's own members and install the fastest:
- * coordinate descent over tile_x, tile_y, the z variant and its CTAs per SM
- * for each group, then parallel_groups; each trial restores the member
+ * coordinate descent over plan_x, tile_x, tile_y, the z variant and its CTAs
+ * per SM for each group, then parallel_groups; each trial restores the member
  * state from a device snapshot, runs one untimed step and times `steps`
  * graph replays with CUDA events; a candidate wins only if it is more than
  * 1% faster.  The member state is restored afterwards (the simulation does
@@ -429,7 +434,11 @@ ens_status ens_surrogate_loss_grad(ens_surrogate *s, int n, const double *lambda
 ens_status ens_surrogate_train(ens_surrogate *s, int n, const double *lambdas, const uint64_t *counts,
                                const ens_hist_spec *hist, int steps, double lr, double *final_loss);
 /* Densities (bin probabilities) at n lambda values: probs [n][qr_bins^2 +
- * 2 tail_bins], each kind summing to one. */
+ * 2 tail_bins], each kind summing to one.  Inference (here and in
+ * ens_surrogate_mixture) runs the fused kernel: per 128-row tile the
+ * features, the three tcgen05 layers with bias + SiLU epilogues from TMEM and
+ * the head, activations kept in shared memory, weights streamed in by bulk
+ * copies. */
 ens_status ens_surrogate_density(ens_surrogate *s, int n, const double *lambdas, const ens_hist_spec *hist,
                                  double *probs);
 /* Mixture over a midpoint lambda quadrature of nquad points on
@@ -441,6 +450,15 @@ ens_status ens_surrogate_mixture(ens_surrogate *s, const ens_hist_spec *hist, co
 /* Average device time (ms, CUDA events on the object's stream) of one
  * hidden-layer GEMM of `rows` rows (rows x 256 x 256, BF16 in, FP32 out). */
 ens_status ens_surrogate_time_gemm(ens_surrogate *s, long long rows, int iters, double *ms);
+/* Logits [n][qr_bins^2 + 2 tail_bins] at n lambda values from the fused
+ * inference kernel (fused != 0) or the layer-by-layer forward pass that
+ * training uses (fused == 0); both round activations to BF16 the same way. */
+ens_status ens_surrogate_logits(ens_surrogate *s, int n, const double *lambdas, const ens_hist_spec *hist, int fused,
+                                float *logits);
+/* Average device time (ms) of one fused inference launch over nquad lambda
+ * values of this histogram layout (nquad (qr_bins^2 + 2 tail_bins) rows;
+ * 2 (64 + 2 x 256 + 1) 256 flops per row). */
+ens_status ens_surrogate_time_infer(ens_surrogate *s, const ens_hist_spec *hist, int nquad, int iters, double *ms);
 /* Tensor-core GEMM check C = A B^T on host BF16 bit patterns: A [M][K],
  * B [N][K], C [M][N] FP32; M % 128 == 0, N % 64 == 0, K % (64 ksplit) == 0,
  * ksplit <= 32 splits K across CTAs (partials summed in a fixed order). */

@@ -18,6 +18,7 @@
 #include "ens_internal.h"
 #include "ens_tc.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -206,7 +207,7 @@ __global__ void k_features(RowSpec rs, const double *lams, int nlam, long long r
     }
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 __device__ __forceinline__ float dsilu(float z)
 {
     const float s = 1.f / (1.f + __expf(-z));
@@ -408,7 +409,31 @@ __global__ void k_adam(float *p, const float *g, float *m1, float *m2, long long
     p[i] -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
 }
 
-// BF16 operand copies: W1 [256][64], W2/W3 [256][256] and their transposes
+// byte offset of W[o][k] in the shared-memory image of a [256 out][K in]
+// weight: K-blocks of 64 (32 KB each: 256 rows x 128 bytes, 128-byte swizzle)
+__device__ __forceinline__ uint32_t wimg_offset(int o, int k)
+{
+    return (uint32_t)((k >> 6) * 32768) + sw128_offset(o, k & 63);
+}
+
+// BF16 operand copies: W1 [256][64], W2/W3 [256][256] and their transposes,
+// and (optional) the swizzled shared-memory images of W1, W2, W3 that the
+// fused inference kernel copies in with bulk copies
+__global__ void k_pack_weights_img(const float *p, unsigned char *img1, unsigned char *img2, unsigned char *img3)
+{
+    const ParamLayout L = param_layout();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (long long)kHid * kIn) {
+        const int o = (int)(i / kIn), k = (int)(i % kIn);
+        *reinterpret_cast<__nv_bfloat16 *>(img1 + wimg_offset(o, k)) = __float2bfloat16(p[L.W1 + i]);
+    }
+    if (i < (long long)kHid * kHid) {
+        const int o = (int)(i / kHid), k = (int)(i % kHid);
+        *reinterpret_cast<__nv_bfloat16 *>(img2 + wimg_offset(o, k)) = __float2bfloat16(p[L.W2 + i]);
+        *reinterpret_cast<__nv_bfloat16 *>(img3 + wimg_offset(o, k)) = __float2bfloat16(p[L.W3 + i]);
+    }
+}
+
 __global__ void k_pack_weights(const float *p, __nv_bfloat16 *W1b, __nv_bfloat16 *W2b, __nv_bfloat16 *W3b,
                                __nv_bfloat16 *W2t, __nv_bfloat16 *W3t)
 {
@@ -480,6 +505,191 @@ __global__ void k_init_params(float *p, long long n, unsigned long long seed)
     p[i] = u * scale;
 }
 
+// ---------------------------------------------------------------------------
+// Fused inference: features -> 3 x (tcgen05 GEMM + bias + SiLU) -> head, per
+// 128-row tile, activations never leave the SM.  Persistent CTAs (one per
+// SM, 256 threads); per CTA one 256-column FP32 accumulator in TMEM.
+//   shared memory: H  4 K-blocks of 128 rows x 64 BF16 (64 KB; K-block 0
+//                     also holds the features of the tile)
+//                  W1 image (32 KB, loaded once), W2 or W3 image (128 KB,
+//                     refilled by bulk copies while the epilogues run)
+//   per tile: features -> MMA(H0, W1) -> epilogue -> MMA(H, W2) -> [copy W3]
+//             epilogue -> MMA(H, W3) -> [copy W2] -> epilogue + head
+// The epilogue warp w reads TMEM lanes 32 (w mod 4) .. +31 (its rows) and
+// columns 128 (w / 4) .. +127.  Every mbarrier wait is bounded; a wait that
+// gives up sets *err, waits (bounded) for the copies and MMAs in flight,
+// frees the TMEM and returns.
+// ---------------------------------------------------------------------------
+constexpr int kInferThreads = 256;
+constexpr size_t kInferSmem = 1024 + 65536 + 32768 + 131072 + 64;
+
+__global__ void __launch_bounds__(kInferThreads, 1)
+k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long long ntiles,
+            const unsigned char *__restrict__ img1, const unsigned char *__restrict__ img2,
+            const unsigned char *__restrict__ img3, const float *__restrict__ p, float *__restrict__ logit,
+            int *err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *sH = sm;                      // 64 KB
+    unsigned char *sW1 = sm + 65536;             // 32 KB
+    unsigned char *sW = sW1 + 32768;             // 128 KB
+    uint64_t *bar_mma = reinterpret_cast<uint64_t *>(sW + 131072);
+    uint64_t *bar_w = bar_mma + 1;
+    uint32_t *holder = reinterpret_cast<uint32_t *>(bar_w + 1);
+    float *part = reinterpret_cast<float *>(sH);   // head partials [2][128], once layer 3 is done
+    const ParamLayout L = param_layout();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    if (warp == 0) tmem_alloc(holder, 256);
+    if (tid == 0) {
+        mbar_init(bar_mma, 1);
+        mbar_init(bar_w, 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *holder;
+    constexpr uint32_t idesc = idesc_bf16(128, kHid);
+    uint32_t n_mma = 0, n_w = 0;   // completed phases expected on each barrier
+    bool ok = true;
+    auto copy_w = [&](const unsigned char *img, unsigned char *dst, uint32_t bytes) {   // thread 0
+        mbar_arrive_expect_tx(bar_w, bytes);
+        for (uint32_t o = 0; o < bytes; o += 32768) bulk_g2s(dst + o, img + o, 32768, bar_w);
+    };
+    auto wait = [&](uint64_t *bar, uint32_t &n) {   // the phase stays pending on failure
+        const bool r = mbar_wait_warp(bar, n & 1);
+        if (r) ++n;
+        return r;
+    };
+    // prologue: W1 and W2 images
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar_w, 32768 + 131072);
+        bulk_g2s(sW1, img1, 32768, bar_w);
+        for (uint32_t o = 0; o < 131072; o += 32768) bulk_g2s(sW + o, img2 + o, 32768, bar_w);
+    }
+    ok = wait(bar_w, n_w);
+    // issue one layer: D = A[kblocks] * W^T (thread 0), commit to bar_mma
+    auto mma_layer = [&](const unsigned char *W, int kblocks) {
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int kb = 0; kb < kblocks; ++kb) {
+                const uint64_t da = desc_sw128(sH + kb * 16384), db = desc_sw128(W + kb * 32768);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) tc_mma_bf16(taddr, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+            }
+            tc_commit(bar_mma);
+        }
+    };
+    const int row = quarter * 32 + lane;                       // this thread's TMEM lane = tile row
+    const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16);
+    // bias + SiLU of this thread's 128 columns into H (BF16, swizzled K-blocks)
+    auto epilogue = [&](const float *bias) {
+#pragma unroll 1
+        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+            float v[32];
+            tc_ld_32cols(tl + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                uint32_t w[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float a = silu(v[j + 2 * t] + __ldg(bias + c0 + j + 2 * t));
+                    const float b = silu(v[j + 2 * t + 1] + __ldg(bias + c0 + j + 2 * t + 1));
+                    const __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
+                    w[t] = *reinterpret_cast<const uint32_t *>(&hb);
+                }
+                const int col = c0 + j;
+                *reinterpret_cast<uint4 *>(sH + (col >> 6) * 16384 + sw128_offset(row, col & 63)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    };
+    auto publish = [&]() {   // generic smem writes -> tensor-core reads; TMEM reads done
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+    };
+#pragma unroll 1
+    for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const long long r0 = tile * 128;
+        // features of the tile into K-block 0 of H
+        if (tid < 128) {
+            float f[kIn];
+            const long long rr = r0 + tid;
+            if (rr < real) row_features(rs, lams[rr / rs.per_member], (int)(rr % rs.per_member), f);
+            else
+                for (int i = 0; i < kIn; ++i) f[i] = 0.f;
+#pragma unroll
+            for (int j = 0; j < kIn; j += 8) {
+                uint32_t w[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const __nv_bfloat162 hb = __floats2bfloat162_rn(f[j + 2 * t], f[j + 2 * t + 1]);
+                    w[t] = *reinterpret_cast<const uint32_t *>(&hb);
+                }
+                *reinterpret_cast<uint4 *>(sH + sw128_offset(tid, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        publish();
+        // layer 1 (K = 64): the W2 image of this tile may still be arriving
+        mma_layer(sW1, 1);
+        ok = wait(bar_mma, n_mma);
+        if (tile != blockIdx.x) ok = ok && wait(bar_w, n_w);   // W2 refilled during the last epilogue
+        tc_fence_after();
+        if (!__syncthreads_and(ok)) break;
+        epilogue(p + L.b1);
+        publish();
+        // layer 2, then W3 streams in while the epilogue runs
+        mma_layer(sW, 4);
+        ok = wait(bar_mma, n_mma);
+        tc_fence_after();
+        if (!__syncthreads_and(ok)) break;
+        if (tid == 0) copy_w(img3, sW, 131072);
+        epilogue(p + L.b2);
+        publish();
+        ok = wait(bar_w, n_w);
+        if (!__syncthreads_and(ok)) break;
+        mma_layer(sW, 4);
+        ok = wait(bar_mma, n_mma);
+        tc_fence_after();
+        if (!__syncthreads_and(ok)) break;
+        if (tid == 0) copy_w(img2, sW, 131072);   // for the next tile
+        // head: logit = sum_c BF16(SiLU(z3 + b3)) w4 + b4
+        float acc = 0.f;
+#pragma unroll 1
+        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+            float v[32];
+            tc_ld_32cols(tl + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float h = __bfloat162float(__float2bfloat16(silu(v[j] + __ldg(p + L.b3 + c0 + j))));
+                acc = fmaf(h, __ldg(p + L.w4 + c0 + j), acc);
+            }
+        }
+        part[half * 128 + row] = acc;
+        tc_fence_before();
+        __syncthreads();
+        if (tid < 128 && r0 + tid < real) logit[r0 + tid] = part[tid] + part[128 + tid] + __ldg(p + L.b4);
+        __syncthreads();   // part (in H) is rewritten by the next tile's features
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        // copies or MMAs may still be in flight: bounded waits before freeing
+        mbar_wait_warp(bar_w, n_w & 1);
+        mbar_wait_warp(bar_mma, n_mma & 1);
+    } else if (n_w > 0 && ntiles > (long long)blockIdx.x) {
+        // the last tile started a W2 refill nobody consumes: let it land
+        mbar_wait_warp(bar_w, n_w & 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, 256);
+}
+
 }  // namespace ens
 
 using namespace ens;
@@ -502,6 +712,8 @@ struct ens_surrogate {
           *target = nullptr, *dH = nullptr, *part = nullptr;
     double *lam = nullptr, *loss = nullptr, *wq = nullptr, *pdf = nullptr;
     int groups_cap = 0;
+    unsigned char *img = nullptr;   // swizzled W1 | W2 | W3 images for the fused inference kernel
+    int sms = 0;
 };
 
 namespace {
@@ -555,6 +767,19 @@ bool forward(ens_surrogate *S, long long rows, bool keep_t)
     k_bias_silu<<<blocks(rows * kHid, 256), 256, 0, s>>>(S->Z3, S->p + L.b3, rows, S->H3, nullptr);
     k_head<<<blocks(rows * 32, 256), 256, 0, s>>>(S->H3, S->p + L.w4, S->p + L.b4, rows, S->logit);
     return true;
+}
+
+// fused inference of `real` rows (lambda values in S->lam) into S->logit
+bool forward_fused(ens_surrogate *S, const RowSpec &rs, long long real)
+{
+    cudaStream_t s = S->s;
+    const long long n = (long long)kHid * kHid;
+    k_pack_weights_img<<<blocks(n, 256), 256, 0, s>>>(S->p, S->img, S->img + 32768, S->img + 32768 + 131072);
+    const long long ntiles = (real + 127) / 128;
+    const int grid = (int)std::min<long long>(ntiles, S->sms > 0 ? S->sms : 1);
+    k_mlp_infer<<<grid, kInferThreads, kInferSmem, s>>>(rs, S->lam, real, ntiles, S->img, S->img + 32768,
+                                                       S->img + 32768 + 131072, S->p, S->logit, S->err);
+    return cudaGetLastError() == cudaSuccess;
 }
 
 int pick_split(long long rows)
@@ -634,7 +859,13 @@ ens_status ens_surrogate_create(uint64_t seed, void *stream, ens_surrogate **out
          cudaMalloc(&S->W2t, sizeof(__nv_bfloat16) * kHid * kHid) == cudaSuccess &&
          cudaMalloc(&S->W3t, sizeof(__nv_bfloat16) * kHid * kHid) == cudaSuccess &&
          cudaMalloc(&S->err, sizeof(int)) == cudaSuccess && cudaMalloc(&S->wq, sizeof(double) * 4096) == cudaSuccess &&
-         cudaMalloc(&S->pdf, sizeof(double) * 1 << 20) == cudaSuccess;
+         cudaMalloc(&S->pdf, sizeof(double) * 1 << 20) == cudaSuccess &&
+         cudaMalloc(&S->img, 32768 + 2 * 131072) == cudaSuccess &&
+         cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem) ==
+             cudaSuccess;
+    int dev = 0;
+    ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
     if (!ok) {
         delete S;
         return ENS_ENOMEM;
@@ -658,6 +889,7 @@ ens_status ens_surrogate_destroy(ens_surrogate *S)
     cudaStreamSynchronize(S->s);
     for (void *p : {(void *)S->p, (void *)S->g, (void *)S->m1, (void *)S->m2, (void *)S->W1b, (void *)S->W2b,
                     (void *)S->W3b, (void *)S->W2t, (void *)S->W3t, (void *)S->err, (void *)S->wq, (void *)S->pdf,
+                    (void *)S->img,
                     (void *)S->X, (void *)S->Xt, (void *)S->H1, (void *)S->H2, (void *)S->H3, (void *)S->H1t,
                     (void *)S->H2t, (void *)S->dZ, (void *)S->dZt, (void *)S->Z1, (void *)S->Z2, (void *)S->Z3,
                     (void *)S->logit, (void *)S->dlogit, (void *)S->q, (void *)S->target, (void *)S->dH,
@@ -796,7 +1028,7 @@ ens_status ens_surrogate_density(ens_surrogate *S, int n, const double *lambdas,
     RowSpec rs;
     ens_status st = load_batch(S, n, lambdas, nullptr, h, &rows, &real, &rs);
     if (st != ENS_OK) return st;
-    if (!forward(S, rows, false)) return ENS_EINVAL;
+    if (!forward_fused(S, rs, real)) return ENS_ECUDA;
     k_softmax_ce<<<3 * n, 256, 0, S->s>>>(S->logit, nullptr, rs.nq, rs.nt, 1.0, S->q, nullptr, nullptr);
     if (cudaGetLastError() != cudaSuccess) return ENS_ECUDA;
     std::vector<float> q((size_t)real);
@@ -818,8 +1050,7 @@ ens_status ens_surrogate_mixture(ens_surrogate *S, const ens_hist_spec *h, const
     if (rs.per_member > (1 << 20)) return ENS_EINVAL;
     if (!alloc_work(S, rows, 3 * nquad)) return ENS_ENOMEM;
     k_quad_weights<<<1, 256, 0, S->s>>>(lam_lo, lam_hi, nquad, w->kind, w->c, w->Z, w->mu, w->sigma, S->lam, S->wq);
-    k_features<<<blocks(rows, 256), 256, 0, S->s>>>(rs, S->lam, nquad, rows, S->X, nullptr);
-    if (!forward(S, rows, false)) return ENS_EINVAL;
+    if (!forward_fused(S, rs, real)) return ENS_ECUDA;
     k_softmax_ce<<<3 * nquad, 256, 0, S->s>>>(S->logit, nullptr, rs.nq, rs.nt, 1.0, S->q, nullptr, nullptr);
     const double dq = 2.0 * h->q_lim / h->qr_bins, dr = 2.0 * h->r_lim / h->qr_bins;
     const double dt = (h->tail_hi - h->tail_lo) / h->tail_bins;
@@ -861,6 +1092,56 @@ ens_status ens_surrogate_time_gemm(ens_surrogate *S, long long rows, int iters, 
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (e != cudaSuccess) return ENS_ECUDA;
+    *ms = t / iters;
+    return check_err(S);
+}
+
+// logits of the network at n lambda values, by the fused inference kernel
+// (fused != 0) or by the layer-by-layer training forward pass (tests)
+ens_status ens_surrogate_logits(ens_surrogate *S, int n, const double *lambdas, const ens_hist_spec *h, int fused,
+                                float *logits)
+{
+    long long rows, real;
+    RowSpec rs;
+    if (!logits) return ENS_EINVAL;
+    ens_status st = load_batch(S, n, lambdas, nullptr, h, &rows, &real, &rs);
+    if (st != ENS_OK) return st;
+    if (fused ? !forward_fused(S, rs, real) : !forward(S, rows, false)) return ENS_ECUDA;
+    if (cudaMemcpyAsync(logits, S->logit, sizeof(float) * real, cudaMemcpyDeviceToHost, S->s) != cudaSuccess)
+        return ENS_ECUDA;
+    return check_err(S);
+}
+
+// average time of the fused inference kernel over nquad lambda values of a
+// histogram layout, CUDA events on the object's stream (profiling)
+ens_status ens_surrogate_time_infer(ens_surrogate *S, const ens_hist_spec *h, int nquad, int iters, double *ms)
+{
+    if (!S || !h || nquad < 1 || nquad > 4096 || iters < 1 || !ms) return ENS_EINVAL;
+    RowSpec rs{h->qr_bins, h->tail_bins, h->qr_bins * h->qr_bins + 2 * h->tail_bins};
+    const long long real = (long long)nquad * rs.per_member, rows = pad128(real);
+    if (!alloc_work(S, rows, 3 * nquad)) return ENS_ENOMEM;
+    k_quad_weights<<<1, 256, 0, S->s>>>(-5.0, 5.0, nquad, 1, 0.0, 0.0, 0.0, 1.0, S->lam, S->wq);
+    const long long ntiles = (real + 127) / 128;
+    const int grid = (int)std::min<long long>(ntiles, S->sms > 0 ? S->sms : 1);
+    k_pack_weights_img<<<blocks((long long)kHid * kHid, 256), 256, 0, S->s>>>(S->p, S->img, S->img + 32768,
+                                                                              S->img + 32768 + 131072);
+    auto launch = [&]() {
+        k_mlp_infer<<<grid, kInferThreads, kInferSmem, S->s>>>(rs, S->lam, real, ntiles, S->img, S->img + 32768,
+                                                               S->img + 32768 + 131072, S->p, S->logit, S->err);
+    };
+    launch();   // warm-up
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, S->s);
+    for (int i = 0; i < iters; ++i) launch();
+    cudaEventRecord(b, S->s);
+    float t = 0.f;
+    const cudaError_t e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return ENS_ECUDA;
     *ms = t / iters;
     return check_err(S);
 }

@@ -79,7 +79,7 @@ ENS_MAX_GROUPS = 8
 
 class GroupTuning(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-                ("z_variant", ctypes.c_int), ("z_ctas_per_sm", ctypes.c_int)]
+                ("z_variant", ctypes.c_int), ("z_ctas_per_sm", ctypes.c_int), ("plan_x", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):
@@ -141,6 +141,8 @@ SIGNATURES = [
     ("ens_surrogate_density", _i, [_vp, _i, _vp, _P(HistSpec), _vp]),
     ("ens_surrogate_mixture", _i, [_vp, _P(HistSpec), _P(WeightSpec), _d, _d, _i, _P(MixtureOut)]),
     ("ens_surrogate_time_gemm", _i, [_vp, ctypes.c_longlong, _i, _P(_d)]),
+    ("ens_surrogate_logits", _i, [_vp, _i, _vp, _P(HistSpec), _i, _vp]),
+    ("ens_surrogate_time_infer", _i, [_vp, _P(HistSpec), _i, _i, _P(_d)]),
     ("ens_tc_gemm_check", _i, [_vp, _vp, _vp, _i, _i, _i, _i]),
 ]
 
@@ -213,7 +215,7 @@ def ens_step_sequential(ctx, nsteps=1):
     _check(lib().ens_step_sequential(ctx, nsteps), ctx)
 
 
-_GROUP_KEYS = ("N", "tile_x", "tile_y", "z_variant", "z_ctas_per_sm")
+_GROUP_KEYS = ("N", "tile_x", "tile_y", "z_variant", "z_ctas_per_sm", "plan_x")
 
 
 def _tuning_dict(t: Tuning) -> dict:
@@ -677,6 +679,19 @@ class Surrogate:
         out = np.zeros((lam.size, per), dtype=np.float64)
         _check(lib().ens_surrogate_density(self.h, lam.size, _ptr(lam), ctypes.byref(hist), _ptr(out)))
         return out
+
+    def logits(self, lambdas, hist, fused=True):
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        per = hist.qr_bins ** 2 + 2 * hist.tail_bins
+        out = np.zeros((lam.size, per), dtype=np.float32)
+        _check(lib().ens_surrogate_logits(self.h, lam.size, _ptr(lam), ctypes.byref(hist), int(bool(fused)),
+                                          _ptr(out)))
+        return out
+
+    def time_infer(self, hist, nquad=512, iters=5):
+        ms = ctypes.c_double()
+        _check(lib().ens_surrogate_time_infer(self.h, ctypes.byref(hist), nquad, iters, ctypes.byref(ms)))
+        return ms.value
 
     def time_gemm(self, rows, iters=10):
         ms = ctypes.c_double()

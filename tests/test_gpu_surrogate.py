@@ -73,6 +73,30 @@ def test_gradient_matches_oracle(E):
     S.close()
 
 
+def test_fused_inference_matches_layerwise_and_oracle(E):
+    """The fused inference kernel against the layer-by-layer forward pass
+    (same BF16 roundings: logits to 1e-5 of their scale) and the FP64
+    oracle MLP on the BF16-rounded weights (the kernel also rounds features
+    and activations to BF16, ~0.4% each, so densities agree within 5% and
+    Hellinger < 5e-3 per kind), over several 128-row tiles and a ragged
+    last tile."""
+    nq, nt = 16, 40            # 336 rows per lambda: tiles straddle lambda values
+    h = E.hist_spec(qr_bins=nq, tail_bins=nt)
+    lams = np.array([-2.7, -0.4, 0.9, 3.3, 5.1])
+    counts = I.synthetic_member_counts(lams, nq, nt, 200000, seed=9)
+    S = E.Surrogate(seed=11)
+    S.train(lams, counts, h, 30, lr=2e-3)       # away from the initialisation
+    lf = S.logits(lams, h, fused=True)
+    ll = S.logits(lams, h, fused=False)
+    assert np.abs(lf - ll).max() <= 1e-5 * max(1.0, np.abs(ll).max())
+    q = S.density(lams, h)
+    ref = OMLP.densities(bf16_params(S.params()), lams, nq, nt)
+    assert np.all(np.abs(q - ref) <= 0.05 * ref + 1e-6)
+    for i in range(len(lams)):
+        assert max(hellinger_kinds(q[i], ref[i], nq, nt)) < 5e-3
+    S.close()
+
+
 def trained(E, lams, counts, h, steps=1500, seed=3):
     S = E.Surrogate(seed=seed)
     l0, _ = S.loss_grad(lams, counts, h)
