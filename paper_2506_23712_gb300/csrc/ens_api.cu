@@ -156,6 +156,7 @@ size_t carve(const ens_member_desc *m, int n, const ens_hist_spec *h, char *base
         g.NZ = g.kc + 1;
         g.NZp = (g.NZ + kTile - 1) / kTile * kTile;
         g.tile_x = g.tile_y = kTile;
+        g.plan_x = 0;
         g.z_mode = 0;
         g.members = (int)gr.members.size();
         g.first = first;
@@ -948,6 +949,7 @@ void tuning_of(const ens_ctx *ctx, ens_tuning *t)
         o.tile_y = g.tile_y;
         o.z_variant = g.z_mode;
         o.z_ctas_per_sm = ctx->sms > 0 ? g.z_ctas / ctx->sms : 0;
+        o.plan_x = g.plan_x;
     }
 }
 
@@ -971,6 +973,10 @@ ens_status tuning_valid(const ens_ctx *ctx, const ens_tuning *t, std::string &wh
         }
         if ((o.tile_x != 8 && o.tile_x != 16) || (o.tile_y != 8 && o.tile_y != 16)) {
             why = "column tiles must be 8 or 16";
+            return ENS_EINVAL;
+        }
+        if (o.plan_x != 0 && !(o.plan_x == 1 && plan_variant_available(N))) {
+            why = "plan_x must be 0, or 1 for N = 128, 256, 512";
             return ENS_EINVAL;
         }
         if (o.z_variant != 0 && o.z_variant != 1) {
@@ -1010,6 +1016,7 @@ ens_status apply_tuning(ens_ctx *ctx, const ens_tuning *t)
         const ens_group_tuning &o = t->group[gi];
         g.tile_x = o.tile_x;
         g.tile_y = o.tile_y;
+        g.plan_x = o.plan_x;
         g.z_mode = o.z_variant;
         g.z_ctas = o.z_ctas_per_sm * ctx->sms;
     }
@@ -1142,6 +1149,11 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
     // coordinate descent over the knobs, group by group
     for (int gi = 0; rs == ENS_OK && gi < best.groups; ++gi) {
         const int N = best.group[gi].N;
+        if (plan_variant_available(N)) {
+            cand = best;
+            cand.group[gi].plan_x = 1 - best.group[gi].plan_x;
+            if (!consider(cand)) break;
+        }
         for (int tile : {16, 8}) {
             cand = best;
             if (cand.group[gi].tile_x == tile) continue;

@@ -179,9 +179,19 @@ template <> struct Plan<256> { static constexpr int P = 16, NP = 2, R0 = 16, R1 
 template <> struct Plan<384> { static constexpr int P = 16, NP = 3, R0 = 8,  R1 = 6,  R2 = 8; };
 template <> struct Plan<512> { static constexpr int P = 32, NP = 3, R0 = 8,  R1 = 8,  R2 = 8; };
 
-template <int N>
+// Alternative plans with more threads per line (fewer values and registers
+// per thread, one more exchange), offered to the autotuner for the x passes.
+// VAR 0 is Plan<N>; sizes without an alternative reuse it.
+template <int N, int VAR>
+struct PlanV : Plan<N> {};
+template <> struct PlanV<128, 1> { static constexpr int P = 16, NP = 3, R0 = 8, R1 = 2, R2 = 8; };
+template <> struct PlanV<256, 1> { static constexpr int P = 32, NP = 3, R0 = 8, R1 = 4, R2 = 8; };
+template <> struct PlanV<512, 1> { static constexpr int P = 64, NP = 3, R0 = 8, R1 = 8, R2 = 8; };
+__host__ __device__ constexpr bool has_plan_variant(int N) { return N == 128 || N == 256 || N == 512; }
+
+template <int N, int VAR = 0>
 struct PlanInfo {
-    using PL = Plan<N>;
+    using PL = PlanV<N, VAR>;
     static constexpr int P = PL::P;
     static constexpr int V = N / P;
     static constexpr int NP = PL::NP;
@@ -251,10 +261,10 @@ __device__ __forceinline__ void exchange(float2 *v, int p, At at)
 // Full line transform.  In: v in first-pass input order.  Out: v in
 // last-pass output order (PlanInfo::out_pos).  Every thread of the block
 // must call it (it contains block barriers).
-template <int N, bool FWD, class At>
+template <int N, bool FWD, int VAR = 0, class At>
 __device__ __forceinline__ void fft_line(float2 *v, int p, const float2 *__restrict__ tw, At at)
 {
-    using PI = PlanInfo<N>;
+    using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P;
     pass_regs<N, PI::R0, 1, P, FWD>(v, p, tw);
     exchange<N, PI::R0, 1, PI::R1, P>(v, p, at);

@@ -55,6 +55,7 @@ struct Geo {
     int mom_blocks;
     // tuning of the stage passes (chosen by the autotuner)
     int tile_x, tile_y;          // columns per CTA of the x / y passes (8 or 16)
+    int plan_x;                  // FFT plan of the x passes (0: default, 1: more threads per line)
     int z_mode;                  // 0: persistent TMA z pass, 1: one CTA per row group
     int z_ctas;                  // persistent CTAs of the z-direction nonlinear pass
 };

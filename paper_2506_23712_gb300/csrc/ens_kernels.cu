@@ -332,6 +332,8 @@ cudaError_t prepare_kernels(int N, int nq, int nt, int ng)
     return o ? o->prepare(nq, nt, ng) : cudaErrorInvalidValue;
 }
 
+bool plan_variant_available(int N) { return has_plan_variant(N); }
+
 int znl_ctas_per_sm(int N)
 {
     const SizedOps *o = sized_ops(N);

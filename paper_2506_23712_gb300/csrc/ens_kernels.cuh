@@ -70,11 +70,14 @@ struct RowCfg {
 // divisor of kTile) as a template parameter: the autotuner picks it per grid
 // size.  Registers per thread stay the same for every T (128 at most where
 // the T = kTile variant asks for two CTAs per SM).
-template <int N, int T>
+template <int N, int T, int VAR = 0>
 struct ColCfg {
     static_assert(kTile % T == 0, "tile width must divide the column padding");
-    static constexpr int threads = T * PlanInfo<N>::P;
-    static constexpr int min_blocks = (256 / (kTile * PlanInfo<N>::P) > 0 ? 2 : 1) * (kTile / T);
+    static constexpr int threads = T * PlanInfo<N, VAR>::P;
+    // VAR 0 keeps 128 registers per thread where two 256-thread CTAs fit an
+    // SM; the wider plans (VAR 1) aim at 1024 resident threads (<= 64 registers)
+    static constexpr int min_blocks =
+        VAR == 0 ? (256 / (kTile * PlanInfo<N>::P) > 0 ? 2 : 1) * (kTile / T) : (1024 / threads > 0 ? 1024 / threads : 1);
 };
 
 // Launch helpers (host): shared memory bytes per pass.
@@ -101,11 +104,11 @@ __device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restri
 //   MODE 1: A_ij = i k_j u_i for ij = 11,12,13,21,22,23,31,32
 // grid (NK*NZp/T, members), block T*P.
 // ---------------------------------------------------------------------------
-template <int N, int MODE, int T>
-__global__ void __launch_bounds__(ColCfg<N, T>::threads, ColCfg<N, T>::min_blocks)
+template <int N, int MODE, int T, int VAR = 0>
+__global__ void __launch_bounds__(ColCfg<N, T, VAR>::threads, ColCfg<N, T, VAR>::min_blocks)
 k_inv_x(Geo g, int use_S)
 {
-    using PI = PlanInfo<N>;
+    using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P, V = PI::V;
     constexpr int NF = MODE == 0 ? 6 : 8;
     extern __shared__ float2 sm[];
@@ -158,7 +161,7 @@ k_inv_x(Geo g, int use_S)
             const float2 u = keep ? tile[q * per + ix * T + c] : make_float2(0.f, 0.f);
             v[i] = dx ? mul_i(cscale(u, (float)kxi)) : u;
         }
-        fft_line<N, false>(v, p, tw, at);
+        fft_line<N, false, VAR>(v, p, tw, at);
     };
     auto store = [&](const float2 *v, int f) {
         if (valid) {
@@ -533,11 +536,11 @@ __device__ __forceinline__ void block_sum_to(double *out, double (&vals)[NW], do
     }
 }
 
-template <int N, int MODE, int T>
-__global__ void __launch_bounds__(ColCfg<N, T>::threads, ColCfg<N, T>::min_blocks)
+template <int N, int MODE, int T, int VAR = 0>
+__global__ void __launch_bounds__(ColCfg<N, T, VAR>::threads, ColCfg<N, T, VAR>::min_blocks)
 k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
 {
-    using PI = PlanInfo<N>;
+    using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P, V = PI::V;
     extern __shared__ float2 sm[];
     float2 *tw = sm, *buf = sm + N, *tile = buf + N * T;   // tile: [3][NK][T]
@@ -566,7 +569,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
                 nxt[i] = valid ? Ain[(long long)(q + 1) * Dims<N>::SA + (long long)PI::in_pos(p, i) * Dims<N>::NZP]
                                : make_float2(0.f, 0.f);
         }
-        fft_line<N, true>(v, p, tw, at);
+        fft_line<N, true, VAR>(v, p, tw, at);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const int kx = wnum(PI::out_pos(p, i), N);
@@ -602,7 +605,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
     }
     // per kept mode of the tile: thread <-> (kx row, column), coalesced in the
     // column; the state reads of UB modes are issued together before use
-    constexpr int UB = 4;
+    constexpr int UB = VAR == 0 ? 4 : 2;   // fewer batched state reads under the tighter register budget
     for (int base = threadIdx.x; base < per; base += UB * blockDim.x) {
         float2 unb[UB][3], usb[UB][3];
         if constexpr (MODE == 0 || MODE == 1) {

@@ -29,6 +29,7 @@ int plan_threads(int N);
 int stats_blocks(int N);
 cudaError_t prepare_kernels(int N, int nq, int nt, int ng);
 int znl_ctas_per_sm(int N);   // resident CTAs per SM of the persistent z pass (0 on error)
+bool plan_variant_available(int N);   // the x passes have a second FFT plan for this size
 
 // Pass launchers of one grid size (ens_sized.cu, one translation unit per N).
 struct SizedOps {

@@ -23,12 +23,29 @@ cudaError_t allow_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// the second x-pass plan exists for some sizes only (a template, so that the
+// discarded branch is never instantiated)
+template <int M>
+cudaError_t prepare_variants()
+{
+    cudaError_t e = cudaSuccess;
+    if constexpr (has_plan_variant(M)) {
+        auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        chk(allow_smem(k_inv_x<M, 0, 16, 1>, smem_x<M, 16>()));
+        chk(allow_smem(k_inv_x<M, 0, 8, 1>, smem_x<M, 8>()));
+        chk(allow_smem(k_fwd_x<M, 0, 16, 1>, smem_x<M, 16>()));
+        chk(allow_smem(k_fwd_x<M, 0, 8, 1>, smem_x<M, 8>()));
+    }
+    return e;
+}
+
 cudaError_t prepare(int nq, int nt, int ng)
 {
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     chk(allow_smem(k_inv_x<N, 0, 16>, smem_x<N, 16>()));
     chk(allow_smem(k_inv_x<N, 0, 8>, smem_x<N, 8>()));
+    chk(prepare_variants<N>());
     chk(allow_smem(k_inv_x<N, 1, 16>, smem_x<N, 16>()));
     chk(allow_smem(k_inv_y<N, 16>, smem_cols<N, 16>()));
     chk(allow_smem(k_inv_y<N, 8>, smem_cols<N, 8>()));
@@ -56,15 +73,15 @@ int znl_per_sm()
     return per_sm;
 }
 
-template <int T>
+template <int T, int VAR = 0>
 void launch_cols(Pass pass, int mode, const Geo &g, MemberDev *md, int stage, int last, int arg, cudaStream_t s)
 {
-    constexpr int TC = ColCfg<N, T>::threads;
+    constexpr int TC = ColCfg<N, T, VAR>::threads;
     const dim3 grid_state(g.NK * g.NZp / T, g.members);
     const int col_tiles_mid = N * g.NZp / T;
     switch (pass) {
     case Pass::IX:
-        if (mode == 0) k_inv_x<N, 0, T><<<grid_state, TC, smem_x<N, T>(), s>>>(g, arg);
+        if (mode == 0) k_inv_x<N, 0, T, VAR><<<grid_state, TC, smem_x<N, T>(), s>>>(g, arg);
         break;
     case Pass::IY:
         // arg = number of fields, mode = first field
@@ -74,10 +91,30 @@ void launch_cols(Pass pass, int mode, const Geo &g, MemberDev *md, int stage, in
         k_fwd_y<N, T><<<dim3(col_tiles_mid, 3, g.members), TC, smem_cols<N, T>(), s>>>(g);
         break;
     case Pass::FX:
-        if (mode == 0) k_fwd_x<N, 0, T><<<grid_state, TC, smem_x<N, T>(), s>>>(g, md, stage, last);
+        if (mode == 0) k_fwd_x<N, 0, T, VAR><<<grid_state, TC, smem_x<N, T>(), s>>>(g, md, stage, last);
         break;
     default: break;
     }
+}
+
+// stage passes along x: tile width and FFT plan from the group's tuning
+template <int M>
+void launch_x_t(Pass pass, int mode, const Geo &g, MemberDev *md, int stage, int last, int arg, cudaStream_t s)
+{
+    if constexpr (has_plan_variant(M)) {
+        if (g.plan_x == 1) {
+            if (g.tile_x == 8) launch_cols<8, 1>(pass, mode, g, md, stage, last, arg, s);
+            else launch_cols<16, 1>(pass, mode, g, md, stage, last, arg, s);
+            return;
+        }
+    }
+    if (g.tile_x == 8) launch_cols<8>(pass, mode, g, md, stage, last, arg, s);
+    else launch_cols<16>(pass, mode, g, md, stage, last, arg, s);
+}
+
+void launch_x(Pass pass, int mode, const Geo &g, MemberDev *md, int stage, int last, int arg, cudaStream_t s)
+{
+    launch_x_t<N>(pass, mode, g, md, stage, last, arg, s);
 }
 
 void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last, int arg,
@@ -97,8 +134,7 @@ void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, 
     switch (pass) {
     case Pass::IX:
         if (mode == 0) {
-            if (g.tile_x == 8) launch_cols<8>(pass, mode, g, md, stage, last, arg, s);
-            else launch_cols<16>(pass, mode, g, md, stage, last, arg, s);
+            launch_x(pass, mode, g, md, stage, last, arg, s);
         } else {
             k_inv_x<N, 1, 16><<<grid_state, TC, smem_x<N, 16>(), s>>>(g, arg);
         }
@@ -124,8 +160,7 @@ void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, 
     case Pass::FX:
         switch (mode) {
         case 0:
-            if (g.tile_x == 8) launch_cols<8>(pass, mode, g, md, stage, last, arg, s);
-            else launch_cols<16>(pass, mode, g, md, stage, last, arg, s);
+            launch_x(pass, mode, g, md, stage, last, arg, s);
             break;
         case 1: k_fwd_x<N, 1, 16><<<grid_state, TC, smem_x<N, 16>(), s>>>(g, md, stage, last); break;
         case 2: k_fwd_x<N, 2, 16><<<grid_state, TC, smem_x<N, 16>(), s>>>(g, md, stage, last); break;

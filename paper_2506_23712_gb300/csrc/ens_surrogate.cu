@@ -516,11 +516,11 @@ __global__ void k_init_params(float *p, long long n, unsigned long long seed)
 //   per tile: features -> MMA(H0, W1) -> epilogue -> MMA(H, W2) -> [copy W3]
 //             epilogue -> MMA(H, W3) -> [copy W2] -> epilogue + head
 // The epilogue warp w reads TMEM lanes 32 (w mod 4) .. +31 (its rows) and
-// columns 128 (w / 4) .. +127.  Every mbarrier wait is bounded; a wait that
+// columns 64 (w / 4) .. +63 (16 warps: four per lane quarter).  Every mbarrier wait is bounded; a wait that
 // gives up sets *err, waits (bounded) for the copies and MMAs in flight,
 // frees the TMEM and returns.
 // ---------------------------------------------------------------------------
-constexpr int kInferThreads = 256;
+constexpr int kInferThreads = 512;
 constexpr size_t kInferSmem = 1024 + 65536 + 32768 + 131072 + 64;
 
 __global__ void __launch_bounds__(kInferThreads, 1)
@@ -538,10 +538,10 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
     uint64_t *bar_mma = reinterpret_cast<uint64_t *>(sW + 131072);
     uint64_t *bar_w = bar_mma + 1;
     uint32_t *holder = reinterpret_cast<uint32_t *>(bar_w + 1);
-    float *part = reinterpret_cast<float *>(sH);   // head partials [2][128], once layer 3 is done
+    float *part = reinterpret_cast<float *>(sH);   // head partials [4][128], once layer 3 is done
     const ParamLayout L = param_layout();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, half = warp >> 2;   // half: which 64 columns (0..3)
     if (warp == 0) tmem_alloc(holder, 256);
     if (tid == 0) {
         mbar_init(bar_mma, 1);
@@ -586,19 +586,22 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
     };
     const int row = quarter * 32 + lane;                       // this thread's TMEM lane = tile row
     const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16);
-    // bias + SiLU of this thread's 128 columns into H (BF16, swizzled K-blocks)
+    // bias + SiLU of this thread's 64 columns into H (BF16, swizzled K-blocks)
     auto epilogue = [&](const float *bias) {
 #pragma unroll 1
-        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
             float v[32];
             tc_ld_32cols(tl + (uint32_t)c0, v);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
+                const float4 b0 = __ldg(reinterpret_cast<const float4 *>(bias + c0 + j));
+                const float4 b1 = __ldg(reinterpret_cast<const float4 *>(bias + c0 + j + 4));
+                const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                 uint32_t w[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const float a = silu(v[j + 2 * t] + __ldg(bias + c0 + j + 2 * t));
-                    const float b = silu(v[j + 2 * t + 1] + __ldg(bias + c0 + j + 2 * t + 1));
+                    const float a = silu(v[j + 2 * t] + bb[2 * t]);
+                    const float b = silu(v[j + 2 * t + 1] + bb[2 * t + 1]);
                     const __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
                     w[t] = *reinterpret_cast<const uint32_t *>(&hb);
                 }
@@ -661,19 +664,26 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
         // head: logit = sum_c BF16(SiLU(z3 + b3)) w4 + b4
         float acc = 0.f;
 #pragma unroll 1
-        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
             float v[32];
             tc_ld_32cols(tl + (uint32_t)c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float h = __bfloat162float(__float2bfloat16(silu(v[j] + __ldg(p + L.b3 + c0 + j))));
-                acc = fmaf(h, __ldg(p + L.w4 + c0 + j), acc);
+            for (int j = 0; j < 32; j += 4) {
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(p + L.b3 + c0 + j));
+                const float4 w = __ldg(reinterpret_cast<const float4 *>(p + L.w4 + c0 + j));
+                const float bb[4] = {b.x, b.y, b.z, b.w}, ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float h = __bfloat162float(__float2bfloat16(silu(v[j + t] + bb[t])));
+                    acc = fmaf(h, ww[t], acc);
+                }
             }
         }
         part[half * 128 + row] = acc;
         tc_fence_before();
         __syncthreads();
-        if (tid < 128 && r0 + tid < real) logit[r0 + tid] = part[tid] + part[128 + tid] + __ldg(p + L.b4);
+        if (tid < 128 && r0 + tid < real)
+            logit[r0 + tid] = ((part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid])) + __ldg(p + L.b4);
         __syncthreads();   // part (in H) is rewritten by the next tile's features
     }
     if (!ok) {

@@ -96,6 +96,37 @@ def test_every_variant_matches_oracle(E):
     base.close()
 
 
+def test_x_plan_variant_matches_oracle(E):
+    """The second FFT plan of the x passes (N = 128: 8x2x8 on 16 threads per
+    line) with both column tiles, against the oracle after one RK3 step."""
+    m = E.Member(N=128, nu=0.01, lam=0.7, k_lo=1, k_hi=2, dt=-1, cfl=0.2, dt_max=0.01, rk_order=3, seed=71)
+    om = oracle_member(m)
+    ref = O.initial_field(om)
+    O.step(om, ref, 1)
+    base = E.Ensemble([m])
+    base.step(1)
+    f0 = base.field(0)
+    base.close()
+    for plan in (1,):
+        for tx in (16, 8):
+            ens = E.Ensemble([m])
+            t = ens.tuning()
+            t["groups"][0].update(plan_x=plan, tile_x=tx)
+            ens.set_tuning(t)
+            ens.step(1)
+            f = ens.field(0)
+            assert rel(f, ref) < 1e-5, (plan, tx)
+            assert rel(f, f0) < 1e-6, (plan, tx)
+            ens.close()
+    # sizes without a second plan refuse plan_x = 1
+    ens = E.Ensemble(members(E))
+    t = ens.tuning()
+    t["groups"][0]["plan_x"] = 1
+    with pytest.raises(E.EnsError):
+        ens.set_tuning(t)
+    ens.close()
+
+
 def test_invalid_tuning_rejected_and_context_usable(E):
     ens = E.Ensemble(members(E))
     good = ens.tuning()
