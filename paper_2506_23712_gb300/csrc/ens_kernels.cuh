@@ -92,6 +92,20 @@ constexpr size_t smem_rows() { return sizeof(float2) * (size_t)(N + RowCfg<N>::R
 
 __device__ __forceinline__ int wnum(int pos, int N) { return pos <= N / 2 ? pos : pos - N; }
 
+// 16-byte asynchronous global -> shared copy (cp.async, L2 only); bytes < 16
+// of the source are read and the rest of the destination is zero-filled
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src, int bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restrict__ g, int N)
 {
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g[i];
@@ -111,7 +125,7 @@ k_inv_x(Geo g, int use_S)
     using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P, V = PI::V;
     constexpr int NF = MODE == 0 ? 6 : 8;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N, *tile = buf + N * T;   // tile: [3][NK][T]
 
     const int c = threadIdx.x % T, p = threadIdx.x / T;
@@ -125,27 +139,17 @@ k_inv_x(Geo g, int use_S)
     const float kzf = (float)kz;
     const long long rowU = (long long)Dims<N>::NK * Dims<N>::NZP;
     const float2 *X = (use_S ? g.S : g.U) + (long long)m * 3 * Dims<N>::SU + col0;
-    // coalesced staging of the three velocity components of this column tile
+    // staging of the three velocity components of this column tile with
+    // asynchronous 16-byte copies (two columns each, the dealiased columns
+    // zero-filled): the whole tile is in flight at once, no registers held
     constexpr int per = Dims<N>::NK * T;
-    constexpr int kBatch = 8;   // loads in flight per thread before the shared stores
-    for (int base = threadIdx.x; base < 3 * per; base += kBatch * blockDim.x) {
-        float2 tmp[kBatch];
-#pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
-            const int idx = base + k * blockDim.x;
-            tmp[k] = make_float2(0.f, 0.f);
-            if (idx < 3 * per) {
-                const int q = idx / per, rem = idx % per;
-                const int ix = rem / T, cc = rem % T;
-                if (kz0 + cc < Dims<N>::NZ) tmp[k] = X[q * Dims<N>::SU + ix * rowU + cc];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
-            const int idx = base + k * blockDim.x;
-            if (idx < 3 * per) tile[idx] = tmp[k];
-        }
+    for (int idx = 2 * threadIdx.x; idx < 3 * per; idx += 2 * blockDim.x) {
+        const int q = idx / per, rem = idx % per;
+        const int ix = rem / T, cc = rem % T;   // cc even
+        const int nvalid = min(max(Dims<N>::NZ - (kz0 + cc), 0), 2);
+        cp_async_16(&tile[idx], X + q * Dims<N>::SU + ix * rowU + cc, 8 * nvalid);
     }
+    cp_async_wait_all();
     load_twiddles(tw, g.tw, N);   // block barrier: tile complete
 
     float2 *dst0 = g.A + (long long)m * kFields * Dims<N>::SA + ((long long)iy * N) * Dims<N>::NZP + kz;
@@ -224,7 +228,7 @@ k_inv_y(Geo g, int f0)
 {
     using PI = PlanInfo<N>;
     constexpr int P = PI::P, V = PI::V;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N;
     load_twiddles(tw, g.tw, N);
     const int c = threadIdx.x % T, p = threadIdx.x / T;
@@ -259,7 +263,7 @@ k_fwd_y(Geo g)
 {
     using PI = PlanInfo<N>;
     constexpr int P = PI::P, V = PI::V;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N;
     load_twiddles(tw, g.tw, N);
     const int c = threadIdx.x % T, p = threadIdx.x / T;
@@ -373,7 +377,7 @@ k_z(Geo g, MemberDev *md, int stage)
     using PI = WPlanInfo<N>;
     using RC = RowCfg<N>;
     constexpr int P = PI::P, V = PI::V, RZ = RC::RZ;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N;
     load_twiddles(tw, g.tw, N);
     const int p = threadIdx.x % P, r = threadIdx.x / P;
@@ -542,7 +546,7 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
 {
     using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P, V = PI::V;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N, *tile = buf + N * T;   // tile: [3][NK][T]
     load_twiddles(tw, g.tw, N);
     const int c = threadIdx.x % T, p = threadIdx.x / T;

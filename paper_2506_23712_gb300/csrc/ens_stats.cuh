@@ -73,7 +73,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     using PI = WPlanInfo<N>;
     using RC = RowCfg<N>;
     constexpr int P = PI::P, V = PI::V, RZ = RC::RZ;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N;
     const int L = h.counts_len;
     unsigned *hist = reinterpret_cast<unsigned *>(buf + RZ * RC::SROW);
