@@ -5,7 +5,8 @@
 // line, Hermitian extension), the rotational nonlinear term n = u x omega is
 // formed point by point together with max|u_i| (CFL step, Sec. IV) and a
 // non-finite check, and n goes straight back along z; the dealiased half
-// spectra of n overwrite fields 0..2 of the row in buffer B.
+// spectra of n overwrite fields 0..2 of the row in buffer B (n_z of two
+// consecutive rows of a warp's stream share one forward complex line).
 //
 // Each warp owns a stream of row groups (32/P rows per group, P threads per
 // row) and double-buffers their inputs in shared memory: one lane issues
@@ -121,6 +122,11 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
     };
     bool timed_out = false;
     int it = 0;
+    // n_z of consecutive rows of this warp's stream are paired into one
+    // complex line for the forward transform (three forward lines per two
+    // rows instead of four): the first row's n_z waits in registers
+    float nzp[V];
+    float2 *pend = nullptr;   // field-2 destination of the waiting row (warp-uniform null / non-null)
     for (; grp < T; ++it, grp += W) {
         const int b = it & 1;
         const long long nxt = grp + W;
@@ -139,7 +145,8 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         }
         const long long rho = lg * LPW + line;
         const float2 *X = st + b * C::STAGE + line * 6 * NZ2;
-        float2 a[V], bb[V], cc[V], w0[V], w1[V];
+        float2 a[V], bb[V], cc[V], w0[V];
+        float nz[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const int pos = PI::in_pos(p, i);
@@ -158,13 +165,28 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
             umax = fmaxf(umax, fmaxf(fabsf(ux), fmaxf(fabsf(uy), fabsf(uz))));
             finite = finite && isfinite(ux + uy + uz + wx + wy + wz);
             w0[i] = make_float2(uy * wz - uz * wy, uz * wx - ux * wz);
-            w1[i] = make_float2(ux * wy - uy * wx, 0.f);
+            nz[i] = ux * wy - uy * wx;
         }
         static_assert(PI::matched, "first and last radix must agree");
         float2 *Bout = g.B + m * kFields * Dims<N>::SB + rho * Dims<N>::NZP;
         forward_pair_store_tw<N>(w0, p, line, TW, rowbuf, Bout, Bout + Dims<N>::SB, Dims<N>::NZ);
-        forward_pair_store_tw<N>(w1, p, line, TW, rowbuf, Bout + 2 * Dims<N>::SB, nullptr, Dims<N>::NZ);
+        if (pend) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) w0[i] = make_float2(nzp[i], nz[i]);
+            forward_pair_store_tw<N>(w0, p, line, TW, rowbuf, pend, Bout + 2 * Dims<N>::SB, Dims<N>::NZ);
+            pend = nullptr;
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) nzp[i] = nz[i];
+            pend = Bout + 2 * Dims<N>::SB;
+        }
         __syncwarp();   // all lanes are done with buffer b before it is refilled
+    }
+    if (pend && !timed_out) {   // an odd row count: the last n_z goes alone
+        float2 w[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) w[i] = make_float2(nzp[i], 0.f);
+        forward_pair_store_tw<N>(w, p, line, TW, rowbuf, pend, nullptr, Dims<N>::NZ);
     }
     if (grp > (long long)blockIdx.x * C::WPB + warp || timed_out) flush(cur_m);
     if (timed_out) {
