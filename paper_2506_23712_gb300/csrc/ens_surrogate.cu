@@ -596,12 +596,21 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
     };
     const int row = quarter * 32 + lane;                       // this thread's TMEM lane = tile row
     const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16);
-    // bias + SiLU of this thread's 64 columns into H (BF16, swizzled K-blocks)
+    // bias + SiLU of this thread's 64 columns into H (BF16, swizzled K-blocks);
+    // the second 32-column TMEM load is in flight while the first is processed
     auto epilogue = [&](const float *bias) {
-#pragma unroll 1
-        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+        uint32_t ra[32], rb[32];
+        tc_ld_32cols_issue(tl + (uint32_t)(half * 64), ra);
+        tc_ld_wait(ra);
+        tc_ld_32cols_issue(tl + (uint32_t)(half * 64 + 32), rb);
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int c0 = half * 64 + 32 * h2;
+            if (h2 == 1) tc_ld_wait(rb);
+            const uint32_t *rr = h2 == 0 ? ra : rb;
             float v[32];
-            tc_ld_32cols(tl + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
                 const float4 b0 = __ldg(reinterpret_cast<const float4 *>(bias + c0 + j));
@@ -673,10 +682,18 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
         if (tid == 0) copy_w(img2, sW, 131072);   // for the next tile
         // head: logit = sum_c BF16(SiLU(z3 + b3)) w4 + b4
         float acc = 0.f;
-#pragma unroll 1
-        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+        uint32_t ra[32], rb[32];
+        tc_ld_32cols_issue(tl + (uint32_t)(half * 64), ra);
+        tc_ld_wait(ra);
+        tc_ld_32cols_issue(tl + (uint32_t)(half * 64 + 32), rb);
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int c0 = half * 64 + 32 * h2;
+            if (h2 == 1) tc_ld_wait(rb);
+            const uint32_t *rr = h2 == 0 ? ra : rb;
             float v[32];
-            tc_ld_32cols(tl + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]);
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
                 const float4 b = __ldg(reinterpret_cast<const float4 *>(p + L.b3 + c0 + j));
