@@ -195,6 +195,10 @@ ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
  *                   1 (N = 128, 256, 512 only) a plan with twice the
  *                   threads per line and a tighter register budget
  *                   (128: 8x2x8, 256: 8x4x8, 512: 8x8x8 on 64 threads);
+ *   fx_split        0: the last pass of a stage fused (forward x transform,
+ *                   projection, forcing, RK update in one launch); 1: two
+ *                   launches (transform into a compact spectral buffer, then
+ *                   a streaming update), more HBM bytes, lighter kernels;
  *   z_variant       0: persistent TMA-pipelined z pass with z_ctas_per_sm
  *                   CTAs per SM (1 .. the kernel's occupancy limit),
  *                   1: one CTA per group of rows (z_ctas_per_sm unused
@@ -210,6 +214,7 @@ typedef struct {
     int z_variant;
     int z_ctas_per_sm;
     int plan_x;
+    int fx_split;
 } ens_group_tuning;
 typedef struct {
     int groups;          /* number of grid-size groups (read-only) */
@@ -228,7 +233,7 @@ ens_status ens_get_tuning(const ens_ctx *ctx, ens_tuning *out);
 ens_status ens_set_tuning(ens_ctx *ctx, const ens_tuning *t);
 /* Time the variants on this context's own members and install the fastest:
  * coordinate descent over plan_x, tile_x, tile_y, the z variant and its CTAs
- * per SM for each group, then parallel_groups; each trial restores the member
+ * per SM, fx_split for each group, then parallel_groups; each trial restores the member
  * state from a device snapshot, runs one untimed step and times `steps`
  * graph replays with CUDA events; a candidate wins only if it is more than
  * 1% faster.  The member state is restored afterwards (the simulation does

@@ -157,6 +157,7 @@ size_t carve(const ens_member_desc *m, int n, const ens_hist_spec *h, char *base
         g.NZp = (g.NZ + kTile - 1) / kTile * kTile;
         g.tile_x = g.tile_y = kTile;
         g.plan_x = 0;
+        g.fx_split = 0;
         g.z_mode = 0;
         g.members = (int)gr.members.size();
         g.first = first;
@@ -172,6 +173,7 @@ size_t carve(const ens_member_desc *m, int n, const ens_hist_spec *h, char *base
         g.shells = (int)std::ceil(std::sqrt(3.0) * g.kc) + 2;
         g.shell = ar.take<double>((size_t)g.shells * g.members);
         PB = std::max(PB, g.NK * g.NZp / 8);   // narrowest column tile of the update pass
+        PB = std::max(PB, (int)((g.sU + kUpdChunk - 1) / kUpdChunk));   // split update pass
         MB = std::max(MB, stats_blocks(N));
         groups.push_back(gr);
     }
@@ -529,7 +531,13 @@ int ens_member_n(const ens_ctx *ctx, int i)
 {
     return (ctx && i >= 0 && i < (int)ctx->desc.size()) ? ctx->desc[i].N : 0;
 }
-int ens_kernels_per_step(const ens_ctx *ctx) { return ctx ? ctx->rk * (5 * (int)ctx->groups.size() + 1) : 0; }
+int ens_kernels_per_step(const ens_ctx *ctx)
+{
+    if (!ctx) return 0;
+    int per_stage = 1;   // the per-member stage reduction
+    for (auto &gr : ctx->groups) per_stage += 5 + gr.geo.fx_split;
+    return ctx->rk * per_stage;
+}
 
 ens_status ens_step_sequential(ens_ctx *ctx, int nsteps)
 {
@@ -950,6 +958,7 @@ void tuning_of(const ens_ctx *ctx, ens_tuning *t)
         o.z_variant = g.z_mode;
         o.z_ctas_per_sm = ctx->sms > 0 ? g.z_ctas / ctx->sms : 0;
         o.plan_x = g.plan_x;
+        o.fx_split = g.fx_split;
     }
 }
 
@@ -979,6 +988,10 @@ ens_status tuning_valid(const ens_ctx *ctx, const ens_tuning *t, std::string &wh
             why = "plan_x must be 0, or 1 for N = 128, 256, 512";
             return ENS_EINVAL;
         }
+        if (o.fx_split != 0 && o.fx_split != 1) {
+            why = "fx_split must be 0 or 1";
+            return ENS_EINVAL;
+        }
         if (o.z_variant != 0 && o.z_variant != 1) {
             why = "z_variant must be 0 or 1";
             return ENS_EINVAL;
@@ -998,7 +1011,8 @@ ens_status sync_nblk(ens_ctx *ctx)
 {
     for (auto &gr : ctx->groups) {
         const Geo &g = gr.geo;
-        std::vector<int> v(g.members, g.NK * g.NZp / g.tile_x);
+        const int nblk = g.fx_split ? (int)((g.sU + kUpdChunk - 1) / kUpdChunk) : g.NK * g.NZp / g.tile_x;
+        std::vector<int> v(g.members, nblk);
         ENS_CUDA(ctx, cudaMemcpy2DAsync(&ctx->md[g.first].nblk, sizeof(MemberDev), v.data(), sizeof(int),
                                         sizeof(int), g.members, cudaMemcpyHostToDevice, ctx->stream));
     }
@@ -1017,6 +1031,7 @@ ens_status apply_tuning(ens_ctx *ctx, const ens_tuning *t)
         g.tile_x = o.tile_x;
         g.tile_y = o.tile_y;
         g.plan_x = o.plan_x;
+        g.fx_split = o.fx_split;
         g.z_mode = o.z_variant;
         g.z_ctas = o.z_ctas_per_sm * ctx->sms;
     }
@@ -1178,6 +1193,11 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
         if (rs == ENS_OK && best.group[gi].z_variant != 1) {
             cand = best;
             cand.group[gi].z_variant = 1;
+            consider(cand);
+        }
+        if (rs == ENS_OK) {
+            cand = best;
+            cand.group[gi].fx_split = 1 - best.group[gi].fx_split;
             consider(cand);
         }
     }

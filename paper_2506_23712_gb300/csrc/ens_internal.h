@@ -10,6 +10,7 @@ constexpr int kTile = 16;        // column padding of the layouts; widest column
 constexpr int kFields = 8;       // fields per member in the pass buffers
 constexpr int kNMom = 48;        // gradient moment sums per member
 constexpr int kStatsIters = 16;  // row groups per CTA in the statistics pass
+constexpr int kUpdChunk = 2048;  // modes per CTA of the split update pass (256 threads x 8)
 
 // Per-member parameters and run state, resident in device memory.
 struct MemberDev {
@@ -56,6 +57,7 @@ struct Geo {
     // tuning of the stage passes (chosen by the autotuner)
     int tile_x, tile_y;          // columns per CTA of the x / y passes (8 or 16)
     int plan_x;                  // FFT plan of the x passes (0: default, 1: more threads per line)
+    int fx_split;                // last pass of a stage: 0 fused, 1 transform + update launches
     int z_mode;                  // 0: persistent TMA z pass, 1: one CTA per row group
     int z_ctas;                  // persistent CTAs of the z-direction nonlinear pass
 };

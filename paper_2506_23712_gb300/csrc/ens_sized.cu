@@ -1,6 +1,7 @@
 // Pass launchers of one grid size N = ENS_N.  The build compiles this file
 // once per supported N (-DENS_N=16 ... 512), so the heavy template
 // instantiations of the FFT passes spread over parallel compiler jobs.
+#include "ens_fxsplit.cuh"
 #include "ens_launch.h"
 #include "ens_stats.cuh"
 #include "ens_znl.cuh"
@@ -46,6 +47,7 @@ cudaError_t prepare(int nq, int nt, int ng)
     chk(allow_smem(k_inv_x<N, 0, 16>, smem_x<N, 16>()));
     chk(allow_smem(k_inv_x<N, 0, 8>, smem_x<N, 8>()));
     chk(prepare_variants<N>());
+    chk(allow_smem(k_fwd_x_fft<N, 16>, smem_cols<N, 16>()));
     chk(allow_smem(k_inv_x<N, 1, 16>, smem_x<N, 16>()));
     chk(allow_smem(k_inv_y<N, 16>, smem_cols<N, 16>()));
     chk(allow_smem(k_inv_y<N, 8>, smem_cols<N, 8>()));
@@ -160,7 +162,13 @@ void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, 
     case Pass::FX:
         switch (mode) {
         case 0:
-            launch_x(pass, mode, g, md, stage, last, arg, s);
+            if (g.fx_split) {
+                k_fwd_x_fft<N, 16><<<dim3(g.NK * g.NZp / 16, 3, g.members), ColCfg<N, 16>::threads,
+                                     smem_cols<N, 16>(), s>>>(g);
+                k_update<N><<<dim3(update_blocks<N>(), g.members), kUpdThreads, 0, s>>>(g, md, stage, last);
+            } else {
+                launch_x(pass, mode, g, md, stage, last, arg, s);
+            }
             break;
         case 1: k_fwd_x<N, 1, 16><<<grid_state, TC, smem_x<N, 16>(), s>>>(g, md, stage, last); break;
         case 2: k_fwd_x<N, 2, 16><<<grid_state, TC, smem_x<N, 16>(), s>>>(g, md, stage, last); break;

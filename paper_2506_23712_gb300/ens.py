@@ -79,7 +79,8 @@ ENS_MAX_GROUPS = 8
 
 class GroupTuning(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-                ("z_variant", ctypes.c_int), ("z_ctas_per_sm", ctypes.c_int), ("plan_x", ctypes.c_int)]
+                ("z_variant", ctypes.c_int), ("z_ctas_per_sm", ctypes.c_int), ("plan_x", ctypes.c_int),
+                ("fx_split", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):
@@ -215,7 +216,7 @@ def ens_step_sequential(ctx, nsteps=1):
     _check(lib().ens_step_sequential(ctx, nsteps), ctx)
 
 
-_GROUP_KEYS = ("N", "tile_x", "tile_y", "z_variant", "z_ctas_per_sm", "plan_x")
+_GROUP_KEYS = ("N", "tile_x", "tile_y", "z_variant", "z_ctas_per_sm", "plan_x", "fx_split")
 
 
 def _tuning_dict(t: Tuning) -> dict:

@@ -59,6 +59,11 @@ def variants(base):
     for g in t["groups"]:
         g["z_ctas_per_sm"] = 1
     out.append(t)
+    for tx in (16, 8):
+        t = json.loads(json.dumps(base))
+        for g in t["groups"]:
+            g.update(fx_split=1, tile_x=tx)
+        out.append(t)
     return out
 
 
@@ -146,15 +151,17 @@ def test_invalid_tuning_rejected_and_context_usable(E):
     ens.close()
 
 
-def test_narrow_tiles_keep_energy_sums_over_several_steps(E):
+@pytest.mark.parametrize("change", [{"tile_x": 8}, {"fx_split": 1}])
+def test_update_variants_keep_energy_sums_over_several_steps(E, change):
     """tile_x = 8 doubles the update pass's CTA partials of the FP64 energy
-    sums; after three steps the forcing amplitude (from E_B) still gives the
-    exact injected power and the fields follow the oracle."""
+    sums and fx_split = 1 moves them to the split update launch; after three
+    steps the forcing amplitude (from E_B) still gives the exact injected
+    power and the fields follow the oracle."""
     ms = members(E)
     ens = E.Ensemble(ms)
     t = ens.tuning()
     for g in t["groups"]:
-        g["tile_x"] = 8
+        g.update(change)
     ens.set_tuning(t)
     ens.step(3)
     for i, (m, d) in enumerate(zip(ms, ens.diagnostics())):
