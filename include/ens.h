@@ -358,6 +358,14 @@ ens_status ens_ratio_exponents(const ens_zeta_spec *zeta, double *out);
  * Host arithmetic; R0 may be NULL. */
 ens_status ens_scale_gap(int n, const double *lambdas, const double *rlambda, double R_ref, double *Z, double *R0);
 
+/* Change a member's time-step rule from the next step on (dt > 0: fixed dt;
+ * otherwise CFL with number cfl > 0, capped at dt_max if dt_max > 0), for
+ * instance to retry a member that went non-finite with a smaller CFL number.
+ * The member's description (and so checkpoint compatibility) is unchanged;
+ * the rule itself is part of the run state that ens_save writes.
+ * Synchronises. */
+ens_status ens_set_timestep(ens_ctx *ctx, int member, double dt, double cfl, double dt_max);
+
 /* ---- checkpoint / resume ------------------------------------------------ */
 
 /* Write the whole ensemble to a file: member descriptions, the spectral

@@ -4,6 +4,7 @@
 #include "ens_launch.h"
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1270,6 +1271,25 @@ bool same_hist(const ens_hist_spec &a, const ens_hist_spec &b)
 }  // namespace
 
 extern "C" {
+
+ens_status ens_set_timestep(ens_ctx *ctx, int member, double dt, double cfl, double dt_max)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (member < 0 || member >= (int)ctx->desc.size() || !std::isfinite(dt) || !std::isfinite(cfl) ||
+        !std::isfinite(dt_max) || (!(dt > 0.0) && !(cfl > 0.0))) {
+        ctx->err = "ens_set_timestep: bad member or time-step rule";   // not sticky
+        return ENS_EINVAL;
+    }
+    MemberDev *d = ctx->md + slot_of(ctx, member);
+    const double v[3] = {dt > 0.0 ? dt : 0.0, cfl, dt_max};   // dt_fixed, cfl, dt_max are adjacent
+    static_assert(offsetof(MemberDev, cfl) == offsetof(MemberDev, dt_fixed) + sizeof(double) &&
+                      offsetof(MemberDev, dt_max) == offsetof(MemberDev, cfl) + sizeof(double),
+                  "time-step fields must be contiguous");
+    ENS_CUDA(ctx, cudaMemcpyAsync(&d->dt_fixed, v, sizeof v, cudaMemcpyHostToDevice, ctx->stream));
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ENS_OK;
+}
 
 ens_status ens_save(ens_ctx *ctx, const char *path)
 {

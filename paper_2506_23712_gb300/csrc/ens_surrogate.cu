@@ -177,7 +177,9 @@ __device__ void row_features(const RowSpec &rs, double lam, int bin, float *f)
     f[1] = r;
     f[2] = (float)(lam / 5.0);
     f[3] = x;
-    f[4 + kind] = 1.f;
+    f[4] = kind == 0 ? 1.f : 0.f;   // one-hot kind, compile-time slots (keeps f in registers)
+    f[5] = kind == 1 ? 1.f : 0.f;
+    f[6] = kind == 2 ? 1.f : 0.f;
     const float s3[3] = {q, r, x};
     int o = 7;
     for (int c = 0; c < 3; ++c)
@@ -531,12 +533,19 @@ __global__ void k_init_params(float *p, long long n, unsigned long long seed)
 // frees the TMEM and returns.
 // ---------------------------------------------------------------------------
 constexpr int kInferThreads = 512;
+
+// biases and head weights by value: kernel parameters live in the constant
+// bank, so the epilogue's warp-uniform reads are broadcasts
+struct MlpBias {
+    float b1[kHid], b2[kHid], b3[kHid], w4[kHid];
+    float b4;
+};
 constexpr size_t kInferSmem = 1024 + 65536 + 32768 + 131072 + 64;
 
 __global__ void __launch_bounds__(kInferThreads, 1)
 k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long long ntiles,
             const unsigned char *__restrict__ img1, const unsigned char *__restrict__ img2,
-            const unsigned char *__restrict__ img3, const float *__restrict__ p, float *__restrict__ logit,
+            const unsigned char *__restrict__ img3, const __grid_constant__ MlpBias bias, float *__restrict__ logit,
             int *err)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -549,7 +558,6 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
     uint64_t *bar_w = bar_mma + 1;
     uint32_t *holder = reinterpret_cast<uint32_t *>(bar_w + 1);
     float *part = reinterpret_cast<float *>(sH);   // head partials [4][128], once layer 3 is done
-    const ParamLayout L = param_layout();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, half = warp >> 2;   // half: which 64 columns (0..3)
     if (warp == 0) tmem_alloc(holder, 256);
@@ -598,7 +606,7 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
     const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16);
     // bias + SiLU of this thread's 64 columns into H (BF16, swizzled K-blocks);
     // the second 32-column TMEM load is in flight while the first is processed
-    auto epilogue = [&](const float *bias) {
+    auto epilogue = [&](const float *bv) {
         uint32_t ra[32], rb[32];
         tc_ld_32cols_issue(tl + (uint32_t)(half * 64), ra);
         tc_ld_wait(ra);
@@ -613,9 +621,9 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
             for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
-                const float4 b0 = __ldg(reinterpret_cast<const float4 *>(bias + c0 + j));
-                const float4 b1 = __ldg(reinterpret_cast<const float4 *>(bias + c0 + j + 4));
-                const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                float bb[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) bb[t] = bv[c0 + j + t];
                 uint32_t w[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
@@ -663,7 +671,7 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
         if (tile != blockIdx.x) ok = ok && wait(bar_w, n_w);   // W2 refilled during the last epilogue
         tc_fence_after();
         if (!__syncthreads_and(ok)) break;
-        epilogue(p + L.b1);
+        epilogue(bias.b1);
         publish();
         // layer 2, then W3 streams in while the epilogue runs
         mma_layer(sW, 4);
@@ -671,7 +679,7 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
         tc_fence_after();
         if (!__syncthreads_and(ok)) break;
         if (tid == 0) copy_w(img3, sW, 131072);
-        epilogue(p + L.b2);
+        epilogue(bias.b2);
         publish();
         ok = wait(bar_w, n_w);
         if (!__syncthreads_and(ok)) break;
@@ -696,9 +704,12 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
             for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]);
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
-                const float4 b = __ldg(reinterpret_cast<const float4 *>(p + L.b3 + c0 + j));
-                const float4 w = __ldg(reinterpret_cast<const float4 *>(p + L.w4 + c0 + j));
-                const float bb[4] = {b.x, b.y, b.z, b.w}, ww[4] = {w.x, w.y, w.z, w.w};
+                float bb[4], ww[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    bb[t] = bias.b3[c0 + j + t];
+                    ww[t] = bias.w4[c0 + j + t];
+                }
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const float h = __bfloat162float(__float2bfloat16(silu(v[j + t] + bb[t])));
@@ -710,7 +721,7 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
         tc_fence_before();
         __syncthreads();
         if (tid < 128 && r0 + tid < real)
-            logit[r0 + tid] = ((part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid])) + __ldg(p + L.b4);
+            logit[r0 + tid] = ((part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid])) + bias.b4;
         __syncthreads();   // part (in H) is rewritten by the next tile's features
     }
     if (!ok) {
@@ -806,16 +817,31 @@ bool forward(ens_surrogate *S, long long rows, bool keep_t)
     return true;
 }
 
+// biases and head of the current parameters (host copy for the kernel parameters)
+bool mlp_bias(ens_surrogate *S, MlpBias *b)
+{
+    const ParamLayout &L = S->L;
+    cudaStream_t s = S->s;
+    return cudaMemcpyAsync(b->b1, S->p + L.b1, sizeof(float) * kHid, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+           cudaMemcpyAsync(b->b2, S->p + L.b2, sizeof(float) * kHid, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+           cudaMemcpyAsync(b->b3, S->p + L.b3, sizeof(float) * kHid, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+           cudaMemcpyAsync(b->w4, S->p + L.w4, sizeof(float) * kHid, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+           cudaMemcpyAsync(&b->b4, S->p + L.b4, sizeof(float), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+           cudaStreamSynchronize(s) == cudaSuccess;
+}
+
 // fused inference of `real` rows (lambda values in S->lam) into S->logit
 bool forward_fused(ens_surrogate *S, const RowSpec &rs, long long real)
 {
     cudaStream_t s = S->s;
     const long long n = (long long)kHid * kHid;
+    MlpBias bias;
+    if (!mlp_bias(S, &bias)) return false;
     k_pack_weights_img<<<blocks(n, 256), 256, 0, s>>>(S->p, S->img, S->img + 32768, S->img + 32768 + 131072);
     const long long ntiles = (real + 127) / 128;
     const int grid = (int)std::min<long long>(ntiles, S->sms > 0 ? S->sms : 1);
     k_mlp_infer<<<grid, kInferThreads, kInferSmem, s>>>(rs, S->lam, real, ntiles, S->img, S->img + 32768,
-                                                       S->img + 32768 + 131072, S->p, S->logit, S->err);
+                                                       S->img + 32768 + 131072, bias, S->logit, S->err);
     return cudaGetLastError() == cudaSuccess;
 }
 
@@ -1162,9 +1188,11 @@ ens_status ens_surrogate_time_infer(ens_surrogate *S, const ens_hist_spec *h, in
     const int grid = (int)std::min<long long>(ntiles, S->sms > 0 ? S->sms : 1);
     k_pack_weights_img<<<blocks((long long)kHid * kHid, 256), 256, 0, S->s>>>(S->p, S->img, S->img + 32768,
                                                                               S->img + 32768 + 131072);
+    MlpBias bias;
+    if (!mlp_bias(S, &bias)) return ENS_ECUDA;
     auto launch = [&]() {
         k_mlp_infer<<<grid, kInferThreads, kInferSmem, S->s>>>(rs, S->lam, real, ntiles, S->img, S->img + 32768,
-                                                               S->img + 32768 + 131072, S->p, S->logit, S->err);
+                                                               S->img + 32768 + 131072, bias, S->logit, S->err);
     };
     launch();   // warm-up
     cudaEvent_t a, b;

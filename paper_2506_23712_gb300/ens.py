@@ -115,6 +115,7 @@ SIGNATURES = [
     ("ens_nelkin_exponents", _i, [_P(ZetaSpec), _i, _vp, _vp]),
     ("ens_ratio_exponents", _i, [_P(ZetaSpec), _vp]),
     ("ens_scale_gap", _i, [_i, _vp, _vp, _d, _P(_d), _P(_d)]),
+    ("ens_set_timestep", _i, [_vp, _i, _d, _d, _d]),
     ("ens_save", _i, [_vp, ctypes.c_char_p]),
     ("ens_load", _i, [_vp, ctypes.c_char_p]),
     ("ens_get_field", _i, [_vp, _i, _vp]),
@@ -396,6 +397,10 @@ def ens_scale_gap(lambdas, rlambda, R_ref):
     return Z.value, R0.value
 
 
+def ens_set_timestep(ctx, member: int, dt: float, cfl: float, dt_max: float):
+    _check(lib().ens_set_timestep(ctx, member, dt, cfl, dt_max), ctx)
+
+
 def ens_save(ctx, path: str):
     _check(lib().ens_save(ctx, path.encode()), ctx)
 
@@ -531,6 +536,9 @@ class Ensemble:
 
     def save(self, path: str):
         ens_save(self.ctx, path)
+
+    def set_timestep(self, member: int, dt: float, cfl: float, dt_max: float):
+        ens_set_timestep(self.ctx, member, dt, cfl, dt_max)
 
     def load(self, path: str):
         ens_load(self.ctx, path)

@@ -105,3 +105,42 @@ def test_load_refuses_bad_files(E, tmp_path):
     a.step(1)
     a.diagnostics()
     a.close()
+
+
+def test_run_driver_recovers_a_nonfinite_member(E, tmp_path):
+    """The run driver on the library: a member made non-finite on the host
+    side (NaN written into its spectrum once, as a stand-in for a blow-up)
+    rolls the ensemble back to the last checkpoint with that member's CFL
+    number halved (ens_set_timestep) and the run completes; the other members
+    end exactly where an undisturbed run ends."""
+    from paper_2506_23712_gb300 import runner
+    ms = members(E)
+
+    class Injecting:
+        def __init__(self, ens):
+            self.ens, self.members, self.done = ens, ens.members, False
+
+        def step(self, n):
+            self.ens.step(n)
+            if not self.done and self.ens.diagnostics()[0]["steps"] >= 6:
+                f = self.ens.field(1)
+                f[0, 1, 1, 1] = np.nan
+                self.ens.set_field(1, f)
+                self.ens.step(1)          # the NaN spreads through the step
+                self.done = True
+
+        def __getattr__(self, k):
+            return getattr(self.ens, k)
+
+    a = E.Ensemble(ms, hist=hist(E))
+    rep = runner.run(Injecting(a), 12, stats_every=3, checkpoint_every=3,
+                     checkpoint_path=str(tmp_path / "run.ckpt"), log_path=str(tmp_path / "run.jsonl"))
+    assert rep.failed == [] and rep.rollbacks == 1 and rep.retried == {1: 1} and rep.steps_done == 12
+    d = a.diagnostics()
+    assert all(x["flags"] == 0 for x in d)
+    b = E.Ensemble(ms, hist=hist(E))
+    b.step(12)
+    for i in (0, 2):
+        assert np.array_equal(a.field(i), b.field(i)), i
+    a.close()
+    b.close()
