@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-surrogate", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep the default pass variants")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-resolution / 512^3 measurements")
+    p.add_argument("--set-tuning", default="", help="KEY=VAL,... applied to every grid-size group after "
+                   "autotuning (for profiling a given variant), e.g. fx_split=1")
     return p.parse_args()
 
 
@@ -425,6 +427,14 @@ def main():
     # pass variants picked by the library's autotuner on these members (the
     # member state is restored afterwards; untimed)
     tuning = None if args.no_tune else ens.autotune(steps=2)
+    if args.set_tuning:
+        t = ens.tuning()
+        for kv in args.set_tuning.split(","):
+            k, v = kv.split("=")
+            for g in t["groups"]:
+                g[k.strip()] = int(v)
+        ens.set_tuning(t)
+        tuning = dict(ens.tuning(), forced=args.set_tuning)
     kps = E.ens_kernels_per_step(ens.ctx)
 
     def barrier():
