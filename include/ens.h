@@ -202,7 +202,10 @@ ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
  *   z_variant       0: persistent TMA-pipelined z pass with z_ctas_per_sm
  *                   CTAs per SM (1 .. the kernel's occupancy limit),
  *                   1: one CTA per group of rows (z_ctas_per_sm unused
- *                   but kept, and checked, for a switch back to 0).
+ *                   but kept, and checked, for a switch back to 0),
+ *                   2 (N = 256 only): the persistent pass with a two-pass
+ *                   16 x 16 warp plan (one shared-memory exchange per line
+ *                   instead of two; z_ctas_per_sm up to its own limit).
  * Every variant computes the same transforms; the FP64 energy sums of the
  * update pass are accumulated over tile_x-dependent CTA partials, so
  * changing tile_x changes their rounding order (fields agree to FP32

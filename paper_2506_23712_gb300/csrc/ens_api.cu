@@ -993,11 +993,11 @@ ens_status tuning_valid(const ens_ctx *ctx, const ens_tuning *t, std::string &wh
             why = "fx_split must be 0 or 1";
             return ENS_EINVAL;
         }
-        if (o.z_variant != 0 && o.z_variant != 1) {
-            why = "z_variant must be 0 or 1";
+        if (o.z_variant < 0 || o.z_variant > 2 || (o.z_variant == 2 && !zplan_variant_available(N))) {
+            why = "z_variant must be 0, 1, or 2 for N = 256";
             return ENS_EINVAL;
         }
-        const int occ = znl_ctas_per_sm(N);
+        const int occ = znl_ctas_per_sm(N, o.z_variant == 2 ? 1 : 0);
         if (o.z_ctas_per_sm < 1 || o.z_ctas_per_sm > occ) {
             why = "z_ctas_per_sm must lie in [1, " + std::to_string(occ) + "] for N = " + std::to_string(N);
             return ENS_EINVAL;
@@ -1190,6 +1190,16 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
             cand.group[gi].z_variant = 0;
             cand.group[gi].z_ctas_per_sm = c;
             if (!consider(cand)) break;
+        }
+        if (zplan_variant_available(N)) {
+            const int occ2 = znl_ctas_per_sm(N, 1);
+            for (int c = 1; rs == ENS_OK && c <= occ2; ++c) {
+                cand = best;
+                if (cand.group[gi].z_variant == 2 && cand.group[gi].z_ctas_per_sm == c) continue;
+                cand.group[gi].z_variant = 2;
+                cand.group[gi].z_ctas_per_sm = c;
+                if (!consider(cand)) break;
+            }
         }
         if (rs == ENS_OK && best.group[gi].z_variant != 1) {
             cand = best;

@@ -290,9 +290,17 @@ template <> struct WPlan<256> { static constexpr int P = 32, NP = 3, R0 = 8,  R1
 template <> struct WPlan<384> { static constexpr int P = 32, NP = 4, R0 = 4,  R1 = 4, R2 = 6, R3 = 4; };
 template <> struct WPlan<512> { static constexpr int P = 32, NP = 3, R0 = 16, R1 = 2, R2 = 16, R3 = 1; };
 
-template <int N>
+// Alternative warp-local plans offered to the autotuner for the z pass:
+// VAR 1 at N = 256 is a two-pass 16 x 16 plan on 16 threads per line (one
+// exchange per line transform instead of two; twice the values per thread).
+template <int N, int VAR>
+struct WPlanV : WPlan<N> {};
+template <> struct WPlanV<256, 1> { static constexpr int P = 16, NP = 2, R0 = 16, R1 = 16, R2 = 1, R3 = 1; };
+__host__ __device__ constexpr bool has_zplan_variant(int N) { return N == 256; }
+
+template <int N, int VAR = 0>
 struct WPlanInfo {
-    using PL = WPlan<N>;
+    using PL = WPlanV<N, VAR>;
     static constexpr int P = PL::P;
     static constexpr int V = N / P;
     static constexpr int NP = PL::NP;
@@ -363,9 +371,9 @@ __device__ __forceinline__ void pass_regs_tw(float2 *v, const PassTw<N, R, Ns, P
     }
 }
 
-template <int N>
+template <int N, int VAR = 0>
 struct WarpTw {
-    using PI = WPlanInfo<N>;
+    using PI = WPlanInfo<N, VAR>;
     static constexpr int P = PI::P, R0 = PI::R0, R1 = PI::R1, R2 = PI::R2, R3 = PI::R3;
     PassTw<N, R1, R0, P> t1;
     PassTw<N, (PI::NP >= 3 ? R2 : 2), R0 * R1, P> t2;
@@ -379,10 +387,10 @@ struct WarpTw {
 };
 
 // Warp-local line transform with register twiddles.
-template <int N, bool FWD, class At>
-__device__ __forceinline__ void fft_line_warp_tw(float2 *v, int p, const WarpTw<N> &T, At at)
+template <int N, bool FWD, int VAR = 0, class At>
+__device__ __forceinline__ void fft_line_warp_tw(float2 *v, int p, const WarpTw<N, VAR> &T, At at)
 {
-    using PI = WPlanInfo<N>;
+    using PI = WPlanInfo<N, VAR>;
     constexpr int P = PI::P;
     constexpr int R0 = PI::R0, R1 = PI::R1, R2 = PI::R2, R3 = PI::R3;
     pass_regs<N, R0, 1, P, FWD>(v, p, nullptr);

@@ -334,11 +334,13 @@ cudaError_t prepare_kernels(int N, int nq, int nt, int ng)
 
 bool plan_variant_available(int N) { return has_plan_variant(N); }
 
-int znl_ctas_per_sm(int N)
+int znl_ctas_per_sm(int N, int var)
 {
     const SizedOps *o = sized_ops(N);
-    return o ? o->znl_ctas_per_sm() : 0;
+    return o ? o->znl_ctas_per_sm(var) : 0;
 }
+
+bool zplan_variant_available(int N) { return has_zplan_variant(N); }
 
 void launch_pass(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last, int arg,
                  cudaStream_t s)

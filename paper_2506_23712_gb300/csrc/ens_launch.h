@@ -28,13 +28,14 @@ bool supported_n(int N);
 int plan_threads(int N);
 int stats_blocks(int N);
 cudaError_t prepare_kernels(int N, int nq, int nt, int ng);
-int znl_ctas_per_sm(int N);   // resident CTAs per SM of the persistent z pass (0 on error)
+int znl_ctas_per_sm(int N, int var = 0);   // resident CTAs per SM of the persistent z pass (0 on error)
+bool zplan_variant_available(int N);       // the persistent z pass has a second warp plan for this size
 bool plan_variant_available(int N);   // the x passes have a second FFT plan for this size
 
 // Pass launchers of one grid size (ens_sized.cu, one translation unit per N).
 struct SizedOps {
     cudaError_t (*prepare)(int nq, int nt, int ng);
-    int (*znl_ctas_per_sm)();
+    int (*znl_ctas_per_sm)(int var);
     void (*launch)(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last,
                    int arg, cudaStream_t s);
 };
@@ -59,7 +60,8 @@ const SizedOps *sized_ops(int N);   // nullptr for an unsupported size
 //   FX: mode 0 RK update, 1 right-hand side, 2 initial field, 3 plain transform
 //   ZSTAT: statistics
 // The stage passes (IX mode 0, IY, FY, FX mode 0, Z mode 0) take their
-// variant from the group's tuning in g (tile_x, tile_y, z_mode, z_ctas).
+// variant from the group's tuning in g (tile_x, tile_y, plan_x, fx_split,
+// z_mode: 0 persistent, 1 row groups, 2 persistent with the second warp plan).
 void launch_pass(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last, int arg,
                  cudaStream_t s);
 void launch_state_sums(const Geo &g, MemberDev *md, cudaStream_t s);

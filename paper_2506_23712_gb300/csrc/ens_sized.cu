@@ -30,6 +30,11 @@ template <int M>
 cudaError_t prepare_variants()
 {
     cudaError_t e = cudaSuccess;
+    if constexpr (has_zplan_variant(M)) {
+        if (ZCfg<M, 1>::smem_bytes() > 48 * 1024)
+            e = cudaFuncSetAttribute(k_znl<M, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ZCfg<M, 1>::smem_bytes());
+    }
     if constexpr (has_plan_variant(M)) {
         auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
         chk(allow_smem(k_inv_x<M, 0, 16, 1>, smem_x<M, 16>()));
@@ -67,12 +72,36 @@ cudaError_t prepare(int nq, int nt, int ng)
     return e;
 }
 
-int znl_per_sm()
+template <int M>
+int znl_per_sm_t(int var)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_znl<N>, 256, ZCfg<N>::smem_bytes()) != cudaSuccess)
+    if constexpr (has_zplan_variant(M)) {
+        if (var == 1) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_znl<M, 1>, 256, ZCfg<M, 1>::smem_bytes()) !=
+                cudaSuccess)
+                return 0;
+            return per_sm;
+        }
+    }
+    if (var != 0) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_znl<M>, 256, ZCfg<M>::smem_bytes()) != cudaSuccess)
         return 0;
     return per_sm;
+}
+
+int znl_per_sm(int var) { return znl_per_sm_t<N>(var); }
+
+template <int M>
+void launch_znl_t(const Geo &g, MemberDev *md, int stage, cudaStream_t s)
+{
+    if constexpr (has_zplan_variant(M)) {
+        if (g.z_mode == 2) {
+            k_znl<M, 1><<<g.z_ctas, 256, ZCfg<M, 1>::smem_bytes(), s>>>(g, md, stage);
+            return;
+        }
+    }
+    k_znl<M><<<g.z_ctas, 256, ZCfg<M>::smem_bytes(), s>>>(g, md, stage);
 }
 
 template <int T, int VAR = 0>
@@ -151,7 +180,7 @@ void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, 
         switch (mode) {
         case 0:
             if (g.z_mode == 1) k_z<N, 0><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage);
-            else k_znl<N><<<g.z_ctas, 256, ZCfg<N>::smem_bytes(), s>>>(g, md, stage);
+            else launch_znl_t<N>(g, md, stage, s);
             break;
         case 1: k_z<N, 1><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;
         case 3: k_z<N, 3><<<grid, TZ, smem_rows<N>(), s>>>(g, md, stage); break;

@@ -21,15 +21,22 @@
 
 namespace ens {
 
-template <int N>
+template <int N, int VAR = 0>
 struct ZCfg {
-    using PI = WPlanInfo<N>;
+    using PI = WPlanInfo<N, VAR>;
     static constexpr int P = PI::P, V = PI::V, LPW = 32 / P;
     static constexpr int WPB = 8;                          // warps per CTA
     static constexpr int NZ = kc_of_n(N) + 1;
     static constexpr int NZ2 = (NZ + 1) / 2 * 2;           // copied row length (16-byte multiple)
     static constexpr int STAGE = LPW * 6 * NZ2;            // float2 per warp buffer
-    static constexpr int SROW = RowCfg<N>::SROW;
+    // the default plans use the rows of RowCfg (XOR-swizzled at the large
+    // sizes); the 16 x 16 variant an additive pad of one slot per 16
+    static constexpr int SROW = VAR == 0 ? RowCfg<N>::SROW : N + N / 16 + N / 32 + 1;
+    static __device__ __forceinline__ float2 *slot(float2 *buf, int r, int pos)
+    {
+        if constexpr (VAR == 0) return row_slot<N>(buf, r, pos);
+        else return &buf[r * SROW + pos + (pos >> 4)];
+    }
     static constexpr size_t smem_bytes()
     {
         return sizeof(float2) * (size_t)N + sizeof(uint64_t) * 2 * WPB + sizeof(float2) * (size_t)WPB * 2 * STAGE +
@@ -39,14 +46,14 @@ struct ZCfg {
 
 // forward transform of two real rows with register twiddles, then the half
 // spectra of both rows (kz < NZ) to dstA / dstB (dstB null: one real row)
-template <int N>
-__device__ __forceinline__ void forward_pair_store_tw(float2 *v, int p, int r, const WarpTw<N> &T, float2 *buf,
+template <int N, int VAR>
+__device__ __forceinline__ void forward_pair_store_tw(float2 *v, int p, int r, const WarpTw<N, VAR> &T, float2 *buf,
                                                       float2 *dstA, float2 *dstB, int NZ)
 {
-    using PI = WPlanInfo<N>;
+    using PI = WPlanInfo<N, VAR>;
     constexpr int V = PI::V, P = PI::P;
-    auto at = [&](int pos) { return row_slot<N>(buf, r, pos); };
-    fft_line_warp_tw<N, true>(v, p, T, at);
+    auto at = [&](int pos) { return ZCfg<N, VAR>::slot(buf, r, pos); };
+    fft_line_warp_tw<N, true, VAR>(v, p, T, at);
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < V; ++i) *at(PI::out_pos(p, i)) = v[i];
@@ -60,12 +67,12 @@ __device__ __forceinline__ void forward_pair_store_tw(float2 *v, int p, int r, c
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(256, ZCfg<N>::smem_bytes() <= 110 * 1024 ? 2 : 1)
+template <int N, int VAR = 0>
+__global__ void __launch_bounds__(256, VAR == 0 && ZCfg<N, VAR>::smem_bytes() <= 110 * 1024 ? 2 : 1)
 k_znl(Geo g, MemberDev *md, int stage_idx)
 {
-    using C = ZCfg<N>;
-    using PI = WPlanInfo<N>;
+    using C = ZCfg<N, VAR>;
+    using PI = WPlanInfo<N, VAR>;
     constexpr int P = C::P, V = C::V, LPW = C::LPW, NZ2 = C::NZ2;
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *tw = reinterpret_cast<float2 *>(smraw);
@@ -83,7 +90,7 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         fence_mbar_init();
     }
     load_twiddles(tw, g.tw, N);   // block barrier also publishes the barrier init
-    WarpTw<N> TW;                 // this lane's inter-pass twiddles, for every row it transforms
+    WarpTw<N, VAR> TW;            // this lane's inter-pass twiddles, for every row it transforms
     TW.init(p, tw);
 
     const long long G = (long long)N * N / LPW;   // row groups per member
@@ -105,7 +112,7 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
     };
     if (lane == 0 && grp < T) issue(grp, 0);
 
-    auto at = [&](int pos) { return row_slot<N>(rowbuf, line, pos); };
+    auto at = [&](int pos) { return C::slot(rowbuf, line, pos); };
     float umax = 0.f;
     bool finite = true;
     long long cur_m = grp < T ? grp / G : 0;
@@ -154,9 +161,9 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
             bb[i] = pair_at(X + 2 * NZ2, X + 3 * NZ2, pos, N, Dims<N>::KC);
             cc[i] = pair_at(X + 4 * NZ2, X + 5 * NZ2, pos, N, Dims<N>::KC);
         }
-        fft_line_warp_tw<N, false>(a, p, TW, at);
-        fft_line_warp_tw<N, false>(bb, p, TW, at);
-        fft_line_warp_tw<N, false>(cc, p, TW, at);
+        fft_line_warp_tw<N, false, VAR>(a, p, TW, at);
+        fft_line_warp_tw<N, false, VAR>(bb, p, TW, at);
+        fft_line_warp_tw<N, false, VAR>(cc, p, TW, at);
         // a = ux + i uy, bb = uz + i wx, cc = wy + i wz at positions out_pos
 #pragma unroll
         for (int i = 0; i < V; ++i) {
@@ -169,11 +176,11 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         }
         static_assert(PI::matched, "first and last radix must agree");
         float2 *Bout = g.B + m * kFields * Dims<N>::SB + rho * Dims<N>::NZP;
-        forward_pair_store_tw<N>(w0, p, line, TW, rowbuf, Bout, Bout + Dims<N>::SB, Dims<N>::NZ);
+        forward_pair_store_tw<N, VAR>(w0, p, line, TW, rowbuf, Bout, Bout + Dims<N>::SB, Dims<N>::NZ);
         if (pend) {
 #pragma unroll
             for (int i = 0; i < V; ++i) w0[i] = make_float2(nzp[i], nz[i]);
-            forward_pair_store_tw<N>(w0, p, line, TW, rowbuf, pend, Bout + 2 * Dims<N>::SB, Dims<N>::NZ);
+            forward_pair_store_tw<N, VAR>(w0, p, line, TW, rowbuf, pend, Bout + 2 * Dims<N>::SB, Dims<N>::NZ);
             pend = nullptr;
         } else {
 #pragma unroll
@@ -186,7 +193,7 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         float2 w[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) w[i] = make_float2(nzp[i], 0.f);
-        forward_pair_store_tw<N>(w, p, line, TW, rowbuf, pend, nullptr, Dims<N>::NZ);
+        forward_pair_store_tw<N, VAR>(w, p, line, TW, rowbuf, pend, nullptr, Dims<N>::NZ);
     }
     if (grp > (long long)blockIdx.x * C::WPB + warp || timed_out) flush(cur_m);
     if (timed_out) {

@@ -132,10 +132,40 @@ def test_x_plan_variant_matches_oracle(E):
     ens.close()
 
 
+def test_z_plan_variant_matches_oracle(E):
+    """The persistent z pass with the two-pass 16 x 16 warp plan (N = 256,
+    z_variant 2) against the oracle after one RK3 step, and against the
+    default plan."""
+    m = E.Member(N=256, nu=0.005, lam=0.4, k_lo=6, k_hi=8, dt=-1, cfl=0.2, rk_order=3, seed=2027)
+    om = oracle_member(m)
+    ref = O.initial_field(om)
+    O.step(om, ref, 1)
+    base = E.Ensemble([m])
+    base.step(1)
+    f0 = base.field(0)
+    base.close()
+    ens = E.Ensemble([m])
+    t = ens.tuning()
+    t["groups"][0].update(z_variant=2, z_ctas_per_sm=1)
+    ens.set_tuning(t)
+    ens.step(1)
+    f = ens.field(0)
+    assert rel(f, ref) < 1e-5
+    assert rel(f, f0) < 1e-6
+    ens.close()
+    # other sizes refuse it
+    ens = E.Ensemble(members(E))
+    t = ens.tuning()
+    t["groups"][1]["z_variant"] = 2
+    with pytest.raises(E.EnsError):
+        ens.set_tuning(t)
+    ens.close()
+
+
 def test_invalid_tuning_rejected_and_context_usable(E):
     ens = E.Ensemble(members(E))
     good = ens.tuning()
-    for bad in ({"tile_x": 4}, {"tile_y": 32}, {"z_variant": 2}, {"z_ctas_per_sm": 0}, {"z_ctas_per_sm": 99},
+    for bad in ({"tile_x": 4}, {"tile_y": 32}, {"z_variant": 3}, {"z_ctas_per_sm": 0}, {"z_ctas_per_sm": 99},
                 {"N": 128}):
         t = json.loads(json.dumps(good))
         t["groups"][1].update(bad)
