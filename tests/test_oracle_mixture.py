@@ -272,3 +272,41 @@ def test_rational_numeric_inversion_matches_compound_poisson(Z):
     grid = np.linspace(-30, 30, 65536, endpoint=False)
     P = M.lambda_pdf_from_K(lambda t: (t - zeta(3 * t)) * Z, grid, atom)
     assert abs(P[grid > Z + 0.05].sum() * dl) < max(2e-3 * J * dl, 1e-12)
+
+
+def _power_law_members(lams, rho, c):
+    """Member moments of an exactly scaling ensemble (Sec. III, Eq.
+    scaling_equation_2 at fixed nu and L): <A^m>_lambda ~ exp(lambda (m +
+    rho_m) / 3), negative for m = 3 (negative skewness); all nine components
+    alike.  Layout of the 48 moment sums with one point per member."""
+    mom = np.zeros((len(lams), 48))
+    for j, m in enumerate((2, 3, 4, 6)):
+        v = np.exp(np.asarray(lams) * (m + rho[m]) / 3.0) * (-1.0 if m == 3 else 1.0)
+        for comp in range(9):
+            mom[:, 4 * comp + j] = v
+    return mom
+
+
+def test_mixture_ratios_follow_nelkin_exponents():
+    """Mixing exactly scaling members with P(lambda; Z) gives skewness,
+    flatness and hyper-flatness that scale with R_lambda ~ exp(2Z/3) as the
+    Nelkin relation predicts (Sec. III, Eq. nelkin_rhom; Sec. VII):
+    d ln|S| / d ln R = 2 rho3 - 3 rho2, d ln F / d ln R = 2 rho4 - 4 rho2,
+    d ln H / d ln R = 2 rho6 - 6 rho2."""
+    c = 0.023
+    zeta = lambda p: M.zeta_quadratic(p, c)
+    rho = {m: M.nelkin_rho(m, zeta) for m in (2, 3, 4, 6)}
+    lams = np.linspace(-9.0, 12.0, 2048)
+    mom = _power_law_members(lams, rho, c)
+    npts = np.ones(len(lams))
+    out = {}
+    for Z in (1.0, 3.0):
+        w, _ = M.member_weights(lams, "gauss_paper", c=c, Z=Z, renormalize=False)
+        out[Z] = M.gradient_moment_ratios(M.mix_moments(mom, npts, w))
+    dlnR = 2.0 / 3.0 * (3.0 - 1.0)
+    slope = lambda k: (math.log(abs(out[3.0][k])) - math.log(abs(out[1.0][k]))) / dlnR
+    S, F, H = M.ratio_exponents(zeta)
+    assert slope("S_long") == pytest.approx(S, abs=2e-3)
+    assert slope("F_long") == pytest.approx(F, abs=2e-3)
+    assert slope("H_long") == pytest.approx(H, abs=2e-3)
+    assert slope("F_trans") == pytest.approx(F, abs=2e-3)
