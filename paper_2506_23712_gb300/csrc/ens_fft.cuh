@@ -386,6 +386,78 @@ struct WarpTw {
     }
 };
 
+// Padded exchange layouts of the power-of-two warp-local plans (WPlan<N>).
+// Exchange s (after pass s) puts line position pos at slot
+// pos + (pos >> A_s) * D_s of the line's shared row.  Every position an
+// exchange touches is a per-lane part plus a compile-time part (butterfly
+// index, radix slot) with disjoint bits, and the map is additive over such
+// parts, so each access is one per-lane base plus an immediate offset: no
+// per-access address arithmetic.  A_s, D_s and the row stride SROW are the
+// bank-conflict-free choices printed by swizzle_search.py (half-warp model
+// of 8-byte requests).
+template <int N>
+struct WPad {
+    static constexpr bool on = false;
+    static constexpr int SROW = 0, A0 = 0, D0 = 0, A1 = 0, D1 = 0;
+};
+template <> struct WPad<16>  { static constexpr bool on = true; static constexpr int SROW = 20,  A0 = 2, D0 = 1, A1 = 0, D1 = 0; };
+template <> struct WPad<32>  { static constexpr bool on = true; static constexpr int SROW = 40,  A0 = 3, D0 = 1, A1 = 1, D1 = 0; };
+template <> struct WPad<64>  { static constexpr bool on = true; static constexpr int SROW = 72,  A0 = 3, D0 = 1, A1 = 0, D1 = 0; };
+template <> struct WPad<128> { static constexpr bool on = true; static constexpr int SROW = 184, A0 = 4, D0 = 1, A1 = 4, D1 = 8; };
+template <> struct WPad<256> { static constexpr bool on = true; static constexpr int SROW = 312, A0 = 4, D0 = 1, A1 = 5, D1 = 8; };
+template <> struct WPad<512> { static constexpr bool on = true; static constexpr int SROW = 543, A0 = 4, D0 = 1, A1 = 1, D1 = 0; };
+
+template <int A, int D>
+__host__ __device__ constexpr int pad_slot(int x)
+{
+    return x + (x >> A) * D;
+}
+
+template <int N, int R, int Ns, int Rn, int P, int A, int D>
+__device__ __forceinline__ void exchange_warp_pad(float2 *v, int p, float2 *row)
+{
+    static_assert(P % Ns == 0 || Ns % P == 0, "lane and butterfly parts of a position must not overlap");
+    constexpr int B = N / (R * P);
+    constexpr int Bn = N / (Rn * P);
+    // store: position (j / Ns) Ns R + (j mod Ns) + t Ns, j = p + b P
+    float2 *st = row + pad_slot<A, D>(P % Ns == 0 ? (p / Ns) * Ns * R + p % Ns : p);
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int c = P % Ns == 0 ? b * P * R + t * Ns : (b * P / Ns) * Ns * R + (b * P) % Ns + t * Ns;
+            st[pad_slot<A, D>(c)] = v[b * R + t];
+        }
+    }
+    __syncwarp();
+    // load: position p + b P + t N / Rn
+    const float2 *ld = row + pad_slot<A, D>(p);
+#pragma unroll
+    for (int b = 0; b < Bn; ++b) {
+#pragma unroll
+        for (int t = 0; t < Rn; ++t) v[b * Rn + t] = ld[pad_slot<A, D>(b * P + t * (N / Rn))];
+    }
+}
+
+// Line transform of the default warp plan through the padded layouts; row
+// is this line's shared row (WPad<N>::SROW slots).
+template <int N, bool FWD>
+__device__ __forceinline__ void fft_line_warp_pad(float2 *v, int p, const WarpTw<N, 0> &T, float2 *row)
+{
+    using PI = WPlanInfo<N, 0>;
+    using PD = WPad<N>;
+    static_assert(PD::on && PI::NP <= 3, "padded layouts exist for the power-of-two plans");
+    constexpr int P = PI::P, R0 = PI::R0, R1 = PI::R1, R2 = PI::R2;
+    pass_regs<N, R0, 1, P, FWD>(v, p, nullptr);
+    exchange_warp_pad<N, R0, 1, R1, P, PD::A0, PD::D0>(v, p, row);
+    pass_regs_tw<N, R1, R0, P, FWD>(v, T.t1);
+    if constexpr (PI::NP == 3) {
+        exchange_warp_pad<N, R1, R0, R2, P, PD::A1, PD::D1>(v, p, row);
+        pass_regs_tw<N, R2, R0 * R1, P, FWD>(v, T.t2);
+    }
+}
+
 // Warp-local line transform with register twiddles.
 template <int N, bool FWD, int VAR = 0, class At>
 __device__ __forceinline__ void fft_line_warp_tw(float2 *v, int p, const WarpTw<N, VAR> &T, At at)

@@ -29,9 +29,11 @@ struct ZCfg {
     static constexpr int NZ = kc_of_n(N) + 1;
     static constexpr int NZ2 = (NZ + 1) / 2 * 2;           // copied row length (16-byte multiple)
     static constexpr int STAGE = LPW * 6 * NZ2;            // float2 per warp buffer
-    // the default plans use the rows of RowCfg (XOR-swizzled at the large
-    // sizes); the 16 x 16 variant an additive pad of one slot per 16
-    static constexpr int SROW = VAR == 0 ? RowCfg<N>::SROW : N + N / 16 + N / 32 + 1;
+    // the non-power-of-two default plans use the rows of RowCfg
+    // (XOR-swizzled); the 16 x 16 variant an additive pad of one slot per 16
+    // the power-of-two default plans use the per-exchange padded layouts
+    static constexpr bool PAD = VAR == 0 && WPad<N>::on;
+    static constexpr int SROW = PAD ? WPad<N>::SROW : VAR == 0 ? RowCfg<N>::SROW : N + N / 16 + N / 32 + 1;
     static __device__ __forceinline__ float2 *slot(float2 *buf, int r, int pos)
     {
         if constexpr (VAR == 0) return row_slot<N>(buf, r, pos);
@@ -64,6 +66,64 @@ __device__ __forceinline__ void forward_pair_store_tw(float2 *v, int p, int r, c
         // Xa = (Z_k + conj Z_{N-k}) / 2 ; Xb = (Z_k - conj Z_{N-k}) / (2i)
         dstA[k] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y + w.y));
         if (dstB) dstB[k] = make_float2(0.5f * (z.y - w.y), -0.5f * (z.x - w.x));
+    }
+}
+
+// Slots of the first (inverse) pass of a Hermitian pair line, classified at
+// compile time: lane 0's position c of slot I and the P positions after it
+// lie all in the zero band (KC < k < N - KC), all in the stored half
+// spectrum (0 < k <= KC), all in its mirror (k >= N - KC), or straddle a
+// boundary (checked per lane).
+template <int N, int VAR, int I>
+struct PairSlots {
+    static __device__ __forceinline__ void load(float2 *v, const float2 *Xa, const float2 *Xb, int p)
+    {
+        using PI = WPlanInfo<N, VAR>;
+        constexpr int P = PI::P, KC = Dims<N>::KC;
+        if constexpr (I < PI::V) {
+            constexpr int c = (I / PI::R0) * P + (I % PI::R0) * (N / PI::R0);
+            if constexpr (c > KC && c + P - 1 < N - KC) {
+                v[I] = make_float2(0.f, 0.f);
+            } else if constexpr (c >= 1 && c + P - 1 <= KC) {
+                const float2 a = Xa[c + p], b = Xb[c + p];
+                v[I] = make_float2(a.x - b.y, a.y + b.x);
+            } else if constexpr (c >= N - KC) {
+                const float2 a = Xa[N - c - p], b = Xb[N - c - p];   // conj(a) + i conj(b)
+                v[I] = make_float2(a.x + b.y, b.x - a.y);
+            } else {
+                v[I] = pair_at(Xa, Xb, c + p, N, KC);
+            }
+            PairSlots<N, VAR, I + 1>::load(v, Xa, Xb, p);
+        }
+    }
+};
+
+// Forward transform of two real rows (padded layouts), then the half
+// spectra of both rows (kz < NZ) to dstA / dstB (dstB null: one real row).
+// The last pass leaves position p + P i in slot i of lane p, so Z_{N-k}
+// for this lane's k = p + P i sits in lane (P - p) mod P (slot V - 1 - i,
+// or V - i for lane 0) and comes over by shuffle.
+template <int N>
+__device__ __forceinline__ void forward_pair_store_shfl(float2 *v, int p, int line, const WarpTw<N, 0> &T,
+                                                        float2 *row, float2 *dstA, float2 *dstB)
+{
+    using PI = WPlanInfo<N, 0>;
+    constexpr int P = PI::P, V = PI::V, NZ = Dims<N>::NZ;
+    static_assert(PI::RL == V, "the last pass must hold one butterfly per lane");
+    static_assert((NZ + P - 1) / P <= V, "unpacking rounds exceed the slots");
+    fft_line_warp_pad<N, true>(v, p, T, row);
+    const int src = line * P + ((P - p) & (P - 1));
+#pragma unroll
+    for (int i = 0; i < (NZ + P - 1) / P; ++i) {
+        const float2 send = p == 0 ? v[(V - i) % V] : v[V - 1 - i];
+        const float2 z = v[i];
+        const float2 w = make_float2(__shfl_sync(0xffffffffu, send.x, src), -__shfl_sync(0xffffffffu, send.y, src));
+        const int k = p + i * P;
+        if (k < NZ) {
+            // Xa = (Z_k + conj Z_{N-k}) / 2 ; Xb = (Z_k - conj Z_{N-k}) / (2i)
+            dstA[k] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y + w.y));
+            if (dstB) dstB[k] = make_float2(0.5f * (z.y - w.y), -0.5f * (z.x - w.x));
+        }
     }
 }
 
@@ -113,6 +173,11 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
     if (lane == 0 && grp < T) issue(grp, 0);
 
     auto at = [&](int pos) { return C::slot(rowbuf, line, pos); };
+    float2 *myrow = rowbuf + line * C::SROW;   // this lane's line (padded layouts)
+    auto fwd_pair = [&](float2 *v, float2 *dA, float2 *dB) {
+        if constexpr (C::PAD) forward_pair_store_shfl<N>(v, p, line, TW, myrow, dA, dB);
+        else forward_pair_store_tw<N, VAR>(v, p, line, TW, rowbuf, dA, dB, Dims<N>::NZ);
+    };
     float umax = 0.f;
     bool finite = true;
     long long cur_m = grp < T ? grp / G : 0;
@@ -154,16 +219,18 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         const float2 *X = st + b * C::STAGE + line * 6 * NZ2;
         float2 a[V], bb[V], cc[V], w0[V];
         float nz[V];
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const int pos = PI::in_pos(p, i);
-            a[i] = pair_at(X, X + NZ2, pos, N, Dims<N>::KC);
-            bb[i] = pair_at(X + 2 * NZ2, X + 3 * NZ2, pos, N, Dims<N>::KC);
-            cc[i] = pair_at(X + 4 * NZ2, X + 5 * NZ2, pos, N, Dims<N>::KC);
+        PairSlots<N, VAR, 0>::load(a, X, X + NZ2, p);
+        PairSlots<N, VAR, 0>::load(bb, X + 2 * NZ2, X + 3 * NZ2, p);
+        PairSlots<N, VAR, 0>::load(cc, X + 4 * NZ2, X + 5 * NZ2, p);
+        if constexpr (C::PAD) {
+            fft_line_warp_pad<N, false>(a, p, TW, myrow);
+            fft_line_warp_pad<N, false>(bb, p, TW, myrow);
+            fft_line_warp_pad<N, false>(cc, p, TW, myrow);
+        } else {
+            fft_line_warp_tw<N, false, VAR>(a, p, TW, at);
+            fft_line_warp_tw<N, false, VAR>(bb, p, TW, at);
+            fft_line_warp_tw<N, false, VAR>(cc, p, TW, at);
         }
-        fft_line_warp_tw<N, false, VAR>(a, p, TW, at);
-        fft_line_warp_tw<N, false, VAR>(bb, p, TW, at);
-        fft_line_warp_tw<N, false, VAR>(cc, p, TW, at);
         // a = ux + i uy, bb = uz + i wx, cc = wy + i wz at positions out_pos
 #pragma unroll
         for (int i = 0; i < V; ++i) {
@@ -176,11 +243,11 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         }
         static_assert(PI::matched, "first and last radix must agree");
         float2 *Bout = g.B + m * kFields * Dims<N>::SB + rho * Dims<N>::NZP;
-        forward_pair_store_tw<N, VAR>(w0, p, line, TW, rowbuf, Bout, Bout + Dims<N>::SB, Dims<N>::NZ);
+        fwd_pair(w0, Bout, Bout + Dims<N>::SB);
         if (pend) {
 #pragma unroll
             for (int i = 0; i < V; ++i) w0[i] = make_float2(nzp[i], nz[i]);
-            forward_pair_store_tw<N, VAR>(w0, p, line, TW, rowbuf, pend, Bout + 2 * Dims<N>::SB, Dims<N>::NZ);
+            fwd_pair(w0, pend, Bout + 2 * Dims<N>::SB);
             pend = nullptr;
         } else {
 #pragma unroll
@@ -193,7 +260,7 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         float2 w[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) w[i] = make_float2(nzp[i], 0.f);
-        forward_pair_store_tw<N, VAR>(w, p, line, TW, rowbuf, pend, nullptr, Dims<N>::NZ);
+        fwd_pair(w, pend, nullptr);
     }
     if (grp > (long long)blockIdx.x * C::WPB + warp || timed_out) flush(cur_m);
     if (timed_out) {
