@@ -16,8 +16,15 @@ the masks:
   N = 128, 256: masks that are GF(2)-linear in the block index (exhaustive)
   N = 384, 512: one free mask per block (seeded local search)
 
+The persistent z pass uses, for the power-of-two plans, one additive
+layout per pass exchange instead (WPad in csrc/ens_fft.cuh): exchange s puts
+position pos at slot pos + (pos >> A_s) * D_s, and `pad_search` picks A_s,
+D_s and a common row stride with the fewest wavefronts over that exchange's
+store and load patterns (exhaustive over small A, D).
+
 Run: python -m paper_2506_23712_gb300.swizzle_search   (prints the packed
-64-bit tables and the wavefront counts: ideal, additive padding, swizzle).
+64-bit tables and the wavefront counts: ideal, additive padding, swizzle;
+then the per-exchange pad table).
 """
 from __future__ import annotations
 
@@ -128,6 +135,53 @@ def pack(masks):
     return lo, hi
 
 
+def exchange_patterns(N):
+    """[[per-lane (line, pos)] for every request of exchange s] for each s"""
+    P, radices = PLANS[N]
+    lpw = 32 // P
+    res = []
+    ns = 1
+    for s in range(len(radices) - 1):
+        R, Rn = radices[s], radices[s + 1]
+        pats = []
+        for b in range(N // (R * P)):
+            for t in range(R):
+                pats.append([(line, ((p + b * P) // ns) * ns * R + ((p + b * P) % ns) + t * ns)
+                             for line in range(lpw) for p in range(P)])
+        for b in range(N // (Rn * P)):
+            for t in range(Rn):
+                pats.append([(line, p + b * P + t * (N // Rn)) for line in range(lpw) for p in range(P)])
+        res.append(pats)
+        ns *= R
+    return res
+
+
+def pad_search(N):
+    """(wavefronts, row stride, [(A_s, D_s)]) of the best per-exchange pads"""
+    ex = exchange_patterns(N)
+    best = None
+    for srow in range(N, N + N // 2 + 1):
+        tot, choice = 0, []
+        for pats in ex:
+            bb = None
+            for A in range(1, 10):
+                for D in range(0, 33):
+                    f = lambda pos, A=A, D=D: pos + (pos >> A) * D
+                    if f(N - 1) + 1 > srow:
+                        continue
+                    c = sum(wavefronts([line * srow + f(pos) for line, pos in lanes]) for lanes in pats)
+                    if bb is None or (c, D, A) < bb[0]:
+                        bb = ((c, D, A), A, D)
+            if bb is None:
+                tot = None
+                break
+            tot += bb[0][0]
+            choice.append((bb[1], bb[2]))
+        if tot is not None and (best is None or tot < best[0]):
+            best = (tot, srow, choice)
+    return best
+
+
 if __name__ == "__main__":
     for N in (128, 256, 384, 512):
         pats = patterns(N)
@@ -136,3 +190,6 @@ if __name__ == "__main__":
         lo, hi = pack(masks)
         print("N=%d ideal %d padded %d swizzled %d  lo=0x%016x hi=0x%x" % (N, ideal(pats), cost(pats, f, srow), c,
                                                                          lo, hi))
+    for N in (16, 32, 64, 128, 256, 512):
+        tot, srow, choice = pad_search(N)
+        print("WPad<%d>: SROW %d, (A, D) per exchange %s, %d wavefronts" % (N, srow, choice, tot))
