@@ -71,6 +71,9 @@ __global__ void k_finish(MemberDev *md, const double *partial, int partial_block
     d.E = e;
     d.diss = s;
     d.EB = b;
+    // a non-finite value anywhere in the fields reaches every mode through
+    // the nonlinear term and the transforms, hence these sums
+    if (!isfinite(e) || !isfinite(s)) d.flags |= kFlagNonFinite;
     if (b > 0.0) {
         d.alpha = d.eps_inj / (2.0 * b);
     } else {

@@ -3,10 +3,11 @@
 // Per (y, x) row of a member: the six half spectra (u, omega) along z are
 // taken to physical space as three complex lines (two real rows per complex
 // line, Hermitian extension), the rotational nonlinear term n = u x omega is
-// formed point by point together with max|u_i| (CFL step, Sec. IV) and a
-// non-finite check, and n goes straight back along z; the dealiased half
-// spectra of n overwrite fields 0..2 of the row in buffer B (n_z of two
-// consecutive rows of a warp's stream share one forward complex line).
+// formed point by point together with max|u_i| (CFL step, Sec. IV), and n
+// goes straight back along z; the dealiased half spectra of n overwrite
+// fields 0..2 of the row in buffer B (n_z of two consecutive rows of a
+// warp's stream share one forward complex line).  Non-finite values are
+// caught downstream, in the stage's energy sums (k_finish).
 //
 // Each warp owns a stream of row groups (32/P rows per group, P threads per
 // row) and double-buffers their inputs in shared memory: one lane issues
@@ -21,6 +22,45 @@
 
 namespace ens {
 
+// Classes of the first-pass input slots of a Hermitian pair line (slot I
+// holds positions c + p, p < P, c the position of lane 0): the first slot
+// (c = 0, the kz = 0 mode sits in lane 0), all positions in the zero band
+// KC < k < N - KC, positions in [1, N - KC) read forwards from the staged
+// half spectrum, positions in (KC, N) read backwards (the mirror), or a
+// slot that needs both (checked per lane).  The staged rows are zero past
+// the copied modes, so the forward and backward reads need no checks.
+enum : int { kSlotFirst, kSlotZero, kSlotFwd, kSlotBwd, kSlotMixed };
+
+template <int N, int VAR>
+__host__ __device__ constexpr int slot_class(int i)
+{
+    using PI = WPlanInfo<N, VAR>;
+    const int P = PI::P, KC = kc_of_n(N);
+    const int c = (i / PI::R0) * P + (i % PI::R0) * (N / PI::R0);
+    if (c == 0) return P - 1 < N - KC ? kSlotFirst : kSlotMixed;
+    if (c > KC && c + P - 1 < N - KC) return kSlotZero;
+    if (c + P - 1 < N - KC) return kSlotFwd;
+    if (c > KC) return kSlotBwd;
+    return kSlotMixed;
+}
+
+// staged row pitch (float2, even): the copied modes, then zeros up to the
+// furthest padded read of a forward or backward slot
+template <int N, int VAR>
+__host__ __device__ constexpr int stage_pitch()
+{
+    using PI = WPlanInfo<N, VAR>;
+    const int P = PI::P, NZ = kc_of_n(N) + 1;
+    int need = (NZ + 1) / 2 * 2;
+    for (int i = 0; i < PI::V; ++i) {
+        const int c = (i / PI::R0) * P + (i % PI::R0) * (N / PI::R0);
+        const int k = slot_class<N, VAR>(i);
+        if ((k == kSlotFirst || k == kSlotFwd) && c + P > need) need = c + P;
+        if (k == kSlotBwd && N - c + 1 > need) need = N - c + 1;
+    }
+    return (need + 1) / 2 * 2;
+}
+
 template <int N, int VAR = 0>
 struct ZCfg {
     using PI = WPlanInfo<N, VAR>;
@@ -28,7 +68,8 @@ struct ZCfg {
     static constexpr int WPB = 8;                          // warps per CTA
     static constexpr int NZ = kc_of_n(N) + 1;
     static constexpr int NZ2 = (NZ + 1) / 2 * 2;           // copied row length (16-byte multiple)
-    static constexpr int STAGE = LPW * 6 * NZ2;            // float2 per warp buffer
+    static constexpr int PITCH = stage_pitch<N, VAR>();     // staged row pitch, zero past NZ2
+    static constexpr int STAGE = LPW * 6 * PITCH;          // float2 per warp buffer
     // the non-power-of-two default plans use the rows of RowCfg
     // (XOR-swizzled); the 16 x 16 variant an additive pad of one slot per 16
     // the power-of-two default plans use the per-exchange padded layouts
@@ -69,26 +110,36 @@ __device__ __forceinline__ void forward_pair_store_tw(float2 *v, int p, int r, c
     }
 }
 
-// Slots of the first (inverse) pass of a Hermitian pair line, classified at
-// compile time: lane 0's position c of slot I and the P positions after it
-// lie all in the zero band (KC < k < N - KC), all in the stored half
-// spectrum (0 < k <= KC), all in its mirror (k >= N - KC), or straddle a
-// boundary (checked per lane).
+// First (inverse) pass inputs of a Hermitian pair line a + i b from the
+// staged half spectra Xa, Xb (zero past the copied modes), by slot class.
+// With an odd mode count the copy carries one element past the kept modes
+// (index NZ, outside the spectrum): the one lane that reads it takes zero.
 template <int N, int VAR, int I>
 struct PairSlots {
     static __device__ __forceinline__ void load(float2 *v, const float2 *Xa, const float2 *Xb, int p)
     {
         using PI = WPlanInfo<N, VAR>;
-        constexpr int P = PI::P, KC = Dims<N>::KC;
+        constexpr int P = PI::P, KC = Dims<N>::KC, NZ = KC + 1;
+        constexpr bool odd = (NZ & 1) != 0;
         if constexpr (I < PI::V) {
             constexpr int c = (I / PI::R0) * P + (I % PI::R0) * (N / PI::R0);
-            if constexpr (c > KC && c + P - 1 < N - KC) {
+            constexpr int k = slot_class<N, VAR>(I);
+            if constexpr (k == kSlotZero) {
                 v[I] = make_float2(0.f, 0.f);
-            } else if constexpr (c >= 1 && c + P - 1 <= KC) {
-                const float2 a = Xa[c + p], b = Xb[c + p];
-                v[I] = make_float2(a.x - b.y, a.y + b.x);
-            } else if constexpr (c >= N - KC) {
-                const float2 a = Xa[N - c - p], b = Xb[N - c - p];   // conj(a) + i conj(b)
+            } else if constexpr (k == kSlotFirst || k == kSlotFwd) {
+                float2 a = Xa[c + p], b = Xb[c + p];
+                if constexpr (odd && c <= NZ && NZ < c + P) {
+                    if (p == NZ - c) a = b = make_float2(0.f, 0.f);
+                }
+                if constexpr (k == kSlotFirst)   // kz = 0: real parts only (C2R convention)
+                    v[I] = p == 0 ? make_float2(a.x, b.x) : make_float2(a.x - b.y, a.y + b.x);
+                else
+                    v[I] = make_float2(a.x - b.y, a.y + b.x);
+            } else if constexpr (k == kSlotBwd) {
+                float2 a = Xa[N - c - p], b = Xb[N - c - p];   // conj(a) + i conj(b)
+                if constexpr (odd && N - c - P < NZ && NZ <= N - c) {
+                    if (p == N - c - NZ) a = b = make_float2(0.f, 0.f);
+                }
                 v[I] = make_float2(a.x + b.y, b.x - a.y);
             } else {
                 v[I] = pair_at(Xa, Xb, c + p, N, KC);
@@ -167,9 +218,15 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         for (int l = 0; l < LPW; ++l)
 #pragma unroll
             for (int f = 0; f < 6; ++f)
-                bulk_g2s(dst + (l * 6 + f) * NZ2, src + f * Dims<N>::SB + l * Dims<N>::NZP, NZ2 * (uint32_t)sizeof(float2),
-                         &bar[b]);
+                bulk_g2s(dst + (l * 6 + f) * C::PITCH, src + f * Dims<N>::SB + l * Dims<N>::NZP,
+                         NZ2 * (uint32_t)sizeof(float2), &bar[b]);
     };
+    // zero tails of the staged rows (never written by the copies)
+    constexpr int TAIL = C::PITCH - NZ2;
+    if constexpr (TAIL > 0) {
+        for (int e = lane; e < 2 * LPW * 6 * TAIL; e += 32) st[(e / TAIL) * C::PITCH + NZ2 + e % TAIL] = make_float2(0.f, 0.f);
+        __syncwarp();
+    }
     if (lane == 0 && grp < T) issue(grp, 0);
 
     auto at = [&](int pos) { return C::slot(rowbuf, line, pos); };
@@ -179,18 +236,12 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         else forward_pair_store_tw<N, VAR>(v, p, line, TW, rowbuf, dA, dB, Dims<N>::NZ);
     };
     float umax = 0.f;
-    bool finite = true;
     long long cur_m = grp < T ? grp / G : 0;
     auto flush = [&](long long m) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-        const unsigned bad = __ballot_sync(0xffffffffu, !finite);
-        if (lane == 0) {
-            atomicMax(&md[g.first + m].umax_bits[stage_idx], __float_as_uint(umax));
-            if (bad) atomicOr(&md[g.first + m].flags, kFlagNonFinite);
-        }
+        if (lane == 0) atomicMax(&md[g.first + m].umax_bits[stage_idx], __float_as_uint(umax));
         umax = 0.f;
-        finite = true;
     };
     bool timed_out = false;
     int it = 0;
@@ -216,12 +267,13 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
             cur_m = m;
         }
         const long long rho = lg * LPW + line;
-        const float2 *X = st + b * C::STAGE + line * 6 * NZ2;
+        const float2 *X = st + b * C::STAGE + line * 6 * C::PITCH;
         float2 a[V], bb[V], cc[V], w0[V];
         float nz[V];
-        PairSlots<N, VAR, 0>::load(a, X, X + NZ2, p);
-        PairSlots<N, VAR, 0>::load(bb, X + 2 * NZ2, X + 3 * NZ2, p);
-        PairSlots<N, VAR, 0>::load(cc, X + 4 * NZ2, X + 5 * NZ2, p);
+        constexpr int R = C::PITCH;
+        PairSlots<N, VAR, 0>::load(a, X, X + R, p);
+        PairSlots<N, VAR, 0>::load(bb, X + 2 * R, X + 3 * R, p);
+        PairSlots<N, VAR, 0>::load(cc, X + 4 * R, X + 5 * R, p);
         if constexpr (C::PAD) {
             fft_line_warp_pad<N, false>(a, p, TW, myrow);
             fft_line_warp_pad<N, false>(bb, p, TW, myrow);
@@ -237,7 +289,6 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
             const float ux = a[i].x, uy = a[i].y, uz = bb[i].x;
             const float wx = bb[i].y, wy = cc[i].x, wz = cc[i].y;
             umax = fmaxf(umax, fmaxf(fabsf(ux), fmaxf(fabsf(uy), fabsf(uz))));
-            finite = finite && isfinite(ux + uy + uz + wx + wy + wz);
             w0[i] = make_float2(uy * wz - uz * wy, uz * wx - ux * wz);
             nz[i] = ux * wy - uy * wx;
         }
