@@ -56,84 +56,142 @@ k_fwd_x_fft(Geo g)
 }
 
 constexpr int kUpdThreads = 256;
-constexpr int kUpdModes = kUpdChunk / kUpdThreads;   // modes per thread
+constexpr int kUpdPairs = kUpdChunk / (2 * kUpdThreads);   // mode pairs per thread
 
 template <int N>
 constexpr int update_blocks()
 {
-    return (int)((Dims<N>::SU + (long long)kUpdThreads * kUpdModes - 1) / ((long long)kUpdThreads * kUpdModes));
+    return (int)((Dims<N>::SU + kUpdChunk - 1) / kUpdChunk);
 }
 
-// grid (update_blocks<N>(), members), block kUpdThreads
+// the update of one kept mode (Sec. IV): Leray projection of the nonlinear
+// term, band forcing, one integrating-factor RK stage; returns |u|^2 of the
+// result (both Hermitian halves counted by the caller)
+struct UpdCoef {
+    float inv_n3, dtf, alpha, nu, a, b, ha, hb;
+    int blo, bhi;
+};
+
+__device__ __forceinline__ float update_mode(const UpdCoef &c, int kx, int ky, int kz, float2 (&n)[3],
+                                             const float2 (&un)[3], const float2 (&us)[3], float2 (&out)[3],
+                                             bool &band, float &k2out)
+{
+    const float fk[3] = {(float)kx, (float)ky, (float)kz};
+    const int k2i = kx * kx + ky * ky + kz * kz;
+    const float k2 = (float)k2i;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) n[q] = cscale(n[q], c.inv_n3);
+    // Leray projection P_ij = delta_ij - k_i k_j / k^2; k = 0 held at zero
+    if (k2i == 0) {
+        n[0] = n[1] = n[2] = make_float2(0.f, 0.f);
+    } else {
+        const float inv = 1.f / k2;
+        const float dr = (fk[0] * n[0].x + fk[1] * n[1].x + fk[2] * n[2].x) * inv;
+        const float di = (fk[0] * n[0].y + fk[1] * n[1].y + fk[2] * n[2].y) * inv;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) n[q] = make_float2(n[q].x - fk[q] * dr, n[q].y - fk[q] * di);
+    }
+    band = k2i >= c.blo && k2i <= c.bhi;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (band) n[q] = make_float2(n[q].x + c.alpha * us[q].x, n[q].y + c.alpha * us[q].y);
+    const float ea = c.a != 0.f ? expf(-c.nu * k2 * c.ha * c.dtf) : 0.f;
+    const float eb = expf(-c.nu * k2 * c.hb * c.dtf);
+    float a2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float rx = us[q].x + c.dtf * n[q].x, ry = us[q].y + c.dtf * n[q].y;
+        const float ox = c.a * ea * un[q].x + c.b * eb * rx;
+        const float oy = c.a * ea * un[q].y + c.b * eb * ry;
+        out[q] = make_float2(ox, oy);
+        a2 += ox * ox + oy * oy;
+    }
+    k2out = k2;
+    return a2;
+}
+
+// grid (update_blocks<N>(), members), block kUpdThreads.  Thread t takes
+// the mode pairs (2j, 2j + 1), j = first + t + u * kUpdThreads: 16-byte
+// loads and stores, and every load of a pair issued before its arithmetic.
+// A pair never straddles a kz row (NZp is even); a mode past the kept kz
+// (odd NZ) is written as zero, a pair wholly past it is not touched.
 template <int N>
-__global__ void __launch_bounds__(kUpdThreads)
+__global__ void __launch_bounds__(kUpdThreads, 4)
 k_update(Geo g, MemberDev *md, int stage, int last_stage)
 {
+    using D = Dims<N>;
+    static_assert(D::NZP % 2 == 0 && D::SU % 2 == 0, "mode pairs must not straddle a row");
     __shared__ double scratch[(kUpdThreads / 32) * 3];
     const int m = blockIdx.y;
     const MemberDev &d = md[g.first + m];
-    const float inv_n3 = 1.0f / ((float)N * (float)N * (float)N);
-    const float dtf = (float)member_dt(d, N);
-    const float alpha = (float)d.alpha;
-    const float nu = (float)d.nu;
     const StageCoef co = stage_coef(d.rk, stage);
-    const int blo = d.band_lo2, bhi = d.band_hi2;
-    const float2 *nh = nhat_of<N>(g, m);
-    float2 *U = g.U + (long long)m * 3 * Dims<N>::SU;
-    float2 *S = g.S + (long long)m * 3 * Dims<N>::SU;
-    float2 *dst = last_stage ? U : S;
-    constexpr long long rowU = (long long)Dims<N>::NK * Dims<N>::NZP;
+    UpdCoef c;
+    c.inv_n3 = 1.0f / ((float)N * (float)N * (float)N);
+    c.dtf = (float)member_dt(d, N);
+    c.alpha = (float)d.alpha;
+    c.nu = (float)d.nu;
+    c.a = co.a;
+    c.b = co.b;
+    c.ha = co.ha;
+    c.hb = co.hb;
+    c.blo = d.band_lo2;
+    c.bhi = d.band_hi2;
+    const float4 *nh = reinterpret_cast<const float4 *>(nhat_of<N>(g, m));
+    const float4 *U = reinterpret_cast<const float4 *>(g.U + (long long)m * 3 * D::SU);
+    const float4 *S = reinterpret_cast<const float4 *>(g.S + (long long)m * 3 * D::SU);
+    float4 *dst = reinterpret_cast<float4 *>((last_stage ? g.U : g.S) + (long long)m * 3 * D::SU);
+    constexpr long long rowU = (long long)D::NK * D::NZP;
+    constexpr long long SU2 = D::SU / 2;   // pairs per component
     float se = 0.f, sd = 0.f, sb = 0.f;
-    const long long first = (long long)blockIdx.x * kUpdThreads * kUpdModes + threadIdx.x;
+    const long long first = (long long)blockIdx.x * (kUpdChunk / 2) + threadIdx.x;
 #pragma unroll
-    for (int u = 0; u < kUpdModes; ++u) {
-        const long long mi = first + (long long)u * kUpdThreads;
-        if (mi >= Dims<N>::SU) break;
+    for (int u = 0; u < kUpdPairs; ++u) {
+        const long long j = first + (long long)u * kUpdThreads;
+        const long long mi = 2 * j;
         const int ix = (int)(mi / rowU);
         const int rem = (int)(mi % rowU);
-        const int iy = rem / Dims<N>::NZP, kz = rem % Dims<N>::NZP;
-        if (kz >= Dims<N>::NZ) continue;
-        const int kx = ix <= Dims<N>::KC ? ix : ix - Dims<N>::NK;
-        const int ky = iy <= Dims<N>::KC ? iy : iy - Dims<N>::NK;
-        const float fk[3] = {(float)kx, (float)ky, (float)kz};
-        const int k2i = kx * kx + ky * ky + kz * kz;
-        const float k2 = (float)k2i;
-        float2 n[3], un[3], us[3];
+        const int iy = rem / D::NZP, kz = rem % D::NZP;
+        const bool any = j < SU2 && kz < D::NZ;
+        const bool both = any && kz + 1 < D::NZ;
+        float4 n4[3], u4[3], s4[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            n[q] = cscale(nh[q * Dims<N>::SU + mi], inv_n3);
-            un[q] = U[q * Dims<N>::SU + mi];
-            us[q] = stage != 0 ? S[q * Dims<N>::SU + mi] : un[q];
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            n4[q] = any ? nh[q * SU2 + j] : z4;
+            u4[q] = any ? U[q * SU2 + j] : z4;
+            s4[q] = (any && stage != 0) ? S[q * SU2 + j] : u4[q];
         }
-        // Leray projection P_ij = delta_ij - k_i k_j / k^2; k = 0 held at zero
-        if (k2i == 0) {
-            n[0] = n[1] = n[2] = make_float2(0.f, 0.f);
-        } else {
-            const float inv = 1.f / k2;
-            const float dr = (fk[0] * n[0].x + fk[1] * n[1].x + fk[2] * n[2].x) * inv;
-            const float di = (fk[0] * n[0].y + fk[1] * n[1].y + fk[2] * n[2].y) * inv;
+        if (!any) continue;
+        const int kx = ix <= D::KC ? ix : ix - D::NK;
+        const int ky = iy <= D::KC ? iy : iy - D::NK;
+        float4 o4[3];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) n[q] = make_float2(n[q].x - fk[q] * dr, n[q].y - fk[q] * di);
+        for (int h = 0; h < 2; ++h) {
+            float2 n[3], un[3], us[3], o[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                n[q] = h ? make_float2(n4[q].z, n4[q].w) : make_float2(n4[q].x, n4[q].y);
+                un[q] = h ? make_float2(u4[q].z, u4[q].w) : make_float2(u4[q].x, u4[q].y);
+                us[q] = h ? make_float2(s4[q].z, s4[q].w) : make_float2(s4[q].x, s4[q].y);
+            }
+            bool band;
+            float k2;
+            const float a2 = update_mode(c, kx, ky, kz + h, n, un, us, o, band, k2);
+            const bool keep = h == 0 || both;
+            const float wgt = (kz + h) == 0 ? 1.f : 2.f;   // Hermitian multiplicity in the full spectrum
+            if (keep) {
+                se += 0.5f * wgt * a2;
+                sd += c.nu * k2 * wgt * a2;
+                if (band) sb += 0.5f * wgt * a2;
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float2 v = keep ? o[q] : make_float2(0.f, 0.f);
+                if (h == 0) { o4[q].x = v.x; o4[q].y = v.y; } else { o4[q].z = v.x; o4[q].w = v.y; }
+            }
         }
-        const float wgt = kz == 0 ? 1.f : 2.f;   // Hermitian multiplicity in the full spectrum
-        const bool band = k2i >= blo && k2i <= bhi;
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (band) n[q] = make_float2(n[q].x + alpha * us[q].x, n[q].y + alpha * us[q].y);
-        const float ea = co.a != 0.f ? expf(-nu * k2 * co.ha * dtf) : 0.f;
-        const float eb = expf(-nu * k2 * co.hb * dtf);
-        float a2 = 0.f;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const float rx = us[q].x + dtf * n[q].x, ry = us[q].y + dtf * n[q].y;
-            const float ox = co.a * ea * un[q].x + co.b * eb * rx;
-            const float oy = co.a * ea * un[q].y + co.b * eb * ry;
-            dst[q * Dims<N>::SU + mi] = make_float2(ox, oy);
-            a2 += ox * ox + oy * oy;
-        }
-        se += 0.5f * wgt * a2;
-        sd += nu * k2 * wgt * a2;
-        if (band) sb += 0.5f * wgt * a2;
+        for (int q = 0; q < 3; ++q) dst[q * SU2 + j] = o4[q];
     }
     double vals[3] = {(double)se, (double)sd, (double)sb};
     double *out = g.partial + ((long long)(g.first + m) * g.partial_blocks + blockIdx.x) * 4;

@@ -283,12 +283,16 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
             fft_line_warp_tw<N, false, VAR>(bb, p, TW, at);
             fft_line_warp_tw<N, false, VAR>(cc, p, TW, at);
         }
-        // a = ux + i uy, bb = uz + i wx, cc = wy + i wz at positions out_pos
+        // a = ux + i uy, bb = uz + i wx, cc = wy + i wz at positions out_pos;
+        // the CFL step takes max|u_i| of the first stage only
+        if (stage_idx == 0) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) umax = fmaxf(umax, fmaxf(fabsf(a[i].x), fmaxf(fabsf(a[i].y), fabsf(bb[i].x))));
+        }
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const float ux = a[i].x, uy = a[i].y, uz = bb[i].x;
             const float wx = bb[i].y, wy = cc[i].x, wz = cc[i].y;
-            umax = fmaxf(umax, fmaxf(fabsf(ux), fmaxf(fabsf(uy), fabsf(uz))));
             w0[i] = make_float2(uy * wz - uz * wy, uz * wx - ux * wz);
             nz[i] = ux * wy - uy * wx;
         }
