@@ -106,6 +106,15 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// wait until at most `Pending` of this thread's committed groups are in flight
+template <int Pending>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory");
+}
+
 __device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restrict__ g, int N)
 {
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g[i];
@@ -141,16 +150,29 @@ k_inv_x(Geo g, int use_S)
     const float2 *X = (use_S ? g.S : g.U) + (long long)m * 3 * Dims<N>::SU + col0;
     // staging of the three velocity components of this column tile with
     // asynchronous 16-byte copies (two columns each, the dealiased columns
-    // zero-filled): the whole tile is in flight at once, no registers held
+    // zero-filled), one commit group per component in the order the
+    // transforms use them: the whole tile is in flight at once, no registers
+    // held, and the first transform starts once its component has landed
     constexpr int per = Dims<N>::NK * T;
-    for (int idx = 2 * threadIdx.x; idx < 3 * per; idx += 2 * blockDim.x) {
-        const int q = idx / per, rem = idx % per;
-        const int ix = rem / T, cc = rem % T;   // cc even
-        const int nvalid = min(max(Dims<N>::NZ - (kz0 + cc), 0), 2);
-        cp_async_16(&tile[idx], X + q * Dims<N>::SU + ix * rowU + cc, 8 * nvalid);
+    constexpr int order[3] = {MODE == 0 ? 1 : 0, MODE == 0 ? 2 : 1, MODE == 0 ? 0 : 2};
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int q = order[s];
+        for (int idx = 2 * threadIdx.x; idx < per; idx += 2 * blockDim.x) {
+            const int ix = idx / T, cc = idx % T;   // cc even
+            const int nvalid = min(max(Dims<N>::NZ - (kz0 + cc), 0), 2);
+            cp_async_16(&tile[q * per + idx], X + q * Dims<N>::SU + ix * rowU + cc, 8 * nvalid);
+        }
+        cp_async_commit();
     }
-    cp_async_wait_all();
-    load_twiddles(tw, g.tw, N);   // block barrier: tile complete
+    load_twiddles(tw, g.tw, N);
+    // component order[s] complete and visible to the block
+    auto landed = [&](int s) {
+        if (s == 0) cp_async_wait<2>();
+        else if (s == 1) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();
+    };
 
     float2 *dst0 = g.A + (long long)m * kFields * Dims<N>::SA + ((long long)iy * N) * Dims<N>::NZP + kz;
     auto at = [&](int pos) { return &buf[pos * T + c]; };
@@ -179,14 +201,17 @@ k_inv_x(Geo g, int use_S)
     float2 Ua[V], Ub[V];
     if constexpr (MODE == 0) {
         // omega = i k x u: (k x u)_x = ky uz - kz uy, _y = kz ux - kx uz, _z = kx uy - ky ux
+        landed(0);
         transform(Ua, 1, false);                                  // uy
         store(Ua, 1);
+        landed(1);
         transform(Ub, 2, false);                                  // uz
         store(Ub, 2);
 #pragma unroll
         for (int i = 0; i < V; ++i)
             Ua[i] = mul_i(make_float2(ky * Ub[i].x - kzf * Ua[i].x, ky * Ub[i].y - kzf * Ua[i].y));
         store(Ua, 3);                                             // omega_x
+        landed(2);
         transform(Ua, 0, false);                                  // ux
         store(Ua, 0);
         transform(Ub, 2, true);                                   // i kx uz
@@ -203,6 +228,7 @@ k_inv_x(Geo g, int use_S)
         // A_ij = i k_j u_i, f = 3 i + j (A_33 is not stored)
 #pragma unroll 1
         for (int ci = 0; ci < 3; ++ci) {
+            landed(ci);
             transform(Ua, ci, false);
 #pragma unroll
             for (int i = 0; i < V; ++i) Ub[i] = mul_i(cscale(Ua[i], ky));
