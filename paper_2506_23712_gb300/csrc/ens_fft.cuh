@@ -407,6 +407,15 @@ template <> struct WPad<128> { static constexpr bool on = true; static constexpr
 template <> struct WPad<256> { static constexpr bool on = true; static constexpr int SROW = 312, A0 = 4, D0 = 1, A1 = 5, D1 = 8; };
 template <> struct WPad<512> { static constexpr bool on = true; static constexpr int SROW = 543, A0 = 4, D0 = 1, A1 = 1, D1 = 0; };
 
+// the same per plan variant (WPlanV<N, VAR>): VAR 0 is WPad<N>
+template <int N, int VAR>
+struct WPadV {
+    static constexpr bool on = false;
+    static constexpr int SROW = 0, A0 = 0, D0 = 0, A1 = 0, D1 = 0;
+};
+template <int N> struct WPadV<N, 0> : WPad<N> {};
+template <> struct WPadV<256, 1> { static constexpr bool on = true; static constexpr int SROW = 271, A0 = 4, D0 = 1, A1 = 0, D1 = 0; };
+
 template <int A, int D>
 __host__ __device__ constexpr int pad_slot(int x)
 {
@@ -440,13 +449,13 @@ __device__ __forceinline__ void exchange_warp_pad(float2 *v, int p, float2 *row)
     }
 }
 
-// Line transform of the default warp plan through the padded layouts; row
-// is this line's shared row (WPad<N>::SROW slots).
-template <int N, bool FWD>
-__device__ __forceinline__ void fft_line_warp_pad(float2 *v, int p, const WarpTw<N, 0> &T, float2 *row)
+// Line transform of a warp plan through the padded layouts; row is this
+// line's shared row (WPadV<N, VAR>::SROW slots).
+template <int N, bool FWD, int VAR = 0>
+__device__ __forceinline__ void fft_line_warp_pad(float2 *v, int p, const WarpTw<N, VAR> &T, float2 *row)
 {
-    using PI = WPlanInfo<N, 0>;
-    using PD = WPad<N>;
+    using PI = WPlanInfo<N, VAR>;
+    using PD = WPadV<N, VAR>;
     static_assert(PD::on && PI::NP <= 3, "padded layouts exist for the power-of-two plans");
     constexpr int P = PI::P, R0 = PI::R0, R1 = PI::R1, R2 = PI::R2;
     pass_regs<N, R0, 1, P, FWD>(v, p, nullptr);

@@ -70,11 +70,10 @@ struct ZCfg {
     static constexpr int NZ2 = (NZ + 1) / 2 * 2;           // copied row length (16-byte multiple)
     static constexpr int PITCH = stage_pitch<N, VAR>();     // staged row pitch, zero past NZ2
     static constexpr int STAGE = LPW * 6 * PITCH;          // float2 per warp buffer
-    // the non-power-of-two default plans use the rows of RowCfg
-    // (XOR-swizzled); the 16 x 16 variant an additive pad of one slot per 16
-    // the power-of-two default plans use the per-exchange padded layouts
-    static constexpr bool PAD = VAR == 0 && WPad<N>::on;
-    static constexpr int SROW = PAD ? WPad<N>::SROW : VAR == 0 ? RowCfg<N>::SROW : N + N / 16 + N / 32 + 1;
+    // the power-of-two plans use the per-exchange padded layouts, the
+    // others the rows of RowCfg (XOR-swizzled)
+    static constexpr bool PAD = WPadV<N, VAR>::on;
+    static constexpr int SROW = PAD ? WPadV<N, VAR>::SROW : VAR == 0 ? RowCfg<N>::SROW : N + N / 16 + N / 32 + 1;
     static __device__ __forceinline__ float2 *slot(float2 *buf, int r, int pos)
     {
         if constexpr (VAR == 0) return row_slot<N>(buf, r, pos);
@@ -154,15 +153,15 @@ struct PairSlots {
 // The last pass leaves position p + P i in slot i of lane p, so Z_{N-k}
 // for this lane's k = p + P i sits in lane (P - p) mod P (slot V - 1 - i,
 // or V - i for lane 0) and comes over by shuffle.
-template <int N>
-__device__ __forceinline__ void forward_pair_store_shfl(float2 *v, int p, int line, const WarpTw<N, 0> &T,
+template <int N, int VAR>
+__device__ __forceinline__ void forward_pair_store_shfl(float2 *v, int p, int line, const WarpTw<N, VAR> &T,
                                                         float2 *row, float2 *dstA, float2 *dstB)
 {
-    using PI = WPlanInfo<N, 0>;
+    using PI = WPlanInfo<N, VAR>;
     constexpr int P = PI::P, V = PI::V, NZ = Dims<N>::NZ;
     static_assert(PI::RL == V, "the last pass must hold one butterfly per lane");
     static_assert((NZ + P - 1) / P <= V, "unpacking rounds exceed the slots");
-    fft_line_warp_pad<N, true>(v, p, T, row);
+    fft_line_warp_pad<N, true, VAR>(v, p, T, row);
     const int src = line * P + ((P - p) & (P - 1));
 #pragma unroll
     for (int i = 0; i < (NZ + P - 1) / P; ++i) {
@@ -232,7 +231,7 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
     auto at = [&](int pos) { return C::slot(rowbuf, line, pos); };
     float2 *myrow = rowbuf + line * C::SROW;   // this lane's line (padded layouts)
     auto fwd_pair = [&](float2 *v, float2 *dA, float2 *dB) {
-        if constexpr (C::PAD) forward_pair_store_shfl<N>(v, p, line, TW, myrow, dA, dB);
+        if constexpr (C::PAD) forward_pair_store_shfl<N, VAR>(v, p, line, TW, myrow, dA, dB);
         else forward_pair_store_tw<N, VAR>(v, p, line, TW, rowbuf, dA, dB, Dims<N>::NZ);
     };
     float umax = 0.f;
@@ -275,9 +274,9 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         PairSlots<N, VAR, 0>::load(bb, X + 2 * R, X + 3 * R, p);
         PairSlots<N, VAR, 0>::load(cc, X + 4 * R, X + 5 * R, p);
         if constexpr (C::PAD) {
-            fft_line_warp_pad<N, false>(a, p, TW, myrow);
-            fft_line_warp_pad<N, false>(bb, p, TW, myrow);
-            fft_line_warp_pad<N, false>(cc, p, TW, myrow);
+            fft_line_warp_pad<N, false, VAR>(a, p, TW, myrow);
+            fft_line_warp_pad<N, false, VAR>(bb, p, TW, myrow);
+            fft_line_warp_pad<N, false, VAR>(cc, p, TW, myrow);
         } else {
             fft_line_warp_tw<N, false, VAR>(a, p, TW, at);
             fft_line_warp_tw<N, false, VAR>(bb, p, TW, at);

@@ -135,9 +135,17 @@ def pack(masks):
     return lo, hi
 
 
-def exchange_patterns(N):
+# second warp plans of the z pass (WPlanV<N, VAR> in csrc/ens_fft.cuh)
+PLAN_VARIANTS = {(256, 1): (16, (16, 16))}
+
+
+def plan_of(N, var=0):
+    return PLANS[N] if var == 0 else PLAN_VARIANTS[(N, var)]
+
+
+def exchange_patterns(N, var=0):
     """[[per-lane (line, pos)] for every request of exchange s] for each s"""
-    P, radices = PLANS[N]
+    P, radices = plan_of(N, var)
     lpw = 32 // P
     res = []
     ns = 1
@@ -156,9 +164,9 @@ def exchange_patterns(N):
     return res
 
 
-def pad_search(N):
+def pad_search(N, var=0):
     """(wavefronts, row stride, [(A_s, D_s)]) of the best per-exchange pads"""
-    ex = exchange_patterns(N)
+    ex = exchange_patterns(N, var)
     best = None
     for srow in range(N, N + N // 2 + 1):
         tot, choice = 0, []
@@ -193,3 +201,6 @@ if __name__ == "__main__":
     for N in (16, 32, 64, 128, 256, 512):
         tot, srow, choice = pad_search(N)
         print("WPad<%d>: SROW %d, (A, D) per exchange %s, %d wavefronts" % (N, srow, choice, tot))
+    for (N, var) in PLAN_VARIANTS:
+        tot, srow, choice = pad_search(N, var)
+        print("WPadV<%d, %d>: SROW %d, (A, D) per exchange %s, %d wavefronts" % (N, var, srow, choice, tot))

@@ -17,12 +17,16 @@ HDR = os.path.join(os.path.dirname(S.__file__), "csrc", "ens_fft.cuh")
 
 
 def wpad_table():
+    """{(N, plan variant): (row stride, [(A_s, D_s)])} from WPad / WPadV"""
     txt = open(HDR).read()
     out = {}
-    for m in re.finditer(r"struct WPad<(\d+)>\s*\{[^}]*SROW = (\d+),\s*A0 = (\d+), D0 = (\d+), A1 = (\d+), D1 = (\d+);",
-                         txt):
+    num = r"SROW = (\d+),\s*A0 = (\d+), D0 = (\d+), A1 = (\d+), D1 = (\d+);"
+    for m in re.finditer(r"struct WPad<(\d+)>\s*\{[^}]*" + num, txt):
         n, srow, a0, d0, a1, d1 = map(int, m.groups())
-        out[n] = (srow, [(a0, d0), (a1, d1)])
+        out[(n, 0)] = (srow, [(a0, d0), (a1, d1)])
+    for m in re.finditer(r"struct WPadV<(\d+), (\d+)>\s*\{[^}]*" + num, txt):
+        n, var, srow, a0, d0, a1, d1 = map(int, m.groups())
+        out[(n, var)] = (srow, [(a0, d0), (a1, d1)])
     return out
 
 
@@ -33,15 +37,18 @@ def pad(x, A, D):
 TABLE = wpad_table()
 
 
+KEYS = [(16, 0), (32, 0), (64, 0), (128, 0), (256, 0), (512, 0), (256, 1)]
+
+
 def test_table_covers_power_of_two_plans():
-    assert sorted(TABLE) == [16, 32, 64, 128, 256, 512]
+    assert sorted(TABLE) == sorted(KEYS)
 
 
-@pytest.mark.parametrize("N", [16, 32, 64, 128, 256, 512])
-def test_exchange_slots_in_bounds_injective_and_conflict_free(N):
-    srow, ad = TABLE[N]
-    P, radices = S.PLANS[N]
-    ex = S.exchange_patterns(N)
+@pytest.mark.parametrize("N,var", KEYS)
+def test_exchange_slots_in_bounds_injective_and_conflict_free(N, var):
+    srow, ad = TABLE[(N, var)]
+    P, radices = S.plan_of(N, var)
+    ex = S.exchange_patterns(N, var)
     assert len(ex) == len(radices) - 1
     total = 0
     for s, pats in enumerate(ex):
@@ -58,10 +65,10 @@ def test_exchange_slots_in_bounds_injective_and_conflict_free(N):
     assert total == ideal or (N == 32 and total <= ideal + 8)
 
 
-def emulate(N, lanes_v, fwd):
+def emulate(N, var, lanes_v, fwd):
     """the P lanes of one line through pass_regs / exchange_warp_pad"""
-    srow, ad = TABLE[N]
-    P, rad = S.PLANS[N]
+    srow, ad = TABLE[(N, var)]
+    P, rad = S.plan_of(N, var)
     sgn = -1 if fwd else 1
     tw = np.exp(sgn * 2j * np.pi * np.arange(N) / N)
     ns = 1
@@ -97,10 +104,10 @@ def emulate(N, lanes_v, fwd):
     return lanes_v
 
 
-@pytest.mark.parametrize("N", [16, 32, 64, 128, 256, 512])
-def test_emulated_pair_transforms_match_numpy(N):
+@pytest.mark.parametrize("N,var", KEYS)
+def test_emulated_pair_transforms_match_numpy(N, var):
     rng = np.random.default_rng(N)
-    P, rad = S.PLANS[N]
+    P, rad = S.plan_of(N, var)
     V, R0 = N // P, rad[0]
     kc = (N + 2) // 3 - 1
     nz = kc + 1
@@ -112,7 +119,7 @@ def test_emulated_pair_transforms_match_numpy(N):
     full = np.zeros(N, complex)
     full[:nz] = xa + 1j * xb
     full[N - kc:] = np.conj(xa[1:][::-1]) + 1j * np.conj(xb[1:][::-1])
-    out = emulate(N, [np.array([full[pos(p, i)] for i in range(V)]) for p in range(P)], fwd=False)
+    out = emulate(N, var, [np.array([full[pos(p, i)] for i in range(V)]) for p in range(P)], fwd=False)
     got = np.empty(N, complex)
     for p in range(P):
         for i in range(V):
@@ -123,7 +130,7 @@ def test_emulated_pair_transforms_match_numpy(N):
     # forward of two real rows, then the shuffle unpacking
     ra, rb = rng.standard_normal(N), rng.standard_normal(N)
     z = ra + 1j * rb
-    out = emulate(N, [np.array([z[pos(p, i)] for i in range(V)]) for p in range(P)], fwd=True)
+    out = emulate(N, var, [np.array([z[pos(p, i)] for i in range(V)]) for p in range(P)], fwd=True)
     fa, fb = np.fft.rfft(ra), np.fft.rfft(rb)
     for i in range((nz + P - 1) // P):
         for p in range(P):
