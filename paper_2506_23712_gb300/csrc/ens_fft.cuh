@@ -116,9 +116,22 @@ struct Dft {
     static __device__ __forceinline__ void combine(float2 *v, const float2 *e, const float2 *o)
     {
         if constexpr (K < R / 2) {
-            const float2 t = twmul<R, K, FWD>(o[K]);
-            v[K] = cadd(e[K], t);
-            v[K + R / 2] = csub(e[K], t);
+            constexpr int j = (K * (48 / R)) % 48;
+            if constexpr (j % 12 == 6) {
+                // W = h (sc + i ss) with h = sqrt(2)/2: o W = h (A + i B), and
+                // the butterfly is four FMAs on e
+                constexpr float h = 0.70710678118654752f;
+                constexpr float sc = (j == 6 || j == 42) ? 1.f : -1.f;                      // sign of cos
+                constexpr float ss = ((j == 6 || j == 18) ? 1.f : -1.f) * (FWD ? -1.f : 1.f);   // sign of sin
+                const float A = sc * o[K].x - ss * o[K].y;
+                const float B = ss * o[K].x + sc * o[K].y;
+                v[K] = make_float2(fmaf(h, A, e[K].x), fmaf(h, B, e[K].y));
+                v[K + R / 2] = make_float2(fmaf(-h, A, e[K].x), fmaf(-h, B, e[K].y));
+            } else {
+                const float2 t = twmul<R, K, FWD>(o[K]);
+                v[K] = cadd(e[K], t);
+                v[K + R / 2] = csub(e[K], t);
+            }
             combine<K + 1>(v, e, o);
         }
     }
