@@ -501,19 +501,27 @@ def main():
         host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
         E.ens_get_state(ens.ctx, host.data_ptr(), nbytes)
         e2e_steps = max(2, min(args.steps, 5))
+        E.ens_step_host(ens.ctx, host.data_ptr(), host.data_ptr(), nbytes, 0)   # creates the copy streams
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            E.ens_set_state(ens.ctx, host.data_ptr(), nbytes)
-            ens.step(1)
-            E.ens_get_state(ens.ctx, host.data_ptr(), nbytes)
+            E.ens_step_host(ens.ctx, host.data_ptr(), host.data_ptr(), nbytes, 0)
             dg, _ = E.ens_diagnostics(ens.ctx, n_mem, raise_on_flag=False)
         barrier()
         sec = time.perf_counter() - t0
+        # the same without overlap: upload, graph step, download one after another
+        t1 = time.perf_counter()
+        for _ in range(2):
+            E.ens_set_state(ens.ctx, host.data_ptr(), nbytes)
+            ens.step(1)
+            E.ens_get_state(ens.ctx, host.data_ptr(), nbytes)
+            E.ens_diagnostics(ens.ctx, n_mem, raise_on_flag=False)
+        serial = world * n_mem * 2 / (time.perf_counter() - t1)
         diag_bytes = n_mem * 96
         e2e = {"value": world * n_mem * e2e_steps / sec, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + diag_bytes, "steps": e2e_steps,
-               "path": "ens_set_state(pinned host) + ens_step + ens_get_state(pinned host) + ens_diagnostics"}
+               "path": "ens_step_host(pinned host in/out, members in four chunks: upload, step and download "
+                       "overlapped) + ens_diagnostics", "serial_value": serial}
 
     plain = None
     if not args.no_plain and rank == 0:

@@ -185,6 +185,20 @@ ens_status ens_step_nograph(ens_ctx *ctx, int nsteps);
 /* Same results, launched the slow way for comparison: one member at a time,
  * every pass of every member a separate launch on the context stream. */
 ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
+/* One step (the step of ens_step, Sec. IV) of an ensemble whose state lives
+ * in host memory: host_in holds the state in the layout of ens_get_state
+ * (bytes >= ens_state_bytes), the stepped state is written to host_out
+ * (host_out may equal host_in).  The members go through in chunks of
+ * `chunk` members of one grid size (0: a quarter of each group, at least
+ * one): a chunk's upload, its energy sums (as after ens_set_state), its
+ * three RK stages and its download are ordered on the device, and the
+ * upload of the next chunk and the download of the previous one run on two
+ * copy streams while a chunk computes.  Overlap needs page-locked host
+ * memory; pageable memory gives the same results without it.  The device
+ * copy of the state and the diagnostics end as after ens_set_state,
+ * ens_step and ens_get_state; the call returns once host_out is written.
+ * ENS_EINVAL for null buffers, too few bytes or chunk < 0. */
+ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size_t bytes, int chunk);
 
 /* ---- autotuning (no counterpart in the paper: launch shapes of this
  * library's kernels) ------------------------------------------------------ */

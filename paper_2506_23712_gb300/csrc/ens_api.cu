@@ -63,6 +63,10 @@ struct ens_ctx {
     HistDev hd{};
     double *mix = nullptr;       // mixture scratch
     cudaGraphExec_t graph = nullptr;
+    // streamed host step: copy streams and per-chunk events (created on first use)
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaEvent_t ev_start = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_done;
     int rk = 3;
     int sms = 0;                 // streaming multiprocessors of the device
     int parallel_groups = 1;     // grid-size groups as parallel graph branches
@@ -218,6 +222,20 @@ size_t carve(const ens_member_desc *m, int n, const ens_hist_spec *h, char *base
 
 // device slot of user member i
 int slot_of(const ens_ctx *ctx, int i) { return ctx->groups[ctx->member_group[i]].geo.first + ctx->member_local[i]; }
+
+// Members [k0, k0 + cnt) of a group (pointers shifted).
+Geo member_range(const Geo &g0, int k0, int cnt)
+{
+    Geo g = g0;
+    g.U += (long long)k0 * 3 * g.sU;
+    g.S += (long long)k0 * 3 * g.sU;
+    g.A += (long long)k0 * kFields * g.sA;
+    g.B += (long long)k0 * kFields * g.sB;
+    g.shell += (long long)k0 * g.shells;
+    g.first += k0;
+    g.members = cnt;
+    return g;
+}
 
 // Geo restricted to one member of a group (pointers shifted).
 Geo single(const ens_ctx *ctx, int i)
@@ -522,6 +540,13 @@ ens_status ens_destroy(ens_ctx *ctx)
     for (auto ev : ctx->ev_join)
         if (ev) cudaEventDestroy(ev);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->copy_in) cudaStreamSynchronize(ctx->copy_in);
+    if (ctx->copy_out) cudaStreamSynchronize(ctx->copy_out);
+    if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+    if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
+    if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    for (auto ev : ctx->ev_in) cudaEventDestroy(ev);
+    for (auto ev : ctx->ev_done) cudaEventDestroy(ev);
     if (ctx->owns && ctx->workspace) cudaFree(ctx->workspace);
     delete ctx;
     return ENS_OK;
@@ -575,6 +600,71 @@ ens_status ens_step(ens_ctx *ctx, int nsteps)
         if (e != cudaSuccess) return cuda_fail(ctx, "cudaGraphInstantiate", e);
     }
     for (int k = 0; k < nsteps; ++k) ENS_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+    return ENS_OK;
+}
+
+ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size_t bytes, int chunk)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (!host_in || !host_out || bytes < ens_state_bytes(ctx) || chunk < 0)
+        return fail(ctx, ENS_EINVAL, "ens_step_host: null buffer, state buffer too small or chunk < 0");
+    if (!ctx->copy_in) {
+        ENS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
+        ENS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
+        ENS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
+    }
+    int nchunks = 0;
+    for (auto &gr : ctx->groups) {
+        const int c = chunk > 0 ? chunk : std::max(1, (gr.geo.members + 3) / 4);
+        nchunks += (gr.geo.members + c - 1) / c;
+    }
+    while ((int)ctx->ev_in.size() < nchunks) {
+        cudaEvent_t a, b;
+        ENS_CUDA(ctx, cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+        ENS_CUDA(ctx, cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+        ctx->ev_in.push_back(a);
+        ctx->ev_done.push_back(b);
+    }
+    // the uploads overwrite U: earlier work of the context stream first
+    ENS_CUDA(ctx, cudaEventRecord(ctx->ev_start, ctx->stream));
+    ENS_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_in, ctx->ev_start, 0));
+    const int PB = ctx->partial_blocks;
+    const int nst = ctx->rk;
+    const char *in = static_cast<const char *>(host_in);
+    char *out = static_cast<char *>(host_out);
+    size_t off = 0;
+    int ci = 0;
+    for (auto &gr : ctx->groups) {
+        const int c = chunk > 0 ? chunk : std::max(1, (gr.geo.members + 3) / 4);
+        const size_t per = sizeof(float2) * 3 * gr.geo.sU;
+        for (int k0 = 0; k0 < gr.geo.members; k0 += c, ++ci) {
+            const int cnt = std::min(c, gr.geo.members - k0);
+            const Geo g = member_range(gr.geo, k0, cnt);
+            const size_t b = per * cnt;
+            MemberDev *md = ctx->md + g.first;
+            double *part = ctx->partial + (size_t)g.first * PB * 4;
+            ENS_CUDA(ctx, cudaMemcpyAsync(g.U, in + off, b, cudaMemcpyHostToDevice, ctx->copy_in));
+            ENS_CUDA(ctx, cudaEventRecord(ctx->ev_in[ci], ctx->copy_in));
+            ENS_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in[ci], 0));
+            // energy sums of the uploaded state, as after ens_set_state
+            ENS_CUDA(ctx, cudaMemsetAsync(part, 0, sizeof(double) * cnt * PB * 4, ctx->stream));
+            launch_state_sums(g, ctx->md, ctx->stream);
+            launch_finish(md, cnt, part, PB, 0, 0, 1, ctx->stream);
+            for (int st = 0; st < nst; ++st) {
+                const int last = st == nst - 1;
+                record_group_stage(ctx, g, st, last, ctx->stream);
+                launch_finish(md, cnt, part, PB, st, last, 0, ctx->stream);
+            }
+            ENS_CUDA(ctx, cudaEventRecord(ctx->ev_done[ci], ctx->stream));
+            ENS_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_out, ctx->ev_done[ci], 0));
+            ENS_CUDA(ctx, cudaMemcpyAsync(out + off, g.U, b, cudaMemcpyDeviceToHost, ctx->copy_out));
+            off += b;
+        }
+    }
+    ENS_CUDA(ctx, cudaGetLastError());
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->copy_out));
+    ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return ENS_OK;
 }
 

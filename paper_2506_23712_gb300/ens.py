@@ -101,6 +101,7 @@ SIGNATURES = [
     ("ens_step", _i, [_vp, _i]),
     ("ens_step_nograph", _i, [_vp, _i]),
     ("ens_step_sequential", _i, [_vp, _i]),
+    ("ens_step_host", _i, [_vp, _vp, _vp, _sz, _i]),
     ("ens_get_tuning", _i, [_vp, _P(Tuning)]),
     ("ens_set_tuning", _i, [_vp, _P(Tuning)]),
     ("ens_autotune", _i, [_vp, _i, _P(Tuning)]),
@@ -451,6 +452,10 @@ def ens_get_state(ctx, host_ptr, nbytes):
 
 def ens_set_state(ctx, host_ptr, nbytes):
     _check(lib().ens_set_state(ctx, ctypes.c_void_p(host_ptr), nbytes), ctx)
+
+
+def ens_step_host(ctx, host_in_ptr, host_out_ptr, nbytes, chunk=0):
+    _check(lib().ens_step_host(ctx, ctypes.c_void_p(host_in_ptr), ctypes.c_void_p(host_out_ptr), nbytes, chunk), ctx)
 
 
 DIAG_KEYS = ("t", "dt", "E", "diss", "EB", "P", "umax", "Rlambda", "kmeta", "steps", "flags")

@@ -372,3 +372,35 @@ def test_uneven_groups_graph_branches_match_sequential(E):
     assert [d["dt"] for d in da] == [d["dt"] for d in dc]
     for e in (a, b, c):
         e.close()
+
+
+@pytest.mark.parametrize("chunk", [0, 2])
+def test_step_host_matches_device_step(E, chunk):
+    """ens_step_host (state streamed from and back to host memory, members
+    in chunks on copy streams) leaves exactly the state and diagnostics of
+    ens_set_state + ens_step + ens_get_state, over two steps, with members of
+    two grid sizes (CFL steps, so dt depends on the state)."""
+    ms = [E.Member(N=n, nu=0.03, lam=0.3 * i - 0.6, k_lo=1, k_hi=2, dt=-1, cfl=0.3, rk_order=3, seed=70 + i)
+          for i, n in enumerate([32, 16, 32, 16, 32])]
+    a, b = E.Ensemble(ms), E.Ensemble(ms)
+    nbytes = E.ens_state_bytes(a.ctx)
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    E.ens_get_state(a.ctx, host.data_ptr(), nbytes)
+    ref = host.clone()
+    for _ in range(2):
+        E.ens_step_host(a.ctx, host.data_ptr(), host.data_ptr(), nbytes, chunk)
+        E.ens_set_state(b.ctx, ref.data_ptr(), nbytes)
+        b.step(1)
+        E.ens_get_state(b.ctx, ref.data_ptr(), nbytes)
+        assert torch.equal(host, ref)
+    da, _ = E.ens_diagnostics(a.ctx, len(ms))
+    db, _ = E.ens_diagnostics(b.ctx, len(ms))
+    for x, y in zip(da, db):
+        for k in ("t", "dt", "E", "diss", "EB", "umax", "steps"):
+            assert x[k] == y[k], k
+    for i in range(len(ms)):
+        assert np.array_equal(a.field(i), b.field(i))
+    with pytest.raises(Exception):
+        E.ens_step_host(a.ctx, host.data_ptr(), host.data_ptr(), nbytes - 8, chunk)
+    a.close()
+    b.close()
