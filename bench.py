@@ -520,7 +520,7 @@ def main():
         diag_bytes = n_mem * 96
         e2e = {"value": world * n_mem * e2e_steps / sec, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + diag_bytes, "steps": e2e_steps,
-               "path": "ens_step_host(pinned host in/out, members in four chunks: upload, step and download "
+               "path": "ens_step_host(pinned host in/out, members in eight chunks: upload, step and download "
                        "overlapped) + ens_diagnostics", "serial_value": serial}
 
     plain = None

@@ -189,7 +189,7 @@ ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
  * in host memory: host_in holds the state in the layout of ens_get_state
  * (bytes >= ens_state_bytes), the stepped state is written to host_out
  * (host_out may equal host_in).  The members go through in chunks of
- * `chunk` members of one grid size (0: a quarter of each group, at least
+ * `chunk` members of one grid size (0: an eighth of each group, at least
  * one): a chunk's upload, its energy sums (as after ens_set_state), its
  * three RK stages and its download are ordered on the device, and the
  * upload of the next chunk and the download of the previous one run on two

@@ -616,7 +616,7 @@ ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size
     }
     int nchunks = 0;
     for (auto &gr : ctx->groups) {
-        const int c = chunk > 0 ? chunk : std::max(1, (gr.geo.members + 3) / 4);
+        const int c = chunk > 0 ? chunk : std::max(1, (gr.geo.members + 7) / 8);
         nchunks += (gr.geo.members + c - 1) / c;
     }
     while ((int)ctx->ev_in.size() < nchunks) {
@@ -636,7 +636,7 @@ ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size
     size_t off = 0;
     int ci = 0;
     for (auto &gr : ctx->groups) {
-        const int c = chunk > 0 ? chunk : std::max(1, (gr.geo.members + 3) / 4);
+        const int c = chunk > 0 ? chunk : std::max(1, (gr.geo.members + 7) / 8);
         const size_t per = sizeof(float2) * 3 * gr.geo.sU;
         for (int k0 = 0; k0 < gr.geo.members; k0 += c, ++ci) {
             const int cnt = std::min(c, gr.geo.members - k0);
