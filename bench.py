@@ -247,7 +247,7 @@ def hellinger(p, q):
     return float(np.sqrt(max(0.0, 1.0 - np.sum(np.sqrt(p * q)))))
 
 
-def measure_surrogate(E, ens, descs, torch, steps=400):
+def measure_surrogate(E, ens, descs, torch, steps=800):
     """Learned lambda interpolant on this ensemble's own histograms: training
     throughput, the tcgen05 hidden-layer GEMM against the BF16 peak, and the
     512-point quadrature mixture against the member quadrature (Hellinger)."""

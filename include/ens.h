@@ -459,8 +459,10 @@ ens_status ens_surrogate_set_params(ens_surrogate *s, const float *host);
  * on n members' histograms (counts layout of ens_get_stats). */
 ens_status ens_surrogate_loss_grad(ens_surrogate *s, int n, const double *lambdas, const uint64_t *counts,
                                    const ens_hist_spec *hist, double *loss, float *grad);
-/* `steps` full-batch Adam steps (learning rate lr) on the members'
- * histograms; *final_loss is the loss of the last step's forward pass. */
+/* `steps` full-batch Adam steps on the members' histograms, the learning
+ * rate decaying along a cosine from lr at the first step of the call to
+ * lr / 20 at its last; *final_loss is the loss of the last step's forward
+ * pass. */
 ens_status ens_surrogate_train(ens_surrogate *s, int n, const double *lambdas, const uint64_t *counts,
                                const ens_hist_spec *hist, int steps, double lr, double *final_loss);
 /* Densities (bin probabilities) at n lambda values: probs [n][qr_bins^2 +

@@ -1065,7 +1065,9 @@ ens_status ens_surrogate_train(ens_surrogate *S, int n, const double *lambdas, c
         S->steps += 1;
         const float b1 = 0.9f, b2 = 0.999f;
         const float bc1 = 1.f - powf(b1, (float)S->steps), bc2 = 1.f - powf(b2, (float)S->steps);
-        k_adam<<<blocks(np, 256), 256, 0, S->s>>>(S->p, S->g, S->m1, S->m2, np, (float)lr, b1, b2, 1e-8f, bc1, bc2);
+        // cosine decay over the call's steps, from lr to lr / 20
+        const double lr_t = lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.14159265358979323846 * it / steps)));
+        k_adam<<<blocks(np, 256), 256, 0, S->s>>>(S->p, S->g, S->m1, S->m2, np, (float)lr_t, b1, b2, 1e-8f, bc1, bc2);
         k_pack_weights<<<blocks((long long)kHid * kHid, 256), 256, 0, S->s>>>(S->p, S->W1b, S->W2b, S->W3b, S->W2t,
                                                                              S->W3t);
     }
