@@ -23,6 +23,50 @@ namespace ens {
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// The same as one packed FP32x2 instruction (sm_100 family; both halves
+// rounded to nearest, as the two scalar operations): half the issue slots.
+// The line transforms take them where issue slots bound the kernel (PK).
+__device__ __forceinline__ unsigned long long f2bits(float2 a) { return *reinterpret_cast<const unsigned long long *>(&a); }
+__device__ __forceinline__ float2 bitsf2(unsigned long long r) { return *reinterpret_cast<const float2 *>(&r); }
+__device__ __forceinline__ float2 cadd_x2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2bits(a)), "l"(f2bits(b)));
+    return bitsf2(r);
+}
+__device__ __forceinline__ float2 csub_x2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2bits(a)), "l"(f2bits(b)));
+    return bitsf2(r);
+}
+// (s, s) a + c with packed FMAs
+__device__ __forceinline__ float2 cfma_x2(float s, float2 a, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2bits(make_float2(s, s))), "l"(f2bits(a)), "l"(f2bits(c)));
+    return bitsf2(r);
+}
+// (s, s) a with a packed multiply
+__device__ __forceinline__ float2 cscale_x2(float s, float2 a)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2bits(make_float2(s, s))), "l"(f2bits(a)));
+    return bitsf2(r);
+}
+template <bool PK>
+__device__ __forceinline__ float2 cadd_(float2 a, float2 b)
+{
+    if constexpr (PK) return cadd_x2(a, b);
+    else return cadd(a, b);
+}
+template <bool PK>
+__device__ __forceinline__ float2 csub_(float2 a, float2 b)
+{
+    if constexpr (PK) return csub_x2(a, b);
+    else return csub(a, b);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -109,8 +153,9 @@ __device__ __forceinline__ float2 twmul(float2 a)
     }
 }
 
-// In-register R-point DFT, natural order in and out.
-template <int R, bool FWD>
+// In-register R-point DFT, natural order in and out; PK: packed FP32x2
+// complex adds.
+template <int R, bool FWD, bool PK = false>
 struct Dft {
     template <int K>
     static __device__ __forceinline__ void combine(float2 *v, const float2 *e, const float2 *o)
@@ -125,12 +170,17 @@ struct Dft {
                 constexpr float ss = ((j == 6 || j == 18) ? 1.f : -1.f) * (FWD ? -1.f : 1.f);   // sign of sin
                 const float A = sc * o[K].x - ss * o[K].y;
                 const float B = ss * o[K].x + sc * o[K].y;
-                v[K] = make_float2(fmaf(h, A, e[K].x), fmaf(h, B, e[K].y));
-                v[K + R / 2] = make_float2(fmaf(-h, A, e[K].x), fmaf(-h, B, e[K].y));
+                if constexpr (PK) {
+                    v[K] = cfma_x2(h, make_float2(A, B), e[K]);
+                    v[K + R / 2] = cfma_x2(-h, make_float2(A, B), e[K]);
+                } else {
+                    v[K] = make_float2(fmaf(h, A, e[K].x), fmaf(h, B, e[K].y));
+                    v[K + R / 2] = make_float2(fmaf(-h, A, e[K].x), fmaf(-h, B, e[K].y));
+                }
             } else {
                 const float2 t = twmul<R, K, FWD>(o[K]);
-                v[K] = cadd(e[K], t);
-                v[K + R / 2] = csub(e[K], t);
+                v[K] = cadd_<PK>(e[K], t);
+                v[K + R / 2] = csub_<PK>(e[K], t);
             }
             combine<K + 1>(v, e, o);
         }
@@ -145,29 +195,29 @@ struct Dft {
             e[i] = v[2 * i];
             o[i] = v[2 * i + 1];
         }
-        Dft<H, FWD>::run(e);
-        Dft<H, FWD>::run(o);
+        Dft<H, FWD, PK>::run(e);
+        Dft<H, FWD, PK>::run(o);
         combine<0>(v, e, o);
     }
 };
 
-template <bool FWD>
-struct Dft<1, FWD> {
+template <bool FWD, bool PK>
+struct Dft<1, FWD, PK> {
     static __device__ __forceinline__ void run(float2 *) {}
 };
 
-template <bool FWD>
-struct Dft<2, FWD> {
+template <bool FWD, bool PK>
+struct Dft<2, FWD, PK> {
     static __device__ __forceinline__ void run(float2 *v)
     {
         const float2 a = v[0], b = v[1];
-        v[0] = cadd(a, b);
-        v[1] = csub(a, b);
+        v[0] = cadd_<PK>(a, b);
+        v[1] = csub_<PK>(a, b);
     }
 };
 
-template <bool FWD>
-struct Dft<3, FWD> {
+template <bool FWD, bool PK>
+struct Dft<3, FWD, PK> {
     static __device__ __forceinline__ void run(float2 *v)
     {
         // X1,2 = v0 - (v1+v2)/2 -/+ s i (sqrt3/2)(v1 - v2), s = +1 fwd
@@ -226,7 +276,7 @@ struct PlanInfo {
 };
 
 // One radix-R pass on the registers: twiddles then R-point DFTs.
-template <int N, int R, int Ns, int P, bool FWD>
+template <int N, int R, int Ns, int P, bool FWD, bool PK = false>
 __device__ __forceinline__ void pass_regs(float2 *v, int p, const float2 *__restrict__ tw)
 {
     constexpr int B = N / (R * P);
@@ -242,7 +292,7 @@ __device__ __forceinline__ void pass_regs(float2 *v, int p, const float2 *__rest
                 v[b * R + t] = cmul(v[b * R + t], w);
             }
         }
-        Dft<R, FWD>::run(&v[b * R]);
+        Dft<R, FWD, PK>::run(&v[b * R]);
     }
 }
 
@@ -368,7 +418,7 @@ struct PassTw {
     }
 };
 
-template <int N, int R, int Ns, int P, bool FWD>
+template <int N, int R, int Ns, int P, bool FWD, bool PK = false>
 __device__ __forceinline__ void pass_regs_tw(float2 *v, const PassTw<N, R, Ns, P> &T)
 {
     constexpr int B = N / (R * P);
@@ -380,7 +430,7 @@ __device__ __forceinline__ void pass_regs_tw(float2 *v, const PassTw<N, R, Ns, P
             if (!FWD) w.y = -w.y;
             v[b * R + t] = cmul(v[b * R + t], w);
         }
-        Dft<R, FWD>::run(&v[b * R]);
+        Dft<R, FWD, PK>::run(&v[b * R]);
     }
 }
 
@@ -471,12 +521,12 @@ __device__ __forceinline__ void fft_line_warp_pad(float2 *v, int p, const WarpTw
     using PD = WPadV<N, VAR>;
     static_assert(PD::on && PI::NP <= 3, "padded layouts exist for the power-of-two plans");
     constexpr int P = PI::P, R0 = PI::R0, R1 = PI::R1, R2 = PI::R2;
-    pass_regs<N, R0, 1, P, FWD>(v, p, nullptr);
+    pass_regs<N, R0, 1, P, FWD, true>(v, p, nullptr);
     exchange_warp_pad<N, R0, 1, R1, P, PD::A0, PD::D0>(v, p, row);
-    pass_regs_tw<N, R1, R0, P, FWD>(v, T.t1);
+    pass_regs_tw<N, R1, R0, P, FWD, true>(v, T.t1);
     if constexpr (PI::NP == 3) {
         exchange_warp_pad<N, R1, R0, R2, P, PD::A1, PD::D1>(v, p, row);
-        pass_regs_tw<N, R2, R0 * R1, P, FWD>(v, T.t2);
+        pass_regs_tw<N, R2, R0 * R1, P, FWD, true>(v, T.t2);
     }
 }
 
@@ -487,16 +537,16 @@ __device__ __forceinline__ void fft_line_warp_tw(float2 *v, int p, const WarpTw<
     using PI = WPlanInfo<N, VAR>;
     constexpr int P = PI::P;
     constexpr int R0 = PI::R0, R1 = PI::R1, R2 = PI::R2, R3 = PI::R3;
-    pass_regs<N, R0, 1, P, FWD>(v, p, nullptr);
+    pass_regs<N, R0, 1, P, FWD, true>(v, p, nullptr);
     exchange_warp<N, R0, 1, R1, P>(v, p, at);
-    pass_regs_tw<N, R1, R0, P, FWD>(v, T.t1);
+    pass_regs_tw<N, R1, R0, P, FWD, true>(v, T.t1);
     if constexpr (PI::NP >= 3) {
         exchange_warp<N, R1, R0, R2, P>(v, p, at);
-        pass_regs_tw<N, R2, R0 * R1, P, FWD>(v, T.t2);
+        pass_regs_tw<N, R2, R0 * R1, P, FWD, true>(v, T.t2);
     }
     if constexpr (PI::NP >= 4) {
         exchange_warp<N, R2, R0 * R1, R3, P>(v, p, at);
-        pass_regs_tw<N, R3, R0 * R1 * R2, P, FWD>(v, T.t3);
+        pass_regs_tw<N, R3, R0 * R1 * R2, P, FWD, true>(v, T.t3);
     }
 }
 
@@ -507,16 +557,16 @@ __device__ __forceinline__ void fft_line_warp(float2 *v, int p, const float2 *__
     using PI = WPlanInfo<N>;
     constexpr int P = PI::P;
     constexpr int R0 = PI::R0, R1 = PI::R1, R2 = PI::R2, R3 = PI::R3;
-    pass_regs<N, R0, 1, P, FWD>(v, p, tw);
+    pass_regs<N, R0, 1, P, FWD, true>(v, p, tw);
     exchange_warp<N, R0, 1, R1, P>(v, p, at);
-    pass_regs<N, R1, R0, P, FWD>(v, p, tw);
+    pass_regs<N, R1, R0, P, FWD, true>(v, p, tw);
     if constexpr (PI::NP >= 3) {
         exchange_warp<N, R1, R0, R2, P>(v, p, at);
-        pass_regs<N, R2, R0 * R1, P, FWD>(v, p, tw);
+        pass_regs<N, R2, R0 * R1, P, FWD, true>(v, p, tw);
     }
     if constexpr (PI::NP >= 4) {
         exchange_warp<N, R2, R0 * R1, R3, P>(v, p, at);
-        pass_regs<N, R3, R0 * R1 * R2, P, FWD>(v, p, tw);
+        pass_regs<N, R3, R0 * R1 * R2, P, FWD, true>(v, p, tw);
     }
 }
 

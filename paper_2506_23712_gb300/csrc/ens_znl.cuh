@@ -171,8 +171,11 @@ __device__ __forceinline__ void forward_pair_store_shfl(float2 *v, int p, int li
         const int k = p + i * P;
         if (k < NZ) {
             // Xa = (Z_k + conj Z_{N-k}) / 2 ; Xb = (Z_k - conj Z_{N-k}) / (2i)
-            dstA[k] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y + w.y));
-            if (dstB) dstB[k] = make_float2(0.5f * (z.y - w.y), -0.5f * (z.x - w.x));
+            dstA[k] = cscale_x2(0.5f, cadd_x2(z, w));
+            if (dstB) {
+                const float2 d = csub_x2(z, w);
+                dstB[k] = make_float2(0.5f * d.y, -0.5f * d.x);
+            }
         }
     }
 }
