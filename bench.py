@@ -481,6 +481,26 @@ def main():
         passes[name] = {"ms": round(pms, 4), "algorithmic_GB": round(nbytes / 1e9, 4),
                         "GBps": round(nbytes / 1e9 / (pms / 1e3), 1),
                         "frac": round(nbytes / 1e9 / (pms / 1e3) / hbm, 4)}
+    # statistics snapshot (gradient fields, invariants, histograms, moments of
+    # every member) and the FP64 lambda mixture of the snapshot
+    ens.gradient_stats(accumulate=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(3):
+        ens.gradient_stats(accumulate=False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sms = a.elapsed_time(b) / 3
+    sbytes = E.ens_pass_bytes(ens.ctx, 5, 0)
+    t0 = time.perf_counter()
+    E.ens_mixture(ens.ctx, n_mem, ens.hist, kind=E.W_GAUSS_PAPER, c=0.023, Z=1.5 * math.log(261.0 / 63.0))
+    mix_ms = (time.perf_counter() - t0) * 1e3
+    stats = {"ms": round(sms, 4), "algorithmic_GB": round(sbytes / 1e9, 4),
+             "GBps": round(sbytes / 1e9 / (sms / 1e3), 1), "frac": round(sbytes / 1e9 / (sms / 1e3) / hbm, 4),
+             "members": n_mem, "mixture_ms": round(mix_ms, 3),
+             "note": "one ens_gradient_stats snapshot of all members (CUDA events); mixture: ens_mixture "
+                     "with the paper's Gaussian lambda weights, host wall time incl. the copies"}
     dom = max(passes, key=lambda k: passes[k]["ms"])
     dom_idx = PASS_NAMES.index(dom)
     achieved = passes[dom]["GBps"]
@@ -557,7 +577,7 @@ def main():
                            "tuning": tuning,
                            "flagged_members": flagged},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kps * args.steps,
-                "clocks": clk, "plain": plain, "passes": passes, "uneven_batch": uneven, "mixed_resolution": mixed,
+                "clocks": clk, "plain": plain, "passes": passes, "stats_snapshot": stats, "uneven_batch": uneven, "mixed_resolution": mixed,
                 "surrogate": surrogate}
         print(json.dumps(line), flush=True)
     if world > 1:

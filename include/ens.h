@@ -76,7 +76,10 @@ typedef struct {
 /* Histogram specification (common physical bin edges for all members so
  * that histograms can be mixed).  Q axis in units q0 = eps_norm/(2 nu_norm),
  * R axis in q0^(3/2), tails in log10(eps/eps_norm) and
- * log10(omega^2 nu_norm / eps_norm). */
+ * log10(omega^2 nu_norm / eps_norm).  The statistics pass keeps one copy of
+ * the counts per CTA in shared memory: ens_create refuses (ENS_EINVAL) a
+ * layout that does not fit beside its staged rows (about 180 KB of counts at
+ * N = 256, less at N = 128 and 384; 64 x 64 + 2 x 256 bins use 18 KB). */
 typedef struct {
     int qr_bins;        /* bins per axis of the Q-R histogram (e.g. 64) */
     double q_lim;       /* Q/q0 in [-q_lim, q_lim) */
@@ -507,7 +510,8 @@ ens_status ens_run_pass(ens_ctx *ctx, int pass, int stage);
 /* Kernels one ens_step launches per step (graph nodes). */
 int ens_kernels_per_step(const ens_ctx *ctx);
 /* Algorithmic HBM bytes of one pass for all members (unique bytes read +
- * written, valid modes only); pass as in ens_run_pass, stage 0..2. */
+ * written, valid modes only); pass as in ens_run_pass, stage 0..2; pass 5
+ * is one ens_gradient_stats snapshot (stage ignored). */
 double ens_pass_bytes(const ens_ctx *ctx, int pass, int stage);
 
 #ifdef __cplusplus

@@ -428,7 +428,18 @@ static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, co
     launch_edges(ctx->edges, ctx->edges + (h->qr_bins + 1), ctx->edges + 2 * (h->qr_bins + 1),
                  const_cast<float *>(hd.edges_g), h->qr_bins, h->tail_bins, h->grad_bins, h->q_lim, h->r_lim,
                  h->tail_lo, h->tail_hi, h->grad_lim, st);
+    int smem_optin = 0;
+    ENS_CUDA(ctx, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     for (auto &gr : ctx->groups) {
+        const size_t need = stats_smem(gr.geo.N, h->qr_bins, h->tail_bins, h->grad_bins);
+        if (need > (size_t)smem_optin) {
+            char buf[256];
+            snprintf(buf, sizeof buf,
+                     "histogram layout too large for the statistics pass at N = %d: %zu bytes of shared memory per "
+                     "CTA, the device offers %d (fewer Q-R, tail or gradient bins)",
+                     gr.geo.N, need, smem_optin);
+            return fail(ctx, ENS_EINVAL, buf);
+        }
         ENS_CUDA(ctx, prepare_kernels(gr.geo.N, h->qr_bins, h->tail_bins, h->grad_bins));
         const int per_sm = znl_ctas_per_sm(gr.geo.N);
         if (per_sm <= 0 || ctx->sms <= 0) return fail(ctx, ENS_ECUDA, "occupancy query of the z pass failed");
@@ -711,6 +722,9 @@ double ens_pass_bytes(const ens_ctx *ctx, int pass, int stage)
         case 2: bytes = 6 * b + 3 * b; break;
         case 3: bytes = 3 * b + 3 * a; break;
         case 4: bytes = 3 * a + (stage > 0 ? 2 : 1) * 3 * st + 3 * st; break;
+        // statistics snapshot: 8 gradient components along x (3 state comps
+        // in), along y, then the z pass that reads them for the invariants
+        case 5: bytes = 3 * st + 8 * a + 8 * a + 8 * b + 8 * b; break;
         default: bytes = 0.0;
         }
         total += bytes * g.members;

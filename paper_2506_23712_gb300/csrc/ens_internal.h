@@ -9,7 +9,6 @@ namespace ens {
 constexpr int kTile = 16;        // column padding of the layouts; widest column tile of the strided-axis passes
 constexpr int kFields = 8;       // fields per member in the pass buffers
 constexpr int kNMom = 48;        // gradient moment sums per member
-constexpr int kStatsIters = 16;  // row groups per CTA in the statistics pass
 constexpr int kUpdChunk = 2048;  // modes per CTA of the split update pass (256 threads x 8)
 
 // Per-member parameters and run state, resident in device memory.

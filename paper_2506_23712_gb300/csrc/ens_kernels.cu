@@ -313,9 +313,17 @@ int plan_threads(int N)
     return 0;
 }
 
+size_t stats_smem(int N, int nq, int nt, int ng)
+{
+#define X(n) if (N == n) return smem_stats<n>(nq, nt, ng);
+    ENS_SUPPORTED_N(X)
+#undef X
+    return 0;
+}
+
 int stats_blocks(int N)
 {
-#define X(n) if (N == n) return (int)(((long long)n * n + (long long)RowCfg<n>::RZ * kStatsIters - 1) / ((long long)RowCfg<n>::RZ * kStatsIters));
+#define X(n) if (N == n) return stats_ctas<n>();
     ENS_SUPPORTED_N(X)
 #undef X
     return 0;

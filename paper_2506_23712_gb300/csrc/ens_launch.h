@@ -27,6 +27,7 @@ __host__ __device__ inline int mix_pdf_len(const MixPdfArgs &a) { return a.nq * 
 bool supported_n(int N);
 int plan_threads(int N);
 int stats_blocks(int N);
+size_t stats_smem(int N, int nq, int nt, int ng);   // shared memory per CTA of the statistics pass
 cudaError_t prepare_kernels(int N, int nq, int nt, int ng);
 int znl_ctas_per_sm(int N, int var = 0);   // resident CTAs per SM of the persistent z pass (0 on error)
 bool zplan_variant_available(int N);       // the persistent z pass has a second warp plan for this size

@@ -205,10 +205,8 @@ void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, 
         }
         break;
     case Pass::ZSTAT: {
-        const long long rows = (long long)N * N;
-        const dim3 grid((unsigned)((rows + (long long)RZ * kStatsIters - 1) / ((long long)RZ * kStatsIters)),
-                        g.members);
-        k_z_stats<N><<<grid, TZ, smem_stats<N>(h->nq, h->nt, h->ng), s>>>(g, *h, md);
+        const dim3 grid((unsigned)stats_ctas<N>(), g.members);
+        k_z_stats<N><<<grid, 32 * SCfg<N>::WPB, smem_stats<N>(h->nq, h->nt, h->ng), s>>>(g, *h, md);
         break;
     }
     }

@@ -3,22 +3,32 @@
 // Input: the eight independent velocity-gradient components A_ij = d_j u_i
 // (ij = 11,12,13,21,22,23,31,32), already transformed along x and y (buffer
 // B); A_33 = -A_11 - A_22 by incompressibility.  Per grid point:
-//   Q = -1/2 Tr A^2, R = -1/3 Tr A^3            (Sec. V)
+//   Q = -1/2 Tr A^2, R = -1/3 Tr A^3 = -det A   (Sec. V; A traceless)
 //   eps = 2 nu Tr S^2, omega^2 = |omega|^2       (Sec. VI)
 // binned into the joint Q-R histogram (units q0 = eps_norm / (2 nu_norm)),
 // log10 histograms of eps/eps_norm and omega^2 nu_norm/eps_norm and, when
 // requested, linear histograms of the gradient components A_ij / sqrt(q0)
 // (longitudinal and transverse pooled separately, Sec. VI).  Bin rule:
 // bin b iff edge[b] <= x < edge[b+1] on FP32 edges (estimate from the affine
-// or log10 map, then corrected against the edge table, so the decision is
+// or log map, then corrected against the edge table, so the decision is
 // exactly the edge comparison).  Counts go to per-CTA shared-memory
 // histograms with warp-aggregated increments (__match_any_sync), flushed to
 // the member's uint64 counts once per CTA.  Moments: FP32 sums per thread
-// over its points, warp shuffle reduction, FP64 accumulation per warp and
-// per CTA, FP64 fixed-order reduction across CTAs.
+// (packed FP32x2 for the component pairs) over up to kStatsFlush rows, warp
+// shuffle reduction into FP64 per warp, FP64 fixed-order reduction across
+// warps and CTAs.
+//
+// Layout of the work: grid (stats_ctas<N>(), members); CTA c of member m
+// takes a contiguous block of rows, its warps stream over the row groups of
+// the block (32/P rows per group) and double-buffer their eight staged
+// half-spectrum rows in shared memory (cp.async.bulk, TMA; zero past the
+// kept modes), as the z pass of the RK stages does; the four Hermitian pair
+// lines go to physical space with the same warp-local transforms.
 #pragma once
 
 #include "ens_kernels.cuh"
+#include "ens_tma.cuh"
+#include "ens_znl.cuh"
 
 namespace ens {
 
@@ -37,7 +47,8 @@ __device__ __forceinline__ int bin_log(float x, float lo, float inv_w, const flo
 {
     if (!(x > 0.f) || x < e[0]) return -1;
     if (x >= e[n]) return n;
-    int b = (int)floorf((log10f(x) - lo) * inv_w);
+    // estimate from the hardware log2 (the edge comparisons below decide)
+    int b = (int)floorf((__log2f(x) * 0.30102999566f - lo) * inv_w);
     b = min(max(b, 0), n - 1);
     while (b > 0 && e[b] > x) --b;
     while (b < n - 1 && e[b + 1] <= x) ++b;
@@ -59,30 +70,76 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// Shape of the statistics pass: warps per CTA, staged row pitch, CTAs per member.
+template <int N>
+struct SCfg {
+    using PI = WPlanInfo<N>;
+    static constexpr int P = PI::P, V = PI::V, LPW = 32 / P;
+    static constexpr int NZ2 = (kc_of_n(N) + 2) / 2 * 2;     // copied row length (16-byte multiple)
+    static constexpr int PITCH = stage_pitch<N, 0>();        // staged row pitch, zero past NZ2
+    static constexpr int STAGE = LPW * 8 * PITCH;            // float2 per warp buffer
+    static constexpr bool PAD = WPad<N>::on;
+    static constexpr int SROW = PAD ? WPad<N>::SROW : RowCfg<N>::SROW;
+    static constexpr int WPB = N >= 512 ? 4 : 8;             // warps per CTA (shared memory)
+    static constexpr int GROUPS = N * N / LPW;               // row groups per member
+    // CTAs per member: up to 32, at least 32 row groups per warp
+    static constexpr int CTAS = GROUPS / (WPB * 32) >= 32 ? 32 : (GROUPS / (WPB * 32) >= 1 ? GROUPS / (WPB * 32) : 1);
+    static_assert(GROUPS % CTAS == 0, "row groups split evenly over the CTAs of a member");
+};
+
+// moment partials are flushed from FP32 registers to FP64 every kStatsFlush row groups
+constexpr int kStatsFlush = 32;
+
+template <int N>
+constexpr int stats_ctas() { return SCfg<N>::CTAS; }
+
 template <int N>
 constexpr size_t smem_stats(int nq, int nt, int ng)
 {
-    return smem_rows<N>() + sizeof(unsigned) * (size_t)counts_len_of(nq, nt, ng) +
-           sizeof(float) * (2 * (nq + 1) + nt + 1 + ng + 1) + sizeof(double) * 8 * kNMom + 64;
+    using C = SCfg<N>;
+    return sizeof(float2) * (size_t)N + sizeof(uint64_t) * 2 * C::WPB + sizeof(float2) * (size_t)C::WPB * 2 * C::STAGE +
+           sizeof(float2) * (size_t)C::WPB * C::LPW * C::SROW + sizeof(double) * C::WPB * kNMom +
+           sizeof(unsigned) * (size_t)counts_len_of(nq, nt, ng) + sizeof(float) * (2 * (nq + 1) + nt + 1 + ng + 1) + 16;
+}
+
+// packed FP32x2 helpers for the moment sums
+__device__ __forceinline__ float2 pmul(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2bits(a)), "l"(f2bits(b)));
+    return bitsf2(r);
+}
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2bits(a)), "l"(f2bits(b)), "l"(f2bits(c)));
+    return bitsf2(r);
 }
 
 template <int N>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(32 * SCfg<N>::WPB, 1)
 k_z_stats(Geo g, HistDev h, const MemberDev *md)
 {
+    using C = SCfg<N>;
     using PI = WPlanInfo<N>;
-    using RC = RowCfg<N>;
-    constexpr int P = PI::P, V = PI::V, RZ = RC::RZ;
-    extern __shared__ __align__(16) float2 sm[];
-    float2 *tw = sm, *buf = sm + N;
+    constexpr int P = C::P, V = C::V, LPW = C::LPW, NZ2 = C::NZ2, WPB = C::WPB;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *tw = reinterpret_cast<float2 *>(smraw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tw + N);
+    float2 *stage = reinterpret_cast<float2 *>(bars + 2 * WPB);
+    float2 *rows = stage + WPB * 2 * C::STAGE;
+    double *wmom = reinterpret_cast<double *>(rows + WPB * LPW * C::SROW);
+    unsigned *hist = reinterpret_cast<unsigned *>(wmom + WPB * kNMom);
     const int L = h.counts_len;
-    unsigned *hist = reinterpret_cast<unsigned *>(buf + RZ * RC::SROW);
     float *eq = reinterpret_cast<float *>(hist + L);
     float *er = eq + (h.nq + 1);
     float *et = er + (h.nq + 1);
     float *eg = et + (h.nt + 1);
-    double *wmom = reinterpret_cast<double *>(
-        (reinterpret_cast<uintptr_t>(eg + h.ng + 1) + 15) & ~(uintptr_t)15);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int line = lane / P, p = lane % P;
+    uint64_t *bar = bars + 2 * warp;
+    float2 *st = stage + warp * 2 * C::STAGE;
+    float2 *rowbuf = rows + warp * LPW * C::SROW;
     for (int i = threadIdx.x; i < L; i += blockDim.x) hist[i] = 0u;
     for (int i = threadIdx.x; i <= h.nq; i += blockDim.x) {
         eq[i] = h.edges_q[i];
@@ -90,79 +147,129 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     }
     for (int i = threadIdx.x; i <= h.nt; i += blockDim.x) et[i] = h.edges_t[i];
     for (int i = threadIdx.x; i <= h.ng && h.ng > 0; i += blockDim.x) eg[i] = h.edges_g[i];
-    for (int i = threadIdx.x; i < 8 * kNMom; i += blockDim.x) wmom[i] = 0.0;
-    load_twiddles(tw, g.tw, N);
+    for (int i = threadIdx.x; i < WPB * kNMom; i += blockDim.x) wmom[i] = 0.0;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    // zero tails of the staged rows (never written by the copies)
+    constexpr int TAIL = C::PITCH - NZ2;
+    if constexpr (TAIL > 0) {
+        for (int e = lane; e < 2 * LPW * 8 * TAIL; e += 32) st[(e / TAIL) * C::PITCH + NZ2 + e % TAIL] = make_float2(0.f, 0.f);
+    }
+    load_twiddles(tw, g.tw, N);   // block barrier: tables, barrier init and tails published
+    WarpTw<N> TW;
+    TW.init(p, tw);
 
-    const int p = threadIdx.x % P, r = threadIdx.x / P;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m = blockIdx.y;
     const float nu = (float)md[g.first + m].nu;
-    const long long nrows = (long long)N * N;
-    auto at = [&](int pos) { return row_slot<N>(buf, r, pos); };
+    constexpr int GPC = C::GROUPS / C::CTAS;   // row groups of this CTA
+    const long long g0 = (long long)blockIdx.x * GPC;
+    const uint32_t bytes = (uint32_t)(LPW * 8 * NZ2 * sizeof(float2));
+    const float2 *Bm = g.B + (long long)m * kFields * Dims<N>::SB;
+    auto issue = [&](int k, int b) {   // lane 0: row group g0 + k
+        const float2 *src = Bm + ((g0 + k) * LPW) * Dims<N>::NZP;
+        float2 *dst = st + b * C::STAGE;
+        mbar_arrive_expect_tx(&bar[b], bytes);
+#pragma unroll 1
+        for (int l = 0; l < LPW; ++l)
+#pragma unroll
+            for (int f = 0; f < 8; ++f)
+                bulk_g2s(dst + (l * 8 + f) * C::PITCH, src + f * Dims<N>::SB + l * Dims<N>::NZP,
+                         NZ2 * (uint32_t)sizeof(float2), &bar[b]);
+    };
+    int k = warp;
+    if (lane == 0 && k < GPC) issue(k, 0);
+
+    auto at = [&](int pos) { return row_slot<N>(rowbuf, line, pos); };
+    float2 *myrow = rowbuf + line * C::SROW;
     const int off_e = h.nq * h.nq, off_w = off_e + h.nt, off_c = off_w + h.nt;
     const int off_gl = off_c + 8, off_gt = off_gl + h.ng, off_gc = off_gt + h.ng;
-    int valid_rows = 0;
 
-#pragma unroll 1
-    for (int it = 0; it < kStatsIters; ++it) {
-        const long long rho = ((long long)blockIdx.x * kStatsIters + it) * RZ + r;
-        const bool row_ok = rho < nrows;
-        if (threadIdx.x == 0) {
-            const long long first_row = ((long long)blockIdx.x * kStatsIters + it) * RZ;
-            valid_rows += (int)max(0LL, min((long long)RZ, nrows - first_row));
-        }
-        const float2 *B = g.B + (long long)m * kFields * Dims<N>::SB + (row_ok ? rho : 0) * Dims<N>::NZP;
-        float2 v[4][V];
+    // FP32 moment partials: component pairs (2q, 2q + 1) packed, A_33 alone,
+    // invariant sums
+    float2 S2[4], S3[4], S4[4], S6[4];
+    float T2, T3, T4, T6;
+    float inv[8];
+    auto zero = [&]() {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) S2[q] = S3[q] = S4[q] = S6[q] = make_float2(0.f, 0.f);
+        T2 = T3 = T4 = T6 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) inv[q] = 0.f;
+    };
+    auto flush = [&]() {   // whole warp: FP32 partials -> FP64 per warp
+        float vals[kNMom - 4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-#pragma unroll
-            for (int i = 0; i < V; ++i)
-                v[q][i] = row_ok ? pair_at(B + (2 * q) * Dims<N>::SB, B + (2 * q + 1) * Dims<N>::SB, PI::in_pos(p, i), N, Dims<N>::KC)
-                                 : make_float2(0.f, 0.f);
-            fft_line_warp<N, false>(v[q], p, tw, at);
+            vals[4 * (2 * q) + 0] = S2[q].x; vals[4 * (2 * q) + 1] = S3[q].x; vals[4 * (2 * q) + 2] = S4[q].x; vals[4 * (2 * q) + 3] = S6[q].x;
+            vals[4 * (2 * q + 1) + 0] = S2[q].y; vals[4 * (2 * q + 1) + 1] = S3[q].y; vals[4 * (2 * q + 1) + 2] = S4[q].y; vals[4 * (2 * q + 1) + 3] = S6[q].y;
         }
-        float sQ = 0.f, sR = 0.f, sE = 0.f, sW = 0.f, sQ2 = 0.f, sR2 = 0.f, sE2 = 0.f, sW2 = 0.f;
+        vals[32] = T2; vals[33] = T3; vals[34] = T4; vals[35] = T6;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) vals[36 + q] = inv[q];
+#pragma unroll
+        for (int q = 0; q < kNMom - 4; ++q) {
+            const float s = warp_sum(vals[q]);
+            if (lane == 0) wmom[warp * kNMom + q] += (double)s;
+        }
+        zero();
+    };
+    zero();
+
+    bool timed_out = false;
+    int it = 0;
+    for (; k < GPC; ++it, k += WPB) {
+        const int b = it & 1;
+        if (lane == 0 && k + WPB < GPC) {
+            fence_proxy_async_smem();   // this buffer's earlier reads precede the refill
+            issue(k + WPB, b ^ 1);
+        }
+        if (!mbar_wait_warp(&bar[b], (uint32_t)((it >> 1) & 1))) {
+            timed_out = true;
+            break;
+        }
+        const float2 *X = st + b * C::STAGE + line * 8 * C::PITCH;
+        constexpr int R = C::PITCH;
+        float2 v[4][V];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) PairSlots<N, 0, 0>::load(v[q], X + 2 * q * R, X + (2 * q + 1) * R, p);
+        __syncwarp();   // staged rows read: the buffer may be refilled
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if constexpr (C::PAD) fft_line_warp_pad<N, false>(v[q], p, TW, myrow);
+            else fft_line_warp_tw<N, false>(v[q], p, TW, at);
+        }
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const float a11 = v[0][i].x, a12 = v[0][i].y, a13 = v[1][i].x, a21 = v[1][i].y;
             const float a22 = v[2][i].x, a23 = v[2][i].y, a31 = v[3][i].x, a32 = v[3][i].y;
             const float a33 = -a11 - a22;
-            const float A[3][3] = {{a11, a12, a13}, {a21, a22, a23}, {a31, a32, a33}};
-            float tr2 = 0.f, tr3 = 0.f;
-#pragma unroll
-            for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-                for (int jj = 0; jj < 3; ++jj) {
-                    tr2 = fmaf(A[ii][jj], A[jj][ii], tr2);
-                    float b = 0.f;   // (A^2)_ij
-#pragma unroll
-                    for (int kk = 0; kk < 3; ++kk) b = fmaf(A[ii][kk], A[kk][jj], b);
-                    tr3 = fmaf(b, A[jj][ii], tr3);
-                }
+            // traceless A: Tr A^2 = sum_ij a_ij a_ji, Tr A^3 = 3 det A
+            const float tr2 = a11 * a11 + a22 * a22 + a33 * a33 + 2.f * (a12 * a21 + a13 * a31 + a23 * a32);
+            const float det = a11 * (a22 * a33 - a23 * a32) - a12 * (a21 * a33 - a23 * a31) + a13 * (a21 * a32 - a22 * a31);
             const float s12 = 0.5f * (a12 + a21), s13 = 0.5f * (a13 + a31), s23 = 0.5f * (a23 + a32);
             const float ss = a11 * a11 + a22 * a22 + a33 * a33 + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
             const float wx = a32 - a23, wy = a13 - a31, wz = a21 - a12;
-            const float Q = -0.5f * tr2, R = -tr3 * (1.f / 3.f);
+            const float Q = -0.5f * tr2, R3 = -det;
             const float eps = 2.f * nu * ss, ens = wx * wx + wy * wy + wz * wz;
-            if (row_ok) {
-                sQ += Q; sR += R; sE += eps; sW += ens;
-                sQ2 += Q * Q; sR2 += R * R; sE2 += eps * eps; sW2 += ens * ens;
-            }
-            const float xq = Q * h.q_scale, xr = R * h.r_scale, xe = eps * h.eps_scale, xw = ens * h.ens_scale;
+            inv[0] += Q; inv[1] += R3; inv[2] += eps; inv[3] += ens;
+            inv[4] = fmaf(Q, Q, inv[4]); inv[5] = fmaf(R3, R3, inv[5]);
+            inv[6] = fmaf(eps, eps, inv[6]); inv[7] = fmaf(ens, ens, inv[7]);
+            const float xq = Q * h.q_scale, xr = R3 * h.r_scale, xe = eps * h.eps_scale, xw = ens * h.ens_scale;
             const bool finite = isfinite(xq) && isfinite(xr) && isfinite(xe) && isfinite(xw);
-            int kq = -1, ke = -1, kw = -1;
-            if (row_ok) {
-                if (!finite) {
-                    kq = off_c + 5;
-                } else {
-                    const int bq = bin_lin(xq, h.q_lo, h.q_inv_w, eq, h.nq);
-                    const int br = bin_lin(xr, h.r_lo, h.r_inv_w, er, h.nq);
-                    kq = (bq >= 0 && bq < h.nq && br >= 0 && br < h.nq) ? bq * h.nq + br : off_c + 0;
-                    const int be = bin_log(xe, h.t_lo, h.t_inv_w, et, h.nt);
-                    ke = be < 0 ? off_c + 1 : (be >= h.nt ? off_c + 2 : off_e + be);
-                    const int bw = bin_log(xw, h.t_lo, h.t_inv_w, et, h.nt);
-                    kw = bw < 0 ? off_c + 3 : (bw >= h.nt ? off_c + 4 : off_w + bw);
-                }
+            int kq, ke = -1, kw = -1;
+            if (!finite) {
+                kq = off_c + 5;
+            } else {
+                const int bq = bin_lin(xq, h.q_lo, h.q_inv_w, eq, h.nq);
+                const int br = bin_lin(xr, h.r_lo, h.r_inv_w, er, h.nq);
+                kq = (bq >= 0 && bq < h.nq && br >= 0 && br < h.nq) ? bq * h.nq + br : off_c + 0;
+                const int be = bin_log(xe, h.t_lo, h.t_inv_w, et, h.nt);
+                ke = be < 0 ? off_c + 1 : (be >= h.nt ? off_c + 2 : off_e + be);
+                const int bw = bin_log(xw, h.t_lo, h.t_inv_w, et, h.nt);
+                kw = bw < 0 ? off_c + 3 : (bw >= h.nt ? off_c + 4 : off_w + bw);
             }
             warp_count(hist, kq);
             warp_count(hist, ke);
@@ -170,12 +277,12 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
             if (h.ng > 0) {
                 // gradient components (longitudinal c = 0, 4, 8 pooled; the
                 // six transverse ones pooled), finite points only
+                const float A[9] = {a11, a12, a13, a21, a22, a23, a31, a32, a33};
 #pragma unroll
                 for (int c = 0; c < 9; ++c) {
                     int kg = -1;
-                    if (row_ok && finite) {
-                        const float x = A[c / 3][c % 3] * h.g_scale;
-                        const int bg = bin_lin(x, h.g_lo, h.g_inv_w, eg, h.ng);
+                    if (finite) {
+                        const int bg = bin_lin(A[c] * h.g_scale, h.g_lo, h.g_inv_w, eg, h.ng);
                         const bool lon = c % 4 == 0;
                         kg = bg < 0 ? off_gc + (lon ? 0 : 2)
                                     : (bg >= h.ng ? off_gc + (lon ? 1 : 3) : (lon ? off_gl : off_gt) + bg);
@@ -183,60 +290,39 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
                     warp_count(hist, kg);
                 }
             }
-        }
-        // moments: sums of A_c^p (p = 2, 3, 4, 6) and of the invariants
-        const float inv_vals[8] = {sQ, sR, sE, sW, sQ2, sR2, sE2, sW2};
+            // moments of the components: sums of A_c^p, p = 2, 3, 4, 6
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float s = warp_sum(inv_vals[q]);
-            if (lane == 0) wmom[warp * kNMom + 36 + q] += (double)s;
-        }
-#pragma unroll
-        for (int comp = 0; comp < 9; ++comp) {
-            float s2 = 0.f, s3 = 0.f, s4 = 0.f, s6 = 0.f;
-            if (row_ok) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    float a;
-                    switch (comp) {
-                    case 0: a = v[0][i].x; break;
-                    case 1: a = v[0][i].y; break;
-                    case 2: a = v[1][i].x; break;
-                    case 3: a = v[1][i].y; break;
-                    case 4: a = v[2][i].x; break;
-                    case 5: a = v[2][i].y; break;
-                    case 6: a = v[3][i].x; break;
-                    case 7: a = v[3][i].y; break;
-                    default: a = -v[0][i].x - v[2][i].x; break;
-                    }
-                    const float a2 = a * a;
-                    s2 += a2;
-                    s3 = fmaf(a2, a, s3);
-                    s4 = fmaf(a2, a2, s4);
-                    s6 = fmaf(a2 * a2, a2, s6);
-                }
+            for (int q = 0; q < 4; ++q) {
+                const float2 a = v[q][i];
+                const float2 a2 = pmul(a, a);
+                const float2 a4 = pmul(a2, a2);
+                S2[q] = cadd_x2(S2[q], a2);
+                S3[q] = pfma(a2, a, S3[q]);
+                S4[q] = cadd_x2(S4[q], a4);
+                S6[q] = pfma(a4, a2, S6[q]);
             }
-            s2 = warp_sum(s2);
-            s3 = warp_sum(s3);
-            s4 = warp_sum(s4);
-            s6 = warp_sum(s6);
-            if (lane == 0) {
-                double *w = wmom + warp * kNMom + 4 * comp;
-                w[0] += (double)s2;
-                w[1] += (double)s3;
-                w[2] += (double)s4;
-                w[3] += (double)s6;
-            }
+            const float b2 = a33 * a33;
+            T2 += b2;
+            T3 = fmaf(b2, a33, T3);
+            T4 = fmaf(b2, b2, T4);
+            T6 = fmaf(b2 * b2, b2, T6);
         }
+        if ((it + 1) % kStatsFlush == 0) flush();
+    }
+    flush();
+    if (timed_out) {
+        if (lane == 0) atomicOr(const_cast<int *>(&md[g.first + m].flags), kFlagTimeout);
+        // the refill of the other buffer may still be in flight: wait for it (bounded)
+        if (k + WPB < GPC) mbar_wait_warp(&bar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
     }
     __syncthreads();
     unsigned long long *cnt = g.counts + (long long)(g.first + m) * L;
     for (int i = threadIdx.x; i < L; i += blockDim.x)
         if (hist[i]) atomicAdd(&cnt[i], (unsigned long long)hist[i]);
-    if (threadIdx.x == 0) atomicAdd(&cnt[off_c + 6], (unsigned long long)valid_rows * N);
+    if (threadIdx.x == 0) atomicAdd(&cnt[off_c + 6], (unsigned long long)GPC * LPW * N);
     if (threadIdx.x < kNMom) {
         double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wmom[w * kNMom + threadIdx.x];
+        for (int w = 0; w < WPB; ++w) s += wmom[w * kNMom + threadIdx.x];
         g.mom_partial[((long long)(g.first + m) * g.mom_blocks + blockIdx.x) * kNMom + threadIdx.x] = s;
     }
 }
