@@ -10,7 +10,7 @@
 // requested, linear histograms of the gradient components A_ij / sqrt(q0)
 // (longitudinal and transverse pooled separately, Sec. VI).  Bin rule:
 // bin b iff edge[b] <= x < edge[b+1] on FP32 edges (estimate from the affine
-// or log map, then corrected against the edge table, so the decision is
+// or log map; near an edge the edge table decides, so the decision is
 // exactly the edge comparison).  Counts go to per-CTA shared-memory
 // histograms with warp-aggregated increments (__match_any_sync), flushed to
 // the member's uint64 counts once per CTA.  Moments: FP32 sums per thread
@@ -53,6 +53,27 @@ __device__ __forceinline__ int bin_log(float x, float lo, float inv_w, const flo
     while (b > 0 && e[b] > x) --b;
     while (b < n - 1 && e[b + 1] <= x) ++b;
     return b;
+}
+
+// Bin of x from its estimated bin coordinate t (affine or log map): away
+// from every edge (1e-3 of a bin, far above the estimate's error) the
+// estimate decides; near an edge, or out of range, the edge table does.
+__device__ __forceinline__ int bin_lin_fast(float x, float lo, float inv_w, const float *e, int n)
+{
+    const float t = (x - lo) * inv_w;
+    const float fl = floorf(t), f = t - fl;
+    if (t >= 0.001f && t < (float)n - 0.001f && f > 0.001f && f < 0.999f) return (int)fl;
+    return bin_lin(x, lo, inv_w, e, n);
+}
+
+__device__ __forceinline__ int bin_log_fast(float x, float lo, float inv_w, const float *e, int n)
+{
+    if (x > 0.f) {
+        const float t = (__log2f(x) * 0.30102999566f - lo) * inv_w;
+        const float fl = floorf(t), f = t - fl;
+        if (t >= 0.001f && t < (float)n - 0.001f && f > 0.001f && f < 0.999f) return (int)fl;
+    }
+    return bin_log(x, lo, inv_w, e, n);
 }
 
 // warp-aggregated increment of hist[key] (key < 0: no increment)
@@ -263,12 +284,12 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
             if (!finite) {
                 kq = off_c + 5;
             } else {
-                const int bq = bin_lin(xq, h.q_lo, h.q_inv_w, eq, h.nq);
-                const int br = bin_lin(xr, h.r_lo, h.r_inv_w, er, h.nq);
+                const int bq = bin_lin_fast(xq, h.q_lo, h.q_inv_w, eq, h.nq);
+                const int br = bin_lin_fast(xr, h.r_lo, h.r_inv_w, er, h.nq);
                 kq = (bq >= 0 && bq < h.nq && br >= 0 && br < h.nq) ? bq * h.nq + br : off_c + 0;
-                const int be = bin_log(xe, h.t_lo, h.t_inv_w, et, h.nt);
+                const int be = bin_log_fast(xe, h.t_lo, h.t_inv_w, et, h.nt);
                 ke = be < 0 ? off_c + 1 : (be >= h.nt ? off_c + 2 : off_e + be);
-                const int bw = bin_log(xw, h.t_lo, h.t_inv_w, et, h.nt);
+                const int bw = bin_log_fast(xw, h.t_lo, h.t_inv_w, et, h.nt);
                 kw = bw < 0 ? off_c + 3 : (bw >= h.nt ? off_c + 4 : off_w + bw);
             }
             warp_count(hist, kq);
@@ -282,7 +303,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
                 for (int c = 0; c < 9; ++c) {
                     int kg = -1;
                     if (finite) {
-                        const int bg = bin_lin(A[c] * h.g_scale, h.g_lo, h.g_inv_w, eg, h.ng);
+                        const int bg = bin_lin_fast(A[c] * h.g_scale, h.g_lo, h.g_inv_w, eg, h.ng);
                         const bool lon = c % 4 == 0;
                         kg = bg < 0 ? off_gc + (lon ? 0 : 2)
                                     : (bg >= h.ng ? off_gc + (lon ? 1 : 3) : (lon ? off_gl : off_gt) + bg);
