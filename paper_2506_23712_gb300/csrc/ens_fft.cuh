@@ -512,6 +512,24 @@ __device__ __forceinline__ void exchange_warp_pad(float2 *v, int p, float2 *row)
     }
 }
 
+// The same with the inter-pass twiddles read from the shared table (fewer
+// registers held across the transforms).
+template <int N, bool FWD>
+__device__ __forceinline__ void fft_line_warp_pad_tab(float2 *v, int p, const float2 *__restrict__ tw, float2 *row)
+{
+    using PI = WPlanInfo<N, 0>;
+    using PD = WPadV<N, 0>;
+    static_assert(PD::on && PI::NP <= 3, "padded layouts exist for the power-of-two plans");
+    constexpr int P = PI::P, R0 = PI::R0, R1 = PI::R1, R2 = PI::R2;
+    pass_regs<N, R0, 1, P, FWD, true>(v, p, tw);
+    exchange_warp_pad<N, R0, 1, R1, P, PD::A0, PD::D0>(v, p, row);
+    pass_regs<N, R1, R0, P, FWD, true>(v, p, tw);
+    if constexpr (PI::NP == 3) {
+        exchange_warp_pad<N, R1, R0, R2, P, PD::A1, PD::D1>(v, p, row);
+        pass_regs<N, R2, R0 * R1, P, FWD, true>(v, p, tw);
+    }
+}
+
 // Line transform of a warp plan through the padded layouts; row is this
 // line's shared row (WPadV<N, VAR>::SROW slots).
 template <int N, bool FWD, int VAR = 0>

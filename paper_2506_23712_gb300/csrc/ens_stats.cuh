@@ -20,10 +20,13 @@
 //
 // Layout of the work: grid (stats_ctas<N>(), members); CTA c of member m
 // takes a contiguous block of rows, its warps stream over the row groups of
-// the block (32/P rows per group) and double-buffer their eight staged
-// half-spectrum rows in shared memory (cp.async.bulk, TMA; zero past the
-// kept modes), as the z pass of the RK stages does; the four Hermitian pair
-// lines go to physical space with the same warp-local transforms.
+// the block (32/P rows per group).  A warp stages the eight half-spectrum
+// rows of a group in shared memory (cp.async.bulk, TMA; zero past the kept
+// modes), reads them into registers, and refills the same buffer with the
+// next group while it transforms and bins the current one (the work per
+// group far outlasts the copy); the four Hermitian pair lines go to physical
+// space with the z pass's warp-local transforms, twiddles read from the
+// shared table (registers go to more resident warps).
 #pragma once
 
 #include "ens_kernels.cuh"
@@ -98,13 +101,16 @@ struct SCfg {
     static constexpr int P = PI::P, V = PI::V, LPW = 32 / P;
     static constexpr int NZ2 = (kc_of_n(N) + 2) / 2 * 2;     // copied row length (16-byte multiple)
     static constexpr int PITCH = stage_pitch<N, 0>();        // staged row pitch, zero past NZ2
-    static constexpr int STAGE = LPW * 8 * PITCH;            // float2 per warp buffer
+    static constexpr int STAGE = LPW * 8 * PITCH;            // float2 per warp (one buffer)
     static constexpr bool PAD = WPad<N>::on;
     static constexpr int SROW = PAD ? WPad<N>::SROW : RowCfg<N>::SROW;
-    static constexpr int WPB = N >= 512 ? 4 : 8;             // warps per CTA (shared memory)
+    // warps per CTA: 12 where the plan's four lines fit the register share
+    // of 12 resident warps, 8 for the 12- and 16-value plans (384, 512)
+    static constexpr int WPB = V > 8 ? 8 : 12;
     static constexpr int GROUPS = N * N / LPW;               // row groups per member
-    // CTAs per member: up to 32, at least 32 row groups per warp
-    static constexpr int CTAS = GROUPS / (WPB * 32) >= 32 ? 32 : (GROUPS / (WPB * 32) >= 1 ? GROUPS / (WPB * 32) : 1);
+    // CTAs per member: a power of two up to 32, at least 32 row groups per warp
+    static constexpr int pow2_floor(int x) { return x >= 32 ? 32 : x >= 16 ? 16 : x >= 8 ? 8 : x >= 4 ? 4 : x >= 2 ? 2 : 1; }
+    static constexpr int CTAS = pow2_floor(GROUPS / (WPB * 32));
     static_assert(GROUPS % CTAS == 0, "row groups split evenly over the CTAs of a member");
 };
 
@@ -118,7 +124,7 @@ template <int N>
 constexpr size_t smem_stats(int nq, int nt, int ng)
 {
     using C = SCfg<N>;
-    return sizeof(float2) * (size_t)N + sizeof(uint64_t) * 2 * C::WPB + sizeof(float2) * (size_t)C::WPB * 2 * C::STAGE +
+    return sizeof(float2) * (size_t)N + sizeof(uint64_t) * 2 * C::WPB + sizeof(float2) * (size_t)C::WPB * C::STAGE +
            sizeof(float2) * (size_t)C::WPB * C::LPW * C::SROW + sizeof(double) * C::WPB * kNMom +
            sizeof(unsigned) * (size_t)counts_len_of(nq, nt, ng) + sizeof(float) * (2 * (nq + 1) + nt + 1 + ng + 1) + 16;
 }
@@ -148,7 +154,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     float2 *tw = reinterpret_cast<float2 *>(smraw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(tw + N);
     float2 *stage = reinterpret_cast<float2 *>(bars + 2 * WPB);
-    float2 *rows = stage + WPB * 2 * C::STAGE;
+    float2 *rows = stage + WPB * C::STAGE;
     double *wmom = reinterpret_cast<double *>(rows + WPB * LPW * C::SROW);
     unsigned *hist = reinterpret_cast<unsigned *>(wmom + WPB * kNMom);
     const int L = h.counts_len;
@@ -159,7 +165,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int line = lane / P, p = lane % P;
     uint64_t *bar = bars + 2 * warp;
-    float2 *st = stage + warp * 2 * C::STAGE;
+    float2 *st = stage + warp * C::STAGE;
     float2 *rowbuf = rows + warp * LPW * C::SROW;
     for (int i = threadIdx.x; i < L; i += blockDim.x) hist[i] = 0u;
     for (int i = threadIdx.x; i <= h.nq; i += blockDim.x) {
@@ -171,17 +177,14 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     for (int i = threadIdx.x; i < WPB * kNMom; i += blockDim.x) wmom[i] = 0.0;
     if (lane == 0) {
         mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
     // zero tails of the staged rows (never written by the copies)
     constexpr int TAIL = C::PITCH - NZ2;
     if constexpr (TAIL > 0) {
-        for (int e = lane; e < 2 * LPW * 8 * TAIL; e += 32) st[(e / TAIL) * C::PITCH + NZ2 + e % TAIL] = make_float2(0.f, 0.f);
+        for (int e = lane; e < LPW * 8 * TAIL; e += 32) st[(e / TAIL) * C::PITCH + NZ2 + e % TAIL] = make_float2(0.f, 0.f);
     }
     load_twiddles(tw, g.tw, N);   // block barrier: tables, barrier init and tails published
-    WarpTw<N> TW;
-    TW.init(p, tw);
 
     const int m = blockIdx.y;
     const float nu = (float)md[g.first + m].nu;
@@ -189,19 +192,19 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     const long long g0 = (long long)blockIdx.x * GPC;
     const uint32_t bytes = (uint32_t)(LPW * 8 * NZ2 * sizeof(float2));
     const float2 *Bm = g.B + (long long)m * kFields * Dims<N>::SB;
-    auto issue = [&](int k, int b) {   // lane 0: row group g0 + k
+    auto issue = [&](int k) {   // lane 0: row group g0 + k
         const float2 *src = Bm + ((g0 + k) * LPW) * Dims<N>::NZP;
-        float2 *dst = st + b * C::STAGE;
-        mbar_arrive_expect_tx(&bar[b], bytes);
+        float2 *dst = st;
+        mbar_arrive_expect_tx(&bar[0], bytes);
 #pragma unroll 1
         for (int l = 0; l < LPW; ++l)
 #pragma unroll
             for (int f = 0; f < 8; ++f)
                 bulk_g2s(dst + (l * 8 + f) * C::PITCH, src + f * Dims<N>::SB + l * Dims<N>::NZP,
-                         NZ2 * (uint32_t)sizeof(float2), &bar[b]);
+                         NZ2 * (uint32_t)sizeof(float2), &bar[0]);
     };
     int k = warp;
-    if (lane == 0 && k < GPC) issue(k, 0);
+    if (lane == 0 && k < GPC) issue(k);
 
     auto at = [&](int pos) { return row_slot<N>(rowbuf, line, pos); };
     float2 *myrow = rowbuf + line * C::SROW;
@@ -242,25 +245,24 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     bool timed_out = false;
     int it = 0;
     for (; k < GPC; ++it, k += WPB) {
-        const int b = it & 1;
-        if (lane == 0 && k + WPB < GPC) {
-            fence_proxy_async_smem();   // this buffer's earlier reads precede the refill
-            issue(k + WPB, b ^ 1);
-        }
-        if (!mbar_wait_warp(&bar[b], (uint32_t)((it >> 1) & 1))) {
+        if (!mbar_wait_warp(&bar[0], (uint32_t)(it & 1))) {
             timed_out = true;
             break;
         }
-        const float2 *X = st + b * C::STAGE + line * 8 * C::PITCH;
+        const float2 *X = st + line * 8 * C::PITCH;
         constexpr int R = C::PITCH;
         float2 v[4][V];
 #pragma unroll
         for (int q = 0; q < 4; ++q) PairSlots<N, 0, 0>::load(v[q], X + 2 * q * R, X + (2 * q + 1) * R, p);
-        __syncwarp();   // staged rows read: the buffer may be refilled
+        __syncwarp();   // staged rows read: the buffer takes the next group
+        if (lane == 0 && k + WPB < GPC) {
+            fence_proxy_async_smem();   // the reads above precede the refill
+            issue(k + WPB);
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if constexpr (C::PAD) fft_line_warp_pad<N, false>(v[q], p, TW, myrow);
-            else fft_line_warp_tw<N, false>(v[q], p, TW, at);
+            if constexpr (C::PAD) fft_line_warp_pad_tab<N, false>(v[q], p, tw, myrow);
+            else fft_line_warp<N, false>(v[q], p, tw, at);
         }
 #pragma unroll
         for (int i = 0; i < V; ++i) {
@@ -333,8 +335,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     flush();
     if (timed_out) {
         if (lane == 0) atomicOr(const_cast<int *>(&md[g.first + m].flags), kFlagTimeout);
-        // the refill of the other buffer may still be in flight: wait for it (bounded)
-        if (k + WPB < GPC) mbar_wait_warp(&bar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        mbar_wait_warp(&bar[0], (uint32_t)(it & 1));   // the copy in flight, once more (bounded)
     }
     __syncthreads();
     unsigned long long *cnt = g.counts + (long long)(g.first + m) * L;
