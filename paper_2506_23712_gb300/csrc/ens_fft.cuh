@@ -512,21 +512,64 @@ __device__ __forceinline__ void exchange_warp_pad(float2 *v, int p, float2 *row)
     }
 }
 
-// The same with the inter-pass twiddles read from the shared table (fewer
-// registers held across the transforms).
+// Inter-pass twiddles of a warp plan in shared memory, lane-major: entry
+// (pass s, butterfly b, slot t) of lane p at [offset_s + (b (R - 1) + t - 1)
+// P + p], the value WarpTw holds in registers.  A warp's request for one
+// (s, b, t) reads P consecutive entries: no bank conflicts.  Fewer registers
+// are held across the transforms than with WarpTw.
+template <int N>
+struct LaneTw {
+    using PI = WPlanInfo<N, 0>;
+    static constexpr int P = PI::P, R0 = PI::R0, R1 = PI::R1, R2 = PI::R2;
+    static constexpr int B1 = N / (R1 * P), B2 = PI::NP >= 3 ? N / (R2 * P) : 0;
+    static constexpr int OFF2 = B1 * (R1 - 1) * P;
+    static constexpr int SIZE = OFF2 + (PI::NP >= 3 ? B2 * (R2 - 1) * P : 0);   // float2
+    // whole block; tw: the N-entry table W_N^m
+    static __device__ __forceinline__ void init(float2 *tab, const float2 *tw)
+    {
+        for (int i = threadIdx.x; i < SIZE; i += blockDim.x) {
+            const bool second = i >= OFF2;
+            const int j = second ? i - OFF2 : i;
+            const int R = second ? R2 : R1, Ns = second ? R0 * R1 : R0;
+            const int p = j % P, bt = j / P, b = bt / (R - 1), t = bt % (R - 1) + 1;
+            const int k = (p + b * P) % Ns;
+            tab[i] = tw[t * k * (N / (Ns * R))];
+        }
+    }
+};
+
+template <int N, int R, int Ns, int P, bool FWD, bool PK>
+__device__ __forceinline__ void pass_regs_lt(float2 *v, const float2 *__restrict__ lt)
+{
+    constexpr int B = N / (R * P);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+#pragma unroll
+        for (int t = 1; t < R; ++t) {
+            float2 w = lt[(b * (R - 1) + t - 1) * P];
+            if (!FWD) w.y = -w.y;
+            v[b * R + t] = cmul(v[b * R + t], w);
+        }
+        Dft<R, FWD, PK>::run(&v[b * R]);
+    }
+}
+
+// Line transform of the default warp plan through the padded layouts with
+// the lane-major shared twiddles (tab: LaneTw<N> table).
 template <int N, bool FWD>
-__device__ __forceinline__ void fft_line_warp_pad_tab(float2 *v, int p, const float2 *__restrict__ tw, float2 *row)
+__device__ __forceinline__ void fft_line_warp_pad_lt(float2 *v, int p, const float2 *__restrict__ tab, float2 *row)
 {
     using PI = WPlanInfo<N, 0>;
     using PD = WPadV<N, 0>;
+    using LT = LaneTw<N>;
     static_assert(PD::on && PI::NP <= 3, "padded layouts exist for the power-of-two plans");
     constexpr int P = PI::P, R0 = PI::R0, R1 = PI::R1, R2 = PI::R2;
-    pass_regs<N, R0, 1, P, FWD, true>(v, p, tw);
+    pass_regs<N, R0, 1, P, FWD, true>(v, p, nullptr);
     exchange_warp_pad<N, R0, 1, R1, P, PD::A0, PD::D0>(v, p, row);
-    pass_regs<N, R1, R0, P, FWD, true>(v, p, tw);
+    pass_regs_lt<N, R1, R0, P, FWD, true>(v, tab + p);
     if constexpr (PI::NP == 3) {
         exchange_warp_pad<N, R1, R0, R2, P, PD::A1, PD::D1>(v, p, row);
-        pass_regs<N, R2, R0 * R1, P, FWD, true>(v, p, tw);
+        pass_regs_lt<N, R2, R0 * R1, P, FWD, true>(v, tab + LT::OFF2 + p);
     }
 }
 

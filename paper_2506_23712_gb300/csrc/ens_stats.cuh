@@ -25,8 +25,8 @@
 // modes), reads them into registers, and refills the same buffer with the
 // next group while it transforms and bins the current one (the work per
 // group far outlasts the copy); the four Hermitian pair lines go to physical
-// space with the z pass's warp-local transforms, twiddles read from the
-// shared table (registers go to more resident warps).
+// space with the z pass's warp-local transforms, their twiddles read from a
+// lane-major shared table (registers go to more resident warps).
 #pragma once
 
 #include "ens_kernels.cuh"
@@ -108,6 +108,7 @@ struct SCfg {
     // of 12 resident warps, 8 for the 12- and 16-value plans (384, 512)
     static constexpr int WPB = V > 8 ? 8 : 12;
     static constexpr int GROUPS = N * N / LPW;               // row groups per member
+    static constexpr int LT = PAD ? (LaneTw<N>::SIZE + 1) / 2 * 2 : 0;   // lane-major twiddles (float2)
     // CTAs per member: a power of two up to 32, at least 32 row groups per warp
     static constexpr int pow2_floor(int x) { return x >= 32 ? 32 : x >= 16 ? 16 : x >= 8 ? 8 : x >= 4 ? 4 : x >= 2 ? 2 : 1; }
     static constexpr int CTAS = pow2_floor(GROUPS / (WPB * 32));
@@ -124,7 +125,7 @@ template <int N>
 constexpr size_t smem_stats(int nq, int nt, int ng)
 {
     using C = SCfg<N>;
-    return sizeof(float2) * (size_t)N + sizeof(uint64_t) * 2 * C::WPB + sizeof(float2) * (size_t)C::WPB * C::STAGE +
+    return sizeof(float2) * (size_t)(N + C::LT) + sizeof(uint64_t) * 2 * C::WPB + sizeof(float2) * (size_t)C::WPB * C::STAGE +
            sizeof(float2) * (size_t)C::WPB * C::LPW * C::SROW + sizeof(double) * C::WPB * kNMom +
            sizeof(unsigned) * (size_t)counts_len_of(nq, nt, ng) + sizeof(float) * (2 * (nq + 1) + nt + 1 + ng + 1) + 16;
 }
@@ -152,7 +153,8 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     constexpr int P = C::P, V = C::V, LPW = C::LPW, NZ2 = C::NZ2, WPB = C::WPB;
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *tw = reinterpret_cast<float2 *>(smraw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tw + N);
+    float2 *ltw = tw + N;   // lane-major inter-pass twiddles (padded plans)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ltw + C::LT);
     float2 *stage = reinterpret_cast<float2 *>(bars + 2 * WPB);
     float2 *rows = stage + WPB * C::STAGE;
     double *wmom = reinterpret_cast<double *>(rows + WPB * LPW * C::SROW);
@@ -184,6 +186,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     if constexpr (TAIL > 0) {
         for (int e = lane; e < LPW * 8 * TAIL; e += 32) st[(e / TAIL) * C::PITCH + NZ2 + e % TAIL] = make_float2(0.f, 0.f);
     }
+    if constexpr (C::PAD) LaneTw<N>::init(ltw, g.tw);
     load_twiddles(tw, g.tw, N);   // block barrier: tables, barrier init and tails published
 
     const int m = blockIdx.y;
@@ -261,7 +264,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if constexpr (C::PAD) fft_line_warp_pad_tab<N, false>(v[q], p, tw, myrow);
+            if constexpr (C::PAD) fft_line_warp_pad_lt<N, false>(v[q], p, ltw, myrow);
             else fft_line_warp<N, false>(v[q], p, tw, at);
         }
 #pragma unroll
