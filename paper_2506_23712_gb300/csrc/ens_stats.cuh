@@ -12,8 +12,9 @@
 // bin b iff edge[b] <= x < edge[b+1] on FP32 edges (estimate from the affine
 // or log map; near an edge the edge table decides, so the decision is
 // exactly the edge comparison).  Counts go to per-CTA shared-memory
-// histograms with warp-aggregated increments (__match_any_sync), flushed to
-// the member's uint64 counts once per CTA.  Moments: FP32 sums per thread
+// histograms (plain shared atomics for the Q-R and tail histograms,
+// warp-aggregated increments for the gradient components), flushed to the
+// member's uint64 counts once per CTA.  Moments: FP32 sums per thread
 // (packed FP32x2 for the component pairs) over up to kStatsFlush rows, warp
 // shuffle reduction into FP64 per warp, FP64 fixed-order reduction across
 // warps and CTAs.
@@ -77,6 +78,12 @@ __device__ __forceinline__ int bin_log_fast(float x, float lo, float inv_w, cons
         if (t >= 0.001f && t < (float)n - 0.001f && f > 0.001f && f < 0.999f) return (int)fl;
     }
     return bin_log(x, lo, inv_w, e, n);
+}
+
+// increment of hist[key] without aggregation (key < 0: none)
+__device__ __forceinline__ void lane_count(unsigned *hist, int key)
+{
+    if (key >= 0) atomicAdd(&hist[key], 1u);
 }
 
 // warp-aggregated increment of hist[key] (key < 0: no increment)
@@ -297,9 +304,9 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
                 const int bw = bin_log_fast(xw, h.t_lo, h.t_inv_w, et, h.nt);
                 kw = bw < 0 ? off_c + 3 : (bw >= h.nt ? off_c + 4 : off_w + bw);
             }
-            warp_count(hist, kq);
-            warp_count(hist, ke);
-            warp_count(hist, kw);
+            lane_count(hist, kq);
+            lane_count(hist, ke);
+            lane_count(hist, kw);
             if (h.ng > 0) {
                 // gradient components (longitudinal c = 0, 4, 8 pooled; the
                 // six transverse ones pooled), finite points only
