@@ -62,6 +62,41 @@ def parse():
     return p.parse_args()
 
 
+def parse_cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        else:
+            cpus.add(int(part))
+    return cpus
+
+
+def bind_host_to_gpu(local_rank):
+    """Run this process on the CPU cores local to the GPU (sysfs local_cpulist
+    of its PCI function), so that the page-locked buffers of the end-to-end
+    measurement are allocated in the memory next to it.  Returns what was
+    done, for the JSON line."""
+    try:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        idx = vis.split(",")[local_rank] if vis else str(local_rank)
+        out = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i", idx],
+                             capture_output=True, text=True, timeout=30).stdout.strip().lower()
+        dom, rest = out.split(":", 1)
+        path = "/sys/bus/pci/devices/%04x:%s/local_cpulist" % (int(dom, 16), rest)
+        with open(path) as f:
+            cpus = parse_cpulist(f.read()) & os.sched_getaffinity(0)
+        if not cpus:
+            return {"bound": False, "why": "no local cores listed for " + out}
+        os.sched_setaffinity(0, cpus)
+        return {"bound": True, "pci": out, "cores": len(cpus)}
+    except Exception as e:   # the measurement still runs, unbound
+        return {"bound": False, "why": str(e)[:120]}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -518,6 +553,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         nbytes = ens.state_bytes()
+        all_cores = os.sched_getaffinity(0)
+        numa = bind_host_to_gpu(local)
         host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
         E.ens_get_state(ens.ctx, host.data_ptr(), nbytes)
         e2e_steps = max(2, min(args.steps, 5))
@@ -537,11 +574,22 @@ def main():
             E.ens_get_state(ens.ctx, host.data_ptr(), nbytes)
             E.ens_diagnostics(ens.ctx, n_mem, raise_on_flag=False)
         serial = world * n_mem * 2 / (time.perf_counter() - t1)
+        # the copy rates seen by this buffer
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        E.ens_set_state(ens.ctx, host.data_ptr(), nbytes)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        E.ens_get_state(ens.ctx, host.data_ptr(), nbytes)
+        t4 = time.perf_counter()
+        numa.update(h2d_GBs=round(nbytes / (t3 - t2) / 1e9, 1), d2h_GBs=round(nbytes / (t4 - t3) / 1e9, 1))
+        del host
+        os.sched_setaffinity(0, all_cores)   # the CPU baseline below uses every core
         diag_bytes = n_mem * 96
         e2e = {"value": world * n_mem * e2e_steps / sec, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + diag_bytes, "steps": e2e_steps,
                "path": "ens_step_host(pinned host in/out, members in eight chunks: upload, step and download "
-                       "overlapped) + ens_diagnostics", "serial_value": serial}
+                       "overlapped) + ens_diagnostics", "serial_value": serial, "host_binding": numa}
 
     plain = None
     if not args.no_plain and rank == 0:

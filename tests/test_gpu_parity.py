@@ -404,3 +404,13 @@ def test_step_host_matches_device_step(E, chunk):
         E.ens_step_host(a.ctx, host.data_ptr(), host.data_ptr(), nbytes - 8, chunk)
     a.close()
     b.close()
+
+
+def test_histogram_layout_too_large_is_refused(E, capfd):
+    """The statistics pass keeps a CTA's counts in shared memory: a layout
+    that cannot fit (256 x 256 Q-R bins) is refused at creation with
+    ENS_EINVAL and a message on stderr, not at the first snapshot."""
+    with pytest.raises(E.EnsError) as ei:
+        E.Ensemble([config0(E)], hist=E.hist_spec(qr_bins=256, tail_bins=256))
+    assert ei.value.status == 1
+    assert "shared memory" in capfd.readouterr().err
