@@ -36,7 +36,10 @@
 
 namespace ens {
 
-__device__ __forceinline__ int bin_lin(float x, float lo, float inv_w, const float *e, int n)
+// exact bin against the edge table; out of line: taken only near an edge or
+// out of range, so its copies stay out of the per-point code (instruction
+// cache)
+static __device__ __noinline__ int bin_lin(float x, float lo, float inv_w, const float *e, int n)
 {
     if (x < e[0]) return -1;
     if (x >= e[n]) return n;
@@ -47,7 +50,7 @@ __device__ __forceinline__ int bin_lin(float x, float lo, float inv_w, const flo
     return b;
 }
 
-__device__ __forceinline__ int bin_log(float x, float lo, float inv_w, const float *e, int n)
+static __device__ __noinline__ int bin_log(float x, float lo, float inv_w, const float *e, int n)
 {
     if (!(x > 0.f) || x < e[0]) return -1;
     if (x >= e[n]) return n;
