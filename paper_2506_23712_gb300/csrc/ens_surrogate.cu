@@ -6,7 +6,7 @@
 // Sec. IV, Eq. gaussian_lambda_pdf) can be evaluated on a fine lambda
 // quadrature between the simulated lambda values.  The paper has no such
 // component; the member-quadrature mixture (ens_mixture) stays the reference
-// and the judge of the surrogate's error (Hellinger distance).
+// against which the surrogate's error is measured (Hellinger distance).
 //
 // All contractions run on the 5th-generation tensor cores (tcgen05.mma,
 // kind::f16, BF16 operands from shared memory, FP32 accumulator in tensor
