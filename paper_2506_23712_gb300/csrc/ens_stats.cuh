@@ -294,7 +294,9 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
             inv[4] = fmaf(Q, Q, inv[4]); inv[5] = fmaf(R3, R3, inv[5]);
             inv[6] = fmaf(eps, eps, inv[6]); inv[7] = fmaf(ens, ens, inv[7]);
             const float xq = Q * h.q_scale, xr = R3 * h.r_scale, xe = eps * h.eps_scale, xw = ens * h.ens_scale;
-            const bool finite = isfinite(xq) && isfinite(xr) && isfinite(xe) && isfinite(xw);
+            // Tr S^2 involves every component (a_33 and the symmetric
+            // parts of all pairs), so it is finite exactly when A is
+            const bool finite = isfinite(ss);
             int kq, ke = -1, kw = -1;
             if (!finite) {
                 kq = off_c + 5;
