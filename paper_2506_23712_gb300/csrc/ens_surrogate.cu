@@ -182,13 +182,22 @@ __device__ void row_features(const RowSpec &rs, double lam, int bin, float *f)
     f[6] = kind == 2 ? 1.f : 0.f;
     const float s3[3] = {q, r, x};
     int o = 7;
-    for (int c = 0; c < 3; ++c)
+    for (int c = 0; c < 3; ++c) {
+        // sin, cos (pi k s), k = 1..4: one evaluation, then the angle-addition
+        // recurrence sin((k+1) a) = sin(k a) cos a + cos(k a) sin a (and the
+        // cosine likewise); far below the BF16 rounding of the features
+        float s1, c1;
+        sincospif(s3[c], &s1, &c1);
+        float sk = s1, ck = c1;
+#pragma unroll
         for (int k = 1; k <= 4; ++k) {
-            float sv, cv;
-            sincospif((float)k * s3[c], &sv, &cv);
-            f[o++] = sv;
-            f[o++] = cv;
+            f[o++] = sk;
+            f[o++] = ck;
+            const float sn = fmaf(sk, c1, ck * s1), cn = fmaf(ck, c1, -sk * s1);
+            sk = sn;
+            ck = cn;
         }
+    }
 }
 
 __global__ void k_features(RowSpec rs, const double *lams, int nlam, long long rows_pad, __nv_bfloat16 *X,
