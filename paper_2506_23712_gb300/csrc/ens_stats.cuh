@@ -9,9 +9,9 @@
 // log10 histograms of eps/eps_norm and omega^2 nu_norm/eps_norm and, when
 // requested, linear histograms of the gradient components A_ij / sqrt(q0)
 // (longitudinal and transverse pooled separately, Sec. VI).  Bin rule:
-// bin b iff edge[b] <= x < edge[b+1] on FP32 edges (estimate from the affine
-// or log map; near an edge the edge table decides, so the decision is
-// exactly the edge comparison).  Counts go to per-CTA shared-memory
+// bin b iff edge[b] <= x < edge[b+1] on FP32 edges (the floor of the affine
+// or log map's estimate, corrected once against the edge table, so the
+// decision is exactly the edge comparison).  Counts go to per-CTA shared-memory
 // histograms (plain shared atomics for the Q-R and tail histograms,
 // warp-aggregated increments for the gradient components), flushed to the
 // member's uint64 counts once per CTA.  Moments: FP32 sums per thread
@@ -36,51 +36,28 @@
 
 namespace ens {
 
-// exact bin against the edge table; out of line: taken only near an edge or
-// out of range, so its copies stay out of the per-point code (instruction
-// cache)
-static __device__ __noinline__ int bin_lin(float x, float lo, float inv_w, const float *e, int n)
+// Bin of x from its estimated bin coordinate t (affine or log map, within
+// far less than one bin of the exact position): the floor of t, clamped to
+// the table, then one correction against the FP32 edges, so the decision is
+// exactly edge[b] <= x < edge[b + 1]; -1 below edge[0] (x <= 0 for a log
+// map), n at or above edge[n].  Branch-free: no lane of a warp waits on
+// another's edge case.
+__device__ __forceinline__ int bin_tab(float x, float t, const float *e, int n)
 {
-    if (x < e[0]) return -1;
-    if (x >= e[n]) return n;
-    int b = (int)floorf((x - lo) * inv_w);
+    int b = __float2int_rd(t);
     b = min(max(b, 0), n - 1);
-    while (b > 0 && e[b] > x) --b;
-    while (b < n - 1 && e[b + 1] <= x) ++b;
-    return b;
+    return b + (x >= e[b + 1] ? 1 : 0) - (x < e[b] ? 1 : 0);
 }
 
-static __device__ __noinline__ int bin_log(float x, float lo, float inv_w, const float *e, int n)
+__device__ __forceinline__ int bin_lin(float x, float lo, float inv_w, const float *e, int n)
 {
-    if (!(x > 0.f) || x < e[0]) return -1;
-    if (x >= e[n]) return n;
-    // estimate from the hardware log2 (the edge comparisons below decide)
-    int b = (int)floorf((__log2f(x) * 0.30102999566f - lo) * inv_w);
-    b = min(max(b, 0), n - 1);
-    while (b > 0 && e[b] > x) --b;
-    while (b < n - 1 && e[b + 1] <= x) ++b;
-    return b;
+    return bin_tab(x, (x - lo) * inv_w, e, n);
 }
 
-// Bin of x from its estimated bin coordinate t (affine or log map): away
-// from every edge (1e-3 of a bin, far above the estimate's error) the
-// estimate decides; near an edge, or out of range, the edge table does.
-__device__ __forceinline__ int bin_lin_fast(float x, float lo, float inv_w, const float *e, int n)
+// log10 bins from the hardware log2 (the edge comparison decides)
+__device__ __forceinline__ int bin_log(float x, float lo, float inv_w, const float *e, int n)
 {
-    const float t = (x - lo) * inv_w;
-    const float fl = floorf(t), f = t - fl;
-    if (t >= 0.001f && t < (float)n - 0.001f && f > 0.001f && f < 0.999f) return (int)fl;
-    return bin_lin(x, lo, inv_w, e, n);
-}
-
-__device__ __forceinline__ int bin_log_fast(float x, float lo, float inv_w, const float *e, int n)
-{
-    if (x > 0.f) {
-        const float t = (__log2f(x) * 0.30102999566f - lo) * inv_w;
-        const float fl = floorf(t), f = t - fl;
-        if (t >= 0.001f && t < (float)n - 0.001f && f > 0.001f && f < 0.999f) return (int)fl;
-    }
-    return bin_log(x, lo, inv_w, e, n);
+    return bin_tab(x, (__log2f(x) * 0.30102999566f - lo) * inv_w, e, n);
 }
 
 // increment of hist[key] without aggregation (key < 0: none)
@@ -301,12 +278,12 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
             if (!finite) {
                 kq = off_c + 5;
             } else {
-                const int bq = bin_lin_fast(xq, h.q_lo, h.q_inv_w, eq, h.nq);
-                const int br = bin_lin_fast(xr, h.r_lo, h.r_inv_w, er, h.nq);
+                const int bq = bin_lin(xq, h.q_lo, h.q_inv_w, eq, h.nq);
+                const int br = bin_lin(xr, h.r_lo, h.r_inv_w, er, h.nq);
                 kq = (bq >= 0 && bq < h.nq && br >= 0 && br < h.nq) ? bq * h.nq + br : off_c + 0;
-                const int be = bin_log_fast(xe, h.t_lo, h.t_inv_w, et, h.nt);
+                const int be = bin_log(xe, h.t_lo, h.t_inv_w, et, h.nt);
                 ke = be < 0 ? off_c + 1 : (be >= h.nt ? off_c + 2 : off_e + be);
-                const int bw = bin_log_fast(xw, h.t_lo, h.t_inv_w, et, h.nt);
+                const int bw = bin_log(xw, h.t_lo, h.t_inv_w, et, h.nt);
                 kw = bw < 0 ? off_c + 3 : (bw >= h.nt ? off_c + 4 : off_w + bw);
             }
             lane_count(hist, kq);
@@ -320,7 +297,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
                 for (int c = 0; c < 9; ++c) {
                     int kg = -1;
                     if (finite) {
-                        const int bg = bin_lin_fast(A[c] * h.g_scale, h.g_lo, h.g_inv_w, eg, h.ng);
+                        const int bg = bin_lin(A[c] * h.g_scale, h.g_lo, h.g_inv_w, eg, h.ng);
                         const bool lon = c % 4 == 0;
                         kg = bg < 0 ? off_gc + (lon ? 0 : 2)
                                     : (bg >= h.ng ? off_gc + (lon ? 1 : 3) : (lon ? off_gl : off_gt) + bg);
