@@ -274,17 +274,18 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
             // Tr S^2 involves every component (a_33 and the symmetric
             // parts of all pairs), so it is finite exactly when A is
             const bool finite = isfinite(ss);
-            int kq, ke = -1, kw = -1;
+            // keys of all four lookups, then one select for a non-finite
+            // point (its bins are meaningless but in the table's range)
+            const int bq = bin_lin(xq, h.q_lo, h.q_inv_w, eq, h.nq);
+            const int br = bin_lin(xr, h.r_lo, h.r_inv_w, er, h.nq);
+            const int be = bin_log(xe, h.t_lo, h.t_inv_w, et, h.nt);
+            const int bw = bin_log(xw, h.t_lo, h.t_inv_w, et, h.nt);
+            int kq = ((unsigned)bq < (unsigned)h.nq && (unsigned)br < (unsigned)h.nq) ? bq * h.nq + br : off_c + 0;
+            int ke = be < 0 ? off_c + 1 : (be >= h.nt ? off_c + 2 : off_e + be);
+            int kw = bw < 0 ? off_c + 3 : (bw >= h.nt ? off_c + 4 : off_w + bw);
             if (!finite) {
                 kq = off_c + 5;
-            } else {
-                const int bq = bin_lin(xq, h.q_lo, h.q_inv_w, eq, h.nq);
-                const int br = bin_lin(xr, h.r_lo, h.r_inv_w, er, h.nq);
-                kq = (bq >= 0 && bq < h.nq && br >= 0 && br < h.nq) ? bq * h.nq + br : off_c + 0;
-                const int be = bin_log(xe, h.t_lo, h.t_inv_w, et, h.nt);
-                ke = be < 0 ? off_c + 1 : (be >= h.nt ? off_c + 2 : off_e + be);
-                const int bw = bin_log(xw, h.t_lo, h.t_inv_w, et, h.nt);
-                kw = bw < 0 ? off_c + 3 : (bw >= h.nt ? off_c + 4 : off_w + bw);
+                ke = kw = -1;
             }
             lane_count(hist, kq);
             lane_count(hist, ke);
