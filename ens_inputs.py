@@ -148,3 +148,29 @@ def uneven_batch(counts=((128, 24), (256, 12), (384, 4))):
                             dt_max=0.0, rk_order=3, seed=seed, init_energy=0.5))
             seed += 1
     return out
+
+
+def bin_probe_values(edges, n_random: int = 4096, seed: int = 0, log: bool = False) -> np.ndarray:
+    """FP32 probe values for a histogram bin rule on the given FP32 edges:
+    every edge and its FP32 neighbours on both sides, signed zeros, the
+    smallest subnormals, the extremes of the FP32 range, infinities, and
+    seeded values spread over the axis widened by one bin on each side
+    (uniform, or log-uniform for a log axis)."""
+    e = np.asarray(edges, dtype=np.float32)
+    up = np.nextafter(e, np.float32(np.inf))
+    dn = np.nextafter(e, np.float32(-np.inf))
+    fmax = np.finfo(np.float32).max
+    tiny = np.finfo(np.float32).tiny
+    sub = np.float32(1.4e-45)
+    specials = np.array([0.0, -0.0, sub, -sub, tiny, -tiny, fmax, -fmax, np.inf, -np.inf], dtype=np.float32)
+    rng = np.random.default_rng(seed)
+    nb = len(e) - 1
+    if log:
+        lo, hi = math.log10(float(e[0])), math.log10(float(e[-1]))
+        pad = (hi - lo) / nb
+        r = (10.0 ** rng.uniform(lo - pad, hi + pad, n_random)).astype(np.float32)
+    else:
+        lo, hi = float(e[0]), float(e[-1])
+        pad = (hi - lo) / nb
+        r = rng.uniform(lo - pad, hi + pad, n_random).astype(np.float32)
+    return np.concatenate([e, up, dn, specials, r])

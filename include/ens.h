@@ -272,6 +272,16 @@ ens_status ens_gradient_stats(ens_ctx *ctx, int accumulate);
 ens_status ens_get_stats(ens_ctx *ctx, uint64_t *counts, double *moments);
 /* counts_len of a histogram specification. */
 int ens_counts_len(const ens_hist_spec *hist);
+/* The statistics pass's bin rule alone (a check of the rule, used by the
+ * tests): values[0..n) already in an axis's units -- axis 0 Q/q0, 1
+ * R/q0^(3/2), 2 the log10 tail axis (eps/eps_norm, omega^2 nu_norm/eps_norm),
+ * 3 A_ij/sqrt(q0) (needs grad_bins > 0) -- binned on the device with the
+ * context's FP32 edges by the same device code as ens_gradient_stats: bins[i]
+ * = b iff edge[b] <= values[i] < edge[b+1], -1 below the first edge (and a
+ * non-positive value on the log axis), the axis's bin count at or above the
+ * last.  Host buffers, caller-owned; synchronous.  ENS_EINVAL for another
+ * axis, n < 0 or a null buffer with n > 0. */
+ens_status ens_bin_check(ens_ctx *ctx, int axis, const float *values, int n, int *bins);
 
 /* ---- mixture (Sec. II, Eq. pdf_superposition; Sec. IV) ---------------- */
 

@@ -93,6 +93,7 @@ def lib():
         L.or_gradient.argtypes = [vp, i, vp]
         L.or_invariants.argtypes = [vp, i, d, vp, vp, vp, vp]
         L.or_gradient_stats.argtypes = [vp, i, d, P(_HistSpec), vp, vp]
+        L.or_bin_values.argtypes = [P(_HistSpec), i, vp, ctypes.c_long, vp]
         _lib = L
     return _lib
 
@@ -263,6 +264,17 @@ def gradient_stats(uh: np.ndarray, nu: float, h: HistSpec, counts=None, moments=
     hc = h._c()
     lib().or_gradient_stats(_ptr(uh), N, nu, ctypes.byref(hc), _ptr(counts), _ptr(moments))
     return counts, moments
+
+
+def bin_values(h: HistSpec, axis: int, x) -> np.ndarray:
+    """The histogram bin rule on FP32 values already in an axis's units
+    (0 Q/q0, 1 R/q0^1.5, 2 the log10 tail axis, 3 A_ij/sqrt(q0)): -1 for
+    underflow, the axis's bin count for overflow."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(x.size, dtype=np.int32)
+    hc = h._c()
+    lib().or_bin_values(ctypes.byref(hc), axis, _ptr(x), x.size, _ptr(out))
+    return out
 
 
 def split_counts(counts: np.ndarray, h: HistSpec):

@@ -110,6 +110,9 @@ typedef struct {
  * (transverse A_ij, i != j, pooled) | 4 counters: long_under, long_over,
  * trans_under, trans_over]. */
 int or_counts_len(const or_hist_spec *h);
+/* the histogram bin rule on values in an axis's units (axis 0 Q, 1 R,
+ * 2 log10 tail, 3 gradient component): -1 underflow, n overflow */
+void or_bin_values(const or_hist_spec *h, int axis, const float *x, long n, int *out);
 #define OR_NMOM 48
 /* Velocity-gradient fields A_ij = d_j u_i (9 physical fields, row-major ij). */
 void or_gradient(const double *uh, int N, double *A);

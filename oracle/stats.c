@@ -100,6 +100,28 @@ static int find_bin(float x, const float *e, int n)
     return b;
 }
 
+/* The bin rule alone, on values already in the axis's units: axis 0 the Q
+ * axis, 1 the R axis, 2 the log10 tail axis (dissipation and enstrophy),
+ * 3 the gradient-component axis; out[i] = -1 underflow (and a non-positive
+ * value on the log axis), n overflow, else the bin. */
+void or_bin_values(const or_hist_spec *h, int axis, const float *x, long n, int *out)
+{
+    int nb = 0;
+    float *e = NULL;
+    if (axis == 0 || axis == 1 || axis == 3) {
+        const double lim = axis == 0 ? h->q_lim : axis == 1 ? h->r_lim : h->grad_lim;
+        nb = axis == 3 ? h->grad_bins : h->qr_bins;
+        e = (float *)malloc(sizeof(float) * (nb + 1));
+        linear_edges(-lim, lim, nb, e);
+    } else {
+        nb = h->tail_bins;
+        e = (float *)malloc(sizeof(float) * (nb + 1));
+        log_edges(h->tail_lo, h->tail_hi, nb, e);
+    }
+    for (long i = 0; i < n; ++i) out[i] = (axis == 2 && !(x[i] > 0.0f)) ? -1 : find_bin(x[i], e, nb);
+    free(e);
+}
+
 void or_gradient_stats(const double *uh, int N, double nu, const or_hist_spec *h, uint64_t *counts,
                        double *moments)
 {

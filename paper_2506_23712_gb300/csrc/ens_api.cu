@@ -773,6 +773,32 @@ ens_status ens_get_stats(ens_ctx *ctx, uint64_t *counts, double *moments)
     return ENS_OK;
 }
 
+ens_status ens_bin_check(ens_ctx *ctx, int axis, const float *values, int n, int *bins)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (axis < 0 || axis > 3 || n < 0 || (n > 0 && (!values || !bins)) || (axis == 3 && ctx->hd.ng <= 0))
+        return fail(ctx, ENS_EINVAL, "ens_bin_check: axis 0..3 (3 needs grad_bins > 0), n >= 0, buffers");
+    if (n == 0) return ENS_OK;
+    float *dx = nullptr;
+    int *db = nullptr;
+    if (cudaMalloc(&dx, sizeof(float) * n) != cudaSuccess || cudaMalloc(&db, sizeof(int) * n) != cudaSuccess) {
+        if (dx) cudaFree(dx);
+        return fail(ctx, ENS_ENOMEM, "ens_bin_check: device buffers");
+    }
+    cudaError_t e = cudaMemcpyAsync(dx, values, sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        launch_bin_check(ctx->hd, axis, dx, n, db, ctx->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bins, db, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dx);
+    cudaFree(db);
+    ENS_CUDA(ctx, e);
+    return ENS_OK;
+}
+
 static ens_status mixture_device(ens_ctx *ctx, int n, const double *d_lam, const unsigned long long *d_counts,
                                  const double *d_mom, const ens_hist_spec *h, const ens_weight_spec *w,
                                  const double *d_user, double *d_scratch, ens_mixture_out *out, cudaStream_t st)

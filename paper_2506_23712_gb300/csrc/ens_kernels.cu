@@ -393,6 +393,27 @@ void launch_edges(float *eq, float *er, float *et, float *eg, int nq, int nt, in
     k_edges<<<1, 256, 0, s>>>(eq, er, et, eg, nq, nt, ng, q_lim, r_lim, t_lo, t_hi, g_lim);
 }
 
+// the statistics pass's bin rule alone, on values already in an axis's
+// units (0 Q, 1 R, 2 log10 tail, 3 gradient component), edges in global
+// memory: the device functions k_z_stats calls per point
+__global__ void k_bin_check(HistDev h, int axis, const float *__restrict__ x, int n, int *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = x[i];
+    int b;
+    if (axis == 0) b = bin_lin(v, h.q_lo, h.q_inv_w, h.edges_q, h.nq);
+    else if (axis == 1) b = bin_lin(v, h.r_lo, h.r_inv_w, h.edges_r, h.nq);
+    else if (axis == 2) b = bin_log(v, h.t_lo, h.t_inv_w, h.edges_t, h.nt);
+    else b = bin_lin(v, h.g_lo, h.g_inv_w, h.edges_g, h.ng);
+    out[i] = b;
+}
+
+void launch_bin_check(const HistDev &h, int axis, const float *x, int n, int *out, cudaStream_t s)
+{
+    if (n > 0) k_bin_check<<<(n + 255) / 256, 256, 0, s>>>(h, axis, x, n, out);
+}
+
 void launch_finish_stats(const double *mom_partial, int blocks, double *moments, int nmembers, int accumulate,
                          cudaStream_t s)
 {

@@ -74,6 +74,7 @@ void launch_edges(float *eq, float *er, float *et, float *eg, int nq, int nt, in
                   double t_lo, double t_hi, double g_lim, cudaStream_t s);
 void launch_finish_stats(const double *mom_partial, int blocks, double *moments, int nmembers, int accumulate,
                          cudaStream_t s);
+void launch_bin_check(const HistDev &h, int axis, const float *x, int n, int *out, cudaStream_t s);
 void launch_mixture(const double *lam, int n, const MixWeightArgs &wa, const unsigned long long *counts,
                     const double *moments, const MixPdfArgs &pa, double *w, double *covered, double *pdf,
                     double *mom_mix, double *ratios, cudaStream_t s);

@@ -147,6 +147,7 @@ SIGNATURES = [
     ("ens_surrogate_logits", _i, [_vp, _i, _vp, _P(HistSpec), _i, _vp]),
     ("ens_surrogate_time_infer", _i, [_vp, _P(HistSpec), _i, _i, _P(_d)]),
     ("ens_tc_gemm_check", _i, [_vp, _vp, _vp, _i, _i, _i, _i]),
+    ("ens_bin_check", _i, [_vp, _i, _vp, _i, _vp]),
 ]
 
 _lib = None
@@ -636,6 +637,15 @@ class Ensemble:
 # ---------------------------------------------------------------------------
 # learned lambda interpolant (surrogate)
 # ---------------------------------------------------------------------------
+def ens_bin_check(ctx, axis, values):
+    """The statistics pass's bin rule on FP32 values in an axis's units
+    (0 Q/q0, 1 R/q0^1.5, 2 log10 tail, 3 A_ij/sqrt(q0)), on the device."""
+    x = np.ascontiguousarray(values, dtype=np.float32)
+    out = np.empty(x.size, dtype=np.int32)
+    _check(lib().ens_bin_check(ctx, axis, _ptr(x), x.size, _ptr(out)))
+    return out
+
+
 def ens_tc_gemm_check(A_bf16_bits, B_bf16_bits, ksplit=1):
     """C = A B^T on the tensor cores; A [M][K], B [N][K] as uint16 BF16 bits."""
     A = np.ascontiguousarray(A_bf16_bits, dtype=np.uint16)

@@ -441,3 +441,30 @@ def test_statistics_pass_shapes_match_oracle_on_same_field(E, N):
     for k in list(range(0, 36, 4)) + [38, 39]:
         assert mom[0, k] == pytest.approx(rm[k], rel=1e-4), k
     ens.close()
+
+
+def test_bin_rule_matches_oracle_exactly(E):
+    """The statistics pass's bin rule (the device code ens_gradient_stats runs
+    per point, on the context's FP32 edges) against the oracle's on the very
+    same FP32 values: probes at and beside every edge, signed zeros,
+    subnormals, the FP32 extremes, infinities and seeded values over each
+    axis; integer decisions, so bit-exact."""
+    kw = dict(qr_bins=64, q_lim=10.0, r_lim=7.5, tail_bins=256, tail_lo=-8.0, tail_hi=8.0, eps_norm=0.1,
+              nu_norm=0.005, grad_bins=96, grad_lim=40.0)
+    ens = E.Ensemble([config0(E)], hist=E.hist_spec(**kw))
+    h = O.HistSpec(**kw)
+    axes = {
+        0: np.array([-10.0 + 20.0 * b / 64 for b in range(65)], dtype=np.float32),
+        1: np.array([-7.5 + 15.0 * b / 64 for b in range(65)], dtype=np.float32),
+        2: np.array([10.0 ** (-8.0 + 16.0 * b / 256) for b in range(257)], dtype=np.float32),
+        3: np.array([-40.0 + 80.0 * b / 96 for b in range(97)], dtype=np.float32),
+    }
+    for axis, e in axes.items():
+        x = I.bin_probe_values(e, n_random=1 << 16, seed=10 + axis, log=axis == 2)
+        got = E.ens_bin_check(ens.ctx, axis, x)
+        ref = O.bin_values(h, axis, x)
+        bad = np.nonzero(got != ref)[0]
+        assert bad.size == 0, (axis, x[bad[:5]], got[bad[:5]], ref[bad[:5]])
+    with pytest.raises(E.EnsError):
+        E.ens_bin_check(ens.ctx, 4, x)
+    ens.close()

@@ -12,6 +12,7 @@ import math
 import numpy as np
 import pytest
 
+import ens_inputs as I
 import oracle as O
 
 
@@ -155,3 +156,31 @@ def test_log_histogram_underflow_for_zero():
     assert ctr[1] == N ** 3 and ctr[3] == N ** 3 and he.sum() == 0 and hw.sum() == 0
     # Q = R = 0 lies in the interior bins of a symmetric axis
     assert qr[4, 4] == N ** 3
+
+
+def test_bin_rule_on_edges_against_searchsorted():
+    """The oracle's bin rule on probe values at and beside every FP32 edge,
+    signed zeros, subnormals, the FP32 extremes and infinities, against
+    numpy's searchsorted on the same edges (edge[b] <= x < edge[b+1]; -1
+    below, n at or above the last edge; a non-positive value on the log
+    axis is underflow)."""
+    h = O.HistSpec(qr_bins=64, q_lim=10.0, r_lim=7.5, tail_bins=256, tail_lo=-8.0, tail_hi=8.0,
+                   eps_norm=0.1, nu_norm=0.005, grad_bins=96, grad_lim=40.0)
+    axes = {
+        0: np.array([-10.0 + 20.0 * b / 64 for b in range(65)], dtype=np.float32),
+        1: np.array([-7.5 + 15.0 * b / 64 for b in range(65)], dtype=np.float32),
+        2: np.array([10.0 ** (-8.0 + 16.0 * b / 256) for b in range(257)], dtype=np.float32),
+        3: np.array([-40.0 + 80.0 * b / 96 for b in range(97)], dtype=np.float32),
+    }
+    for axis, e in axes.items():
+        x = I.bin_probe_values(e, seed=axis, log=axis == 2)
+        got = O.bin_values(h, axis, x)
+        ref = brute_bins(x, e)
+        ref = np.where(ref >= len(e) - 1, len(e) - 1, ref)
+        if axis == 2:
+            ref = np.where(x > 0, ref, -1)
+        assert np.array_equal(got, ref), axis
+        # every edge opens its own bin, its lower neighbour closes the one before
+        nb = len(e) - 1
+        assert np.array_equal(got[: nb + 1], np.arange(nb + 1))
+        assert np.array_equal(got[2 * (nb + 1): 3 * (nb + 1)], np.arange(-1, nb))
