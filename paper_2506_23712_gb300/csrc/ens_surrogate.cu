@@ -235,6 +235,24 @@ __device__ __forceinline__ float dsilu(float z)
     return s * (1.f + z * (1.f - s));
 }
 
+// BF16 rounding (round to nearest, ties to even) on the integer pipe: the
+// upper 16 bits of the result are the BF16 of f, bit for bit the conversion
+// instruction's result for every non-NaN f (a NaN stays a NaN).  The fused
+// inference rounds three activations per weight-row element, and the
+// conversion instruction shares the special-function unit with tanh.
+__device__ __forceinline__ uint32_t bf16_rne_bits(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return u + 0x7FFFu + ((u >> 16) & 1u);
+}
+// two BF16 values in one word: lo in bits 0..15, hi in bits 16..31
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    return __byte_perm(bf16_rne_bits(lo), bf16_rne_bits(hi), 0x7632);
+}
+// f rounded to BF16, as FP32
+__device__ __forceinline__ float round_bf16(float f) { return __uint_as_float(bf16_rne_bits(f) & 0xFFFF0000u); }
+
 // Z += bias (kept, FP32, for the backward pass); H = SiLU(Z) as BF16 (and H^T)
 __global__ void k_bias_silu(float *Z, const float *bias, long long rows, __nv_bfloat16 *H, __nv_bfloat16 *Ht)
 {
@@ -636,10 +654,7 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
                 uint32_t w[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const float a = silu(v[j + 2 * t] + bb[2 * t]);
-                    const float b = silu(v[j + 2 * t + 1] + bb[2 * t + 1]);
-                    const __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
-                    w[t] = *reinterpret_cast<const uint32_t *>(&hb);
+                    w[t] = pack_bf16x2(silu(v[j + 2 * t] + bb[2 * t]), silu(v[j + 2 * t + 1] + bb[2 * t + 1]));
                 }
                 const int col = c0 + j;
                 *reinterpret_cast<uint4 *>(sH + (col >> 6) * 16384 + sw128_offset(row, col & 63)) =
@@ -667,8 +682,7 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
                 uint32_t w[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const __nv_bfloat162 hb = __floats2bfloat162_rn(f[j + 2 * t], f[j + 2 * t + 1]);
-                    w[t] = *reinterpret_cast<const uint32_t *>(&hb);
+                    w[t] = pack_bf16x2(f[j + 2 * t], f[j + 2 * t + 1]);
                 }
                 *reinterpret_cast<uint4 *>(sH + sw128_offset(tid, j)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
@@ -721,7 +735,7 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
                 }
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const float h = __bfloat162float(__float2bfloat16(silu(v[j + t] + bb[t])));
+                    const float h = round_bf16(silu(v[j + t] + bb[t]));
                     acc = fmaf(h, ww[t], acc);
                 }
             }
