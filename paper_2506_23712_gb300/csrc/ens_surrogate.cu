@@ -667,25 +667,28 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
         tc_fence_before();
         __syncthreads();
     };
+    // features of a tile's rows (threads 0..127, one row each) as packed BF16
+    // pairs; computed for the next tile while the layer-3 MMAs of this one run
+    uint32_t fw[kIn / 2];
+    auto features = [&](long long t) {
+        float f[kIn];
+        const long long rr = t * 128 + tid;
+        if (rr < real) row_features(rs, lams[rr / rs.per_member], (int)(rr % rs.per_member), f);
+        else
+            for (int i = 0; i < kIn; ++i) f[i] = 0.f;
+#pragma unroll
+        for (int j = 0; j < kIn / 2; ++j) fw[j] = pack_bf16x2(f[2 * j], f[2 * j + 1]);
+    };
+    if (tid < 128 && (long long)blockIdx.x < ntiles) features(blockIdx.x);
 #pragma unroll 1
     for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const long long r0 = tile * 128;
         // features of the tile into K-block 0 of H
         if (tid < 128) {
-            float f[kIn];
-            const long long rr = r0 + tid;
-            if (rr < real) row_features(rs, lams[rr / rs.per_member], (int)(rr % rs.per_member), f);
-            else
-                for (int i = 0; i < kIn; ++i) f[i] = 0.f;
 #pragma unroll
-            for (int j = 0; j < kIn; j += 8) {
-                uint32_t w[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    w[t] = pack_bf16x2(f[j + 2 * t], f[j + 2 * t + 1]);
-                }
-                *reinterpret_cast<uint4 *>(sH + sw128_offset(tid, j)) = make_uint4(w[0], w[1], w[2], w[3]);
-            }
+            for (int j = 0; j < kIn; j += 8)
+                *reinterpret_cast<uint4 *>(sH + sw128_offset(tid, j)) =
+                    make_uint4(fw[j / 2], fw[j / 2 + 1], fw[j / 2 + 2], fw[j / 2 + 3]);
         }
         publish();
         // layer 1 (K = 64): the W2 image of this tile may still be arriving
@@ -707,6 +710,8 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
         ok = wait(bar_w, n_w);
         if (!__syncthreads_and(ok)) break;
         mma_layer(sW, 4);
+        // the next tile's features while the layer-3 MMAs run
+        if (tid < 128 && tile + gridDim.x < ntiles) features(tile + gridDim.x);
         ok = wait(bar_mma, n_mma);
         tc_fence_after();
         if (!__syncthreads_and(ok)) break;
