@@ -228,7 +228,11 @@ __device__ __forceinline__ float tanh_approx(float x)
     return y;
 }
 __device__ __forceinline__ float sigmoid(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
-__device__ __forceinline__ float silu(float z) { return z * sigmoid(z); }
+// SiLU z sigmoid(z) written with h = z / 2 as h + h tanh(h): two FMAs and one
+// tanh (the fused inference forms h = v / 2 + b / 2 in one FMA with halved
+// biases, bit for bit the same h as (v + b) / 2)
+__device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_approx(h), h); }
+__device__ __forceinline__ float silu(float z) { return silu_h(0.5f * z); }
 __device__ __forceinline__ float dsilu(float z)
 {
     const float s = sigmoid(z);
@@ -564,7 +568,8 @@ constexpr int kInferThreads = 512;
 // biases and head weights by value: kernel parameters live in the constant
 // bank, so the epilogue's warp-uniform reads are broadcasts
 struct MlpBias {
-    float b1[kHid], b2[kHid], b3[kHid], w4[kHid];
+    float b1[kHid], b2[kHid], b3[kHid];   // halved: the epilogues form (z + b) / 2 in one FMA
+    float w4[kHid];
     float b4;
 };
 constexpr size_t kInferSmem = 1024 + 65536 + 32768 + 131072 + 64;
@@ -654,7 +659,8 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
                 uint32_t w[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    w[t] = pack_bf16x2(silu(v[j + 2 * t] + bb[2 * t]), silu(v[j + 2 * t + 1] + bb[2 * t + 1]));
+                    w[t] = pack_bf16x2(silu_h(fmaf(0.5f, v[j + 2 * t], bb[2 * t])),
+                                       silu_h(fmaf(0.5f, v[j + 2 * t + 1], bb[2 * t + 1])));
                 }
                 const int col = c0 + j;
                 *reinterpret_cast<uint4 *>(sH + (col >> 6) * 16384 + sw128_offset(row, col & 63)) =
@@ -740,7 +746,7 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
                 }
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const float h = round_bf16(silu(v[j + t] + bb[t]));
+                    const float h = round_bf16(silu_h(fmaf(0.5f, v[j + t], bb[t])));
                     acc = fmaf(h, ww[t], acc);
                 }
             }
@@ -846,6 +852,17 @@ bool forward(ens_surrogate *S, long long rows, bool keep_t)
 }
 
 // biases and head of the current parameters (host copy for the kernel parameters)
+// the fused kernel takes b / 2 for the hidden layers (exact in FP32)
+bool halve_biases(MlpBias *b)
+{
+    for (int i = 0; i < kHid; ++i) {
+        b->b1[i] *= 0.5f;
+        b->b2[i] *= 0.5f;
+        b->b3[i] *= 0.5f;
+    }
+    return true;
+}
+
 bool mlp_bias(ens_surrogate *S, MlpBias *b)
 {
     const ParamLayout &L = S->L;
@@ -855,7 +872,7 @@ bool mlp_bias(ens_surrogate *S, MlpBias *b)
            cudaMemcpyAsync(b->b3, S->p + L.b3, sizeof(float) * kHid, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
            cudaMemcpyAsync(b->w4, S->p + L.w4, sizeof(float) * kHid, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
            cudaMemcpyAsync(&b->b4, S->p + L.b4, sizeof(float), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-           cudaStreamSynchronize(s) == cudaSuccess;
+           cudaStreamSynchronize(s) == cudaSuccess && halve_biases(b);
 }
 
 // fused inference of `real` rows (lambda values in S->lam) into S->logit
