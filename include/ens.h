@@ -450,7 +450,7 @@ ens_status ens_synchronize(ens_ctx *ctx);
  * lets the lambda mixture of Sec. II (Eq. ensemble_hypothesis) and Sec. IV
  * (Eq. gaussian_lambda_pdf) be evaluated on a fine lambda quadrature between
  * the simulated members; the member quadrature (ens_mixture) remains the
- * reference and judges its error.  The paper itself mixes member statistics
+ * reference and measures its error.  The paper itself mixes member statistics
  * directly; the interpolant is this library's addition.
  *
  * Row features of (bin, lambda): bin centre coordinates scaled to [-1, 1]
