@@ -121,7 +121,7 @@ typedef struct {
     double Rlambda;   /* Taylor-scale Reynolds number sqrt(20 E^2 / (3 nu diss)) */
     double kmeta;     /* k_max eta with k_max = N/3, eta = (nu^3/diss)^(1/4) */
     int64_t steps;    /* steps taken */
-    int32_t flags;    /* bit 0: non-finite field, bit 1: band energy vanished */
+    int32_t flags;    /* bit 0: non-finite field, bit 1: band energy vanished, bit 2: a device wait gave up */
     int32_t reserved;
 } ens_diag;
 
@@ -437,10 +437,26 @@ ens_status ens_set_velocity(ens_ctx *ctx, int member, const double *host_phys);
 ens_status ens_rhs(ens_ctx *ctx, int member, double *host_spec);
 
 /* Diagnostics of every member (n entries).  Synchronises.  Returns
- * ENS_ENONFINITE or ENS_ESTATE if a member is flagged (the array is still
- * filled). */
+ * ENS_ETIMEOUT, ENS_ENONFINITE or ENS_ESTATE, in that order of precedence,
+ * if a member is flagged (the array is still filled); flags bit 2 marks a
+ * member whose rows a device-side wait gave up on (ENS_ETIMEOUT; its state
+ * is then invalid). */
 ens_status ens_diagnostics(ens_ctx *ctx, ens_diag *out);
 ens_status ens_synchronize(ens_ctx *ctx);
+
+/* Failure-detection test hook (no counterpart in the paper).  Arms the next
+ * ens_step_nograph call (one-shot): in its persistent z passes the bulk
+ * copies of `member`'s first row group are not issued, and the wait on that
+ * group's barrier gives up after wait_polls polls (1 .. 65536) instead of
+ * the full limit, so the bounded wait runs out with nothing in flight; every
+ * other wait, on copies that were issued, keeps its full limit.  The warp
+ * that gives up leaves its remaining rows unprocessed and flags `member` and
+ * every later member of its grid-size group (flags bit 2); ens_diagnostics
+ * then returns ENS_ETIMEOUT.  The context stays usable (the flagged states
+ * are invalid).  ENS_EINVAL (not sticky) for a member out of range, a
+ * wait_polls out of range, or a member whose group runs the z pass variant
+ * without bulk copies (z_variant 1). */
+ens_status ens_test_skip_copy(ens_ctx *ctx, int member, int wait_polls);
 
 /* ---- learned lambda interpolant (surrogate) ------------------------------
  * A 4-layer MLP (width 256, SiLU; BF16 weights, FP32 accumulation on the

@@ -70,6 +70,8 @@ struct ens_ctx {
     int rk = 3;
     int sms = 0;                 // streaming multiprocessors of the device
     int parallel_groups = 1;     // grid-size groups as parallel graph branches
+    int skip_member = -1;        // ens_test_skip_copy: member armed for the next ens_step_nograph (-1: none)
+    int skip_wait = 0;
     ens_status sticky = ENS_OK;
     std::string err;
 };
@@ -164,6 +166,8 @@ size_t carve(const ens_member_desc *m, int n, const ens_hist_spec *h, char *base
         g.plan_x = 0;
         g.fx_split = 0;
         g.z_mode = 0;
+        g.z_skip_member = -1;
+        g.z_skip_wait = 0;
         g.members = (int)gr.members.size();
         g.first = first;
         first += g.members;
@@ -513,6 +517,7 @@ ens_status ens_create(const ens_member_desc *m, int n, const ens_hist_spec *h, v
     const size_t need = carve(m, n, h, nullptr, nullptr);
     if (workspace) {
         if (ws_bytes < need) {
+            fprintf(stderr, "ens_create: workspace of %zu bytes, %zu needed\n", ws_bytes, need);
             delete ctx;
             return ENS_ENOMEM;
         }
@@ -591,8 +596,33 @@ ens_status ens_step_nograph(ens_ctx *ctx, int nsteps)
     ens_status s = check(ctx);
     if (s != ENS_OK) return s;
     if (nsteps < 0) return fail(ctx, ENS_EINVAL, "nsteps < 0");
+    Geo *armed = nullptr;   // ens_test_skip_copy: applies to this call's launches only
+    if (ctx->skip_member >= 0) {
+        armed = &ctx->groups[ctx->member_group[ctx->skip_member]].geo;
+        armed->z_skip_member = ctx->member_local[ctx->skip_member];
+        armed->z_skip_wait = ctx->skip_wait;
+        ctx->skip_member = -1;
+    }
     for (int k = 0; k < nsteps; ++k) record_step(ctx, ctx->stream);
+    if (armed) armed->z_skip_member = -1;
     ENS_CUDA(ctx, cudaGetLastError());
+    return ENS_OK;
+}
+
+ens_status ens_test_skip_copy(ens_ctx *ctx, int member, int wait_polls)
+{
+    ens_status s = check(ctx);
+    if (s != ENS_OK) return s;
+    if (member < 0 || member >= (int)ctx->desc.size() || wait_polls < 1 || wait_polls > (1 << 16)) {
+        std::fprintf(stderr, "libens: ens_test_skip_copy: member out of range or wait_polls not in [1, 65536]\n");
+        return ENS_EINVAL;
+    }
+    if (ctx->groups[ctx->member_group[member]].geo.z_mode == 1) {
+        std::fprintf(stderr, "libens: ens_test_skip_copy: the member's group runs the z pass without bulk copies\n");
+        return ENS_EINVAL;
+    }
+    ctx->skip_member = member;
+    ctx->skip_wait = wait_polls;
     return ENS_OK;
 }
 
@@ -1046,7 +1076,7 @@ ens_status ens_diagnostics(ens_ctx *ctx, ens_diag *out)
     std::vector<MemberDev> md(n);
     ENS_CUDA(ctx, cudaMemcpyAsync(md.data(), ctx->md, sizeof(MemberDev) * n, cudaMemcpyDeviceToHost, ctx->stream));
     ENS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    ens_status flag = ENS_OK;
+    int any = 0;
     for (int i = 0; i < n; ++i) {
         const MemberDev &d = md[slot_of(ctx, i)];
         ens_diag &o = out[i];
@@ -1062,11 +1092,14 @@ ens_status ens_diagnostics(ens_ctx *ctx, ens_diag *out)
         o.steps = d.steps;
         o.flags = d.flags;
         o.reserved = 0;
-        if ((d.flags & kFlagNonFinite) && flag == ENS_OK) flag = ENS_ENONFINITE;
-        if ((d.flags & kFlagNoBandEnergy) && flag == ENS_OK) flag = ENS_ESTATE;
-        if ((d.flags & kFlagTimeout) && flag == ENS_OK) flag = ENS_ETIMEOUT;
+        any |= d.flags;
     }
-    return flag;
+    // a member whose device wait gave up was left partly unprocessed, which
+    // can also make it non-finite: the timeout is the cause and is reported first
+    if (any & kFlagTimeout) return ENS_ETIMEOUT;
+    if (any & kFlagNonFinite) return ENS_ENONFINITE;
+    if (any & kFlagNoBandEnergy) return ENS_ESTATE;
+    return ENS_OK;
 }
 
 }  // extern "C"

@@ -456,7 +456,7 @@ struct WarpTw {
 // index, radix slot) with disjoint bits, and the map is additive over such
 // parts, so each access is one per-lane base plus an immediate offset: no
 // per-access address arithmetic.  A_s, D_s and the row stride SROW are the
-// bank-conflict-free choices printed by swizzle_search.py (half-warp model
+// bank-conflict-free choices printed by tests/swizzle_search.py (half-warp model
 // of 8-byte requests).
 template <int N>
 struct WPad {

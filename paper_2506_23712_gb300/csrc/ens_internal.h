@@ -59,6 +59,13 @@ struct Geo {
     int fx_split;                // last pass of a stage: 0 fused, 1 transform + update launches
     int z_mode;                  // 0: persistent TMA z pass, 1: one CTA per row group
     int z_ctas;                  // persistent CTAs of the z-direction nonlinear pass
+    // failure test only (ens_test_skip_copy): the persistent z pass issues no
+    // bulk copy for the first row group of this member (local index in the
+    // group; -1: none) and waits for that group's barrier at most
+    // z_skip_wait polls, so the bounded wait gives up; every other wait keeps
+    // its full limit
+    int z_skip_member;
+    int z_skip_wait;
 };
 
 struct HistDev {

@@ -45,7 +45,7 @@ struct Dims {
 // offline search over every access pattern of the line transforms (the pass
 // exchanges, the output stores, the Hermitian unpacking reads) so that each
 // half-warp request of 8-byte words meets 16 distinct bank pairs
-// (paper_2506_23712_gb300/swizzle_search.py reproduces the tables); the
+// (tests/swizzle_search.py reproduces the tables); the
 // small sizes keep an additive padding.
 template <int N>
 struct RowSwz {

@@ -62,10 +62,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // All 32 lanes poll the phase; returns true (warp-uniformly) once every lane
-// has observed the completion, false after kWaitIters rounds.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity)
+// has observed the completion, false after `iters` rounds.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, int iters = kWaitIters)
 {
-    for (int it = 0; it < kWaitIters; ++it) {
+    for (int it = 0; it < iters; ++it) {
         const bool ok = mbar_try_wait(bar, parity);
         if (__all_sync(0xffffffffu, ok)) return true;
     }

@@ -211,8 +211,10 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
     const long long W = (long long)gridDim.x * C::WPB;
     long long grp = (long long)blockIdx.x * C::WPB + warp;
     const uint32_t bytes = (uint32_t)(LPW * 6 * NZ2 * sizeof(float2));
+    auto skipped = [&](long long gi) { return gi / G == g.z_skip_member && gi % G == 0; };
     auto issue = [&](long long gi, int b) {   // lane 0 only
         const long long m = gi / G, lg = gi % G;
+        if (skipped(gi)) return;   // failure test: nothing in flight for this barrier
         const float2 *src = g.B + m * kFields * Dims<N>::SB + (lg * LPW) * Dims<N>::NZP;
         float2 *dst = st + b * C::STAGE;
         mbar_arrive_expect_tx(&bar[b], bytes);
@@ -259,7 +261,7 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
             fence_proxy_async_smem();   // this buffer's earlier reads precede the refill
             issue(nxt, b ^ 1);
         }
-        if (!mbar_wait_warp(&bar[b], (uint32_t)((it >> 1) & 1))) {
+        if (!mbar_wait_warp(&bar[b], (uint32_t)((it >> 1) & 1), skipped(grp) ? g.z_skip_wait : kWaitIters)) {
             timed_out = true;
             break;
         }
@@ -321,7 +323,10 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
     }
     if (grp > (long long)blockIdx.x * C::WPB + warp || timed_out) flush(cur_m);
     if (timed_out) {
-        if (lane == 0) atomicOr(&md[g.first + cur_m].flags, kFlagTimeout);
+        // this warp's remaining row groups (this member's and those of every
+        // later member of the group) stay unprocessed: flag them all
+        if (lane == 0)
+            for (long long m = grp / G; m < g.members; ++m) atomicOr(&md[g.first + m].flags, kFlagTimeout);
         // the refill of the other buffer may still be in flight: wait for it (bounded)
         if (grp + W < T) mbar_wait_warp(&bar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
     }

@@ -129,6 +129,7 @@ SIGNATURES = [
     ("ens_rhs", _i, [_vp, _i, _vp]),
     ("ens_diagnostics", _i, [_vp, _P(Diag)]),
     ("ens_synchronize", _i, [_vp]),
+    ("ens_test_skip_copy", _i, [_vp, _i, _i]),
     ("ens_members", _i, [_vp]),
     ("ens_member_n", _i, [_vp, _i]),
     ("ens_run_pass", _i, [_vp, _i, _i]),
@@ -302,11 +303,27 @@ def ens_mixture(ctx, n, hist, **weights):
     return _mixture_result(out, bufs, hist)
 
 
-def ens_mixture_host(lambdas, counts, moments, hist, stream_ptr=None, **weights):
-    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+def _host_stats_arrays(lambdas, counts, moments, hist, weights):
+    """The host inputs of the mixture as contiguous arrays, their shapes
+    checked against the member count and the histogram layout (the C side
+    reads n * counts_len counts, n * ENS_NMOM moments and n user weights)."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64).ravel()
     counts = np.ascontiguousarray(counts, dtype=np.uint64)
     moments = np.ascontiguousarray(moments, dtype=np.float64)
     n = lam.size
+    L = ens_counts_len(hist)
+    if counts.shape != (n, L):
+        raise ValueError("counts has shape %s, expected (%d, %d)" % (counts.shape, n, L))
+    if moments.shape != (n, ENS_NMOM):
+        raise ValueError("moments has shape %s, expected (%d, %d)" % (moments.shape, n, ENS_NMOM))
+    user = weights.get("user")
+    if user is not None and np.asarray(user).size != n:
+        raise ValueError("%d user weights for %d members" % (np.asarray(user).size, n))
+    return lam, counts, moments, n
+
+
+def ens_mixture_host(lambdas, counts, moments, hist, stream_ptr=None, **weights):
+    lam, counts, moments, n = _host_stats_arrays(lambdas, counts, moments, hist, weights)
     ws, keep = _weight_spec(**weights)
     out, bufs = _mixture_out(n, hist)
     if stream_ptr is None:
@@ -325,10 +342,7 @@ def ens_mixture_host_noalloc(lambdas, counts, moments, hist, stream_ptr=None, **
     for callers that cannot allocate device memory.  Raises EnsError with
     ENS_EINVAL beyond ENS_NOALLOC_MAX_MEMBERS members or
     ENS_NOALLOC_MAX_COUNTS counts per member."""
-    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
-    counts = np.ascontiguousarray(counts, dtype=np.uint64)
-    moments = np.ascontiguousarray(moments, dtype=np.float64)
-    n = lam.size
+    lam, counts, moments, n = _host_stats_arrays(lambdas, counts, moments, hist, weights)
     ws, keep = _weight_spec(**weights)
     out, bufs = _mixture_out(n, hist)
     if stream_ptr is None:
@@ -472,6 +486,10 @@ def ens_diagnostics(ctx, n, raise_on_flag=True):
 
 def ens_synchronize(ctx):
     _check(lib().ens_synchronize(ctx), ctx)
+
+
+def ens_test_skip_copy(ctx, member, wait_polls):
+    _check(lib().ens_test_skip_copy(ctx, member, wait_polls), ctx)
 
 
 def ens_run_pass(ctx, pass_id, stage=0):

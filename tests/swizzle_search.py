@@ -1,5 +1,5 @@
 """Offline search for the shared-memory row swizzles of the warp-local line
-transforms (RowSwz in csrc/ens_kernels.cuh).
+transforms (RowSwz in paper_2506_23712_gb300/csrc/ens_kernels.cuh).
 
 A warp-local line of N complex values (float2) lives in one shared-memory
 row; the z-direction passes touch it with a few fixed access patterns: the
@@ -17,12 +17,12 @@ the masks:
   N = 384, 512: one free mask per block (seeded local search)
 
 The persistent z pass uses, for the power-of-two plans, one additive
-layout per pass exchange instead (WPad in csrc/ens_fft.cuh): exchange s puts
+layout per pass exchange instead (WPad in paper_2506_23712_gb300/csrc/ens_fft.cuh): exchange s puts
 position pos at slot pos + (pos >> A_s) * D_s, and `pad_search` picks A_s,
 D_s and a common row stride with the fewest wavefronts over that exchange's
 store and load patterns (exhaustive over small A, D).
 
-Run: python -m paper_2506_23712_gb300.swizzle_search   (prints the packed
+Run: python tests/swizzle_search.py   (prints the packed
 64-bit tables and the wavefront counts: ideal, additive padding, swizzle;
 then the per-exchange pad table).
 """

@@ -70,3 +70,25 @@ def test_binding_refuses_without_gpu():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         E.Ensemble([E.Member(N=32, nu=0.02)])
+
+
+def test_workspace_too_small_is_enomem_before_any_device_call(lib, capfd):
+    """ens_create with a caller-owned workspace one byte short of ens_query's
+    size returns ENS_ENOMEM and no context, checked on the host before any
+    CUDA call (the pointer is never dereferenced)."""
+    h = E.hist_spec()
+    ms = [E.Member(N=32, nu=0.02, k_lo=1, k_hi=2).c(), E.Member(N=64, nu=0.02, k_lo=1, k_hi=2).c()]
+    need = E.ens_query(ms, h)
+    arr = (E.MemberDesc * len(ms))(*ms)
+    ctx = ctypes.c_void_p(12345)
+    st = lib.ens_create(arr, len(ms), ctypes.byref(h), ctypes.c_void_p(1 << 20), need - 1, None, ctypes.byref(ctx))
+    assert st == 2 and not ctx.value
+    assert "workspace" in capfd.readouterr().err
+
+
+def test_noalloc_limits_match_header(lib):
+    with open(B.os.path.join(B.ROOT, "include", "ens.h")) as f:
+        text = f.read()
+    for name in ("ENS_NOALLOC_MAX_MEMBERS", "ENS_NOALLOC_MAX_COUNTS", "ENS_NMOM"):
+        m = re.search(r"#define\s+%s\s+(\d+)" % name, text)
+        assert m and int(m.group(1)) == getattr(E, name), name

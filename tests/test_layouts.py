@@ -11,9 +11,10 @@ import re
 import numpy as np
 import pytest
 
-from paper_2506_23712_gb300 import swizzle_search as S
+import swizzle_search as S
 
-HDR = os.path.join(os.path.dirname(S.__file__), "csrc", "ens_fft.cuh")
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2506_23712_gb300", "csrc",
+                   "ens_fft.cuh")
 
 
 def wpad_table():
