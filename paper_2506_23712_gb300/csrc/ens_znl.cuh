@@ -211,7 +211,8 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
     const long long W = (long long)gridDim.x * C::WPB;
     long long grp = (long long)blockIdx.x * C::WPB + warp;
     const uint32_t bytes = (uint32_t)(LPW * 6 * NZ2 * sizeof(float2));
-    auto skipped = [&](long long gi) { return gi / G == g.z_skip_member && gi % G == 0; };
+    const long long skip_gi = g.z_skip_member >= 0 ? g.z_skip_member * G : -1;   // failure test only
+    auto skipped = [&](long long gi) { return gi == skip_gi; };
     auto issue = [&](long long gi, int b) {   // lane 0 only
         const long long m = gi / G, lg = gi % G;
         if (skipped(gi)) return;   // failure test: nothing in flight for this barrier

@@ -479,7 +479,7 @@ DIAG_KEYS = ("t", "dt", "E", "diss", "EB", "P", "umax", "Rlambda", "kmeta", "ste
 def ens_diagnostics(ctx, n, raise_on_flag=True):
     arr = (Diag * n)()
     st = lib().ens_diagnostics(ctx, arr)
-    if st not in (0, 4, 6) or (raise_on_flag and st != 0):
+    if st not in (0, 4, 5, 6) or (raise_on_flag and st != 0):
         _check(st, ctx)
     return [{k: getattr(d, k) for k in DIAG_KEYS} for d in arr], st
 
