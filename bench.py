@@ -341,8 +341,10 @@ def measure_surrogate(E, ens, descs, torch, steps=800):
     sur = S.mixture(h, lo, hi, 512, kind=E.W_GAUSS_PAPER, c=0.023, Z=Z)
     t_inf = time.perf_counter() - t0
     S.close()
+    gain = held_out_gain(E, lams, counts, h, steps)
     peak = measured_bf16()
     return {"members": len(lams), "bins_per_member": per, "train_steps": steps, "train_s": t_train,
+            "held_out_gain": gain,
             "train_rows_per_step": len(lams) * per, "final_loss": loss,
             "quadrature_points": 512, "mixture_s": t_inf,
             "hellinger_vs_member_quadrature": {k: hellinger(sur[k], ref[k]) for k in ("pdf_qr", "pdf_eps", "pdf_ens")},
@@ -352,6 +354,42 @@ def measure_surrogate(E, ens, descs, torch, steps=800):
             "layer_gemm": {"kernel": "k_gemm_tc<256>", "shape": "%d x 256 x 256 BF16 -> FP32" % pad128(rows_q),
                            "ms": gemm_ms, "TFLOPs": gemm_tflops,
                            "note": "training-path layer GEMM; FP32 output makes it HBM-bound (86 flop/B)"}}
+
+
+def held_out_gain(E, lams, counts, h, steps):
+    """What the interpolant gains over the method without it: trained on
+    every other member in lambda order, evaluated at the held-out interior
+    members against the nearest simulated member and against linear
+    interpolation in lambda (mean Hellinger over held-out members, per PDF)."""
+    nq, nt = h.qr_bins, h.tail_bins
+    order = np.argsort(lams)
+    lam_s, cnt_s = lams[order], counts[order]
+    parts = [slice(0, nq * nq), slice(nq * nq, nq * nq + nt), slice(nq * nq + nt, nq * nq + 2 * nt)]
+
+    def norm(c):
+        c = np.asarray(c, dtype=np.float64)
+        return np.concatenate([c[x] / max(c[x].sum(), 1.0) for x in parts])
+    P = np.array([norm(c) for c in cnt_s])
+    ev = np.arange(0, len(lam_s), 2)
+    od = np.arange(1, len(lam_s) - 1, 2)
+    S = E.Surrogate(seed=5)
+    S.train(lam_s[ev], cnt_s[ev], h, steps, lr=4e-3)
+    q = S.density(lam_s[od], h)
+    S.close()
+    res = {"surrogate": [], "nearest_member": [], "linear_in_lambda": []}
+    for j, i in enumerate(od):
+        near = i - 1 if lam_s[i] - lam_s[i - 1] <= lam_s[i + 1] - lam_s[i] else i + 1
+        a = (lam_s[i + 1] - lam_s[i]) / max(lam_s[i + 1] - lam_s[i - 1], 1e-12)
+        lin = a * P[i - 1] + (1 - a) * P[i + 1]
+        for key, est in (("surrogate", q[j]), ("nearest_member", P[near]), ("linear_in_lambda", lin)):
+            res[key].append([hellinger(est[x], P[i][x]) for x in parts])
+    out = {k: dict(zip(("pdf_qr", "pdf_eps", "pdf_ens"), np.mean(v, axis=0).round(5).tolist()))
+           for k, v in res.items()}
+    means = {k: float(np.mean(v)) for k, v in res.items()}
+    out["best"] = min(means, key=means.get)
+    out["note"] = ("trained on every other member in lambda order, evaluated at the %d held-out interior members "
+                   "(single snapshot of the benchmark ensemble)" % len(od))
+    return out
 
 
 def pad128(r):
@@ -380,8 +418,21 @@ def measure_uneven(E, torch, steps=3, tune=True):
            "members": len(ms), "steps": steps}
     if tune:
         out["tuning"] = ens.autotune(steps=2)
-    for mode in ("batched", "sequential"):
-        run = (lambda k: ens.step(k)) if mode == "batched" else (lambda k: E.ens_step_sequential(ens.ctx, k))
+    tuned = ens.tuning()
+
+    def with_persistent(flag):
+        t = json.loads(json.dumps(tuned))
+        t["persistent"] = flag
+        ens.set_tuning(t)
+    # the autotuner's choice, then each design on its own: all members in one
+    # persistent launch per RK stage, the graph of per-pass launches (one
+    # branch or chain per grid size), and member-by-member launches
+    for mode in ("batched", "persistent", "graph_branches", "sequential"):
+        if mode == "persistent":
+            with_persistent(1)
+        elif mode == "graph_branches":
+            with_persistent(0)
+        run = (lambda k: E.ens_step_sequential(ens.ctx, k)) if mode == "sequential" else (lambda k: ens.step(k))
         run(1)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -392,6 +443,8 @@ def measure_uneven(E, torch, steps=3, tune=True):
         sec = a.elapsed_time(b) / 1e3
         out[mode] = {"member_steps_per_s": len(ms) * steps / sec, "ms_per_step": 1e3 * sec / steps}
     out["batched_over_sequential"] = out["batched"]["member_steps_per_s"] / out["sequential"]["member_steps_per_s"]
+    out["persistent_over_graph_branches"] = (out["persistent"]["member_steps_per_s"] /
+                                             out["graph_branches"]["member_steps_per_s"])
     flags = sum(1 for d in ens.diagnostics(raise_on_flag=False) if d["flags"])
     out["flagged_members"] = flags
     ens.close()

@@ -239,6 +239,15 @@ typedef struct {
 typedef struct {
     int groups;          /* number of grid-size groups (read-only) */
     int parallel_groups; /* 1: groups as parallel graph branches; 0: one chain */
+    int persistent;      /* 1: every member of every grid size advances one RK
+                          * stage in one persistent launch (a cooperative grid of
+                          * one CTA per SM taking work items -- column tiles,
+                          * z-pass row-group chunks, stage finishes -- in
+                          * dependency order, waiting, bounded, on per-member
+                          * pass counters); available when every grid size is
+                          * 128, 256 or 384; the group variants below are then
+                          * ignored (16-column tiles, 16 threads per FFT line,
+                          * the default z warp plan, the fused last pass) */
     ens_group_tuning group[ENS_MAX_GROUPS];   /* ascending N */
     double ms_per_step;  /* ens_autotune: mean step time of the winner, else 0 */
     int trials;          /* ens_autotune: configurations timed */
@@ -253,7 +262,8 @@ ens_status ens_get_tuning(const ens_ctx *ctx, ens_tuning *out);
 ens_status ens_set_tuning(ens_ctx *ctx, const ens_tuning *t);
 /* Time the variants on this context's own members and install the fastest:
  * coordinate descent over plan_x, tile_x, tile_y, the z variant and its CTAs
- * per SM, fx_split for each group, then parallel_groups; each trial restores the member
+ * per SM, fx_split for each group, then parallel_groups, then persistent
+ * (where available); each trial restores the member
  * state from a device snapshot, runs one untimed step and times `steps`
  * graph replays with CUDA events; a candidate wins only if it is more than
  * 1% faster.  The member state is restored afterwards (the simulation does
@@ -533,7 +543,8 @@ int ens_member_n(const ens_ctx *ctx, int member);
 /* Launch one pass of one RK stage for every member (profiling): pass 0 IX,
  * 1 IY, 2 ZNL, 3 FY, 4 FXU.  Asynchronous. */
 ens_status ens_run_pass(ens_ctx *ctx, int pass, int stage);
-/* Kernels one ens_step launches per step (graph nodes). */
+/* Kernels one ens_step launches per step (graph nodes; with the persistent
+ * stage kernel, one per RK stage). */
 int ens_kernels_per_step(const ens_ctx *ctx);
 /* Algorithmic HBM bytes of one pass for all members (unique bytes read +
  * written, valid modes only); pass as in ens_run_pass, stage 0..2; pass 5

@@ -19,6 +19,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libens.so")
 SOURCES = ["ens_kernels.cu", "ens_api.cu", "ens_noalloc.cu", "ens_surrogate.cu", "ens_theory.cu"]
+# the persistent stage kernel reads, within one launch, data other CTAs wrote:
+# its global loads are cached in L2 only
+PERSIST = "ens_persist.cu"
+PERSIST_FLAGS = ["-Xptxas", "-dlcm=cg"]
 # the FFT passes of each grid size compile in their own translation unit
 SIZED = "ens_sized.cu"
 SIZES = [16, 32, 64, 128, 256, 384, 512]
@@ -66,6 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj
 
     jobs = [(SIZED, ["-DENS_N=%d" % n], "ens_sized_%d.o" % n) for n in reversed(SIZES)]
+    jobs += [(PERSIST, PERSIST_FLAGS, PERSIST.replace(".cu", ".o"))]
     jobs += [(src, [], src.replace(".cu", ".o")) for src in SOURCES]
     with ThreadPoolExecutor(max_workers=min(len(jobs), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, jobs))

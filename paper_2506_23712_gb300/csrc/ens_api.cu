@@ -2,6 +2,7 @@
 // orchestration of the hot-path kernels, host<->device marshalling.
 #include "../../include/ens.h"
 #include "ens_launch.h"
+#include "ens_persist.h"
 
 #include <algorithm>
 #include <cstddef>
@@ -71,6 +72,13 @@ struct ens_ctx {
     int sms = 0;                 // streaming multiprocessors of the device
     int parallel_groups = 1;     // grid-size groups as parallel graph branches
     int skip_member = -1;        // ens_test_skip_copy: member armed for the next ens_step_nograph (-1: none)
+    // persistent stage kernel (grid sizes 128, 256, 384): work items, counters
+    PItem *pitems = nullptr;
+    int npitems = 0;
+    unsigned *pwork = nullptr;   // [2 + members * kPKinds]: item counter, abort flag, per-member done counts
+    unsigned pneed[kPSlots][kPKinds] = {};
+    int persist_ctas = 0;        // resident CTAs of the persistent kernel (0: unavailable)
+    int persistent = 0;          // 1: one persistent launch per RK stage
     int skip_wait = 0;
     ens_status sticky = ENS_OK;
     std::string err;
@@ -194,7 +202,27 @@ size_t carve(const ens_member_desc *m, int n, const ens_hist_spec *h, char *base
     float *edges = ar.take<float>((size_t)2 * (h->qr_bins + 1) + h->tail_bins + 1 + h->grad_bins + 1);
     // mixture scratch: lambdas, user weights, weights, covered, pdf, mixed moments, ratios
     double *mix = ar.take<double>((size_t)3 * n + 1 + L + kNMom + 8);
+    // work items of the persistent stage kernel, where every grid size has its pass bodies there
+    PItem *pitems = nullptr;
+    unsigned *pwork = nullptr;
+    int npitems = 0;
+    unsigned pneed[kPSlots][kPKinds];
+    bool persist = groups.size() <= (size_t)kPSlots;
+    for (auto &gr : groups) persist = persist && persist_size_supported(gr.geo.N);
+    if (persist) {
+        std::vector<Geo> geos;
+        for (auto &gr : groups) geos.push_back(gr.geo);
+        std::vector<PItem> items;
+        persist_items(geos, items, pneed);
+        npitems = (int)items.size();
+        pitems = ar.take<PItem>(items.size());
+        pwork = ar.take<unsigned>(2 + (size_t)n * kPKinds);
+    }
     if (ctx) {
+        ctx->pitems = persist ? pitems : nullptr;
+        ctx->npitems = npitems;
+        ctx->pwork = pwork;
+        if (persist) std::memcpy(ctx->pneed, pneed, sizeof pneed);
         ctx->md = md;
         ctx->partial = partial;
         ctx->partial_blocks = PB;
@@ -265,12 +293,38 @@ void record_group_stage(ens_ctx *ctx, const Geo &g, int st, int last, cudaStream
     launch_pass(Pass::FX, 0, g, ctx->md, nullptr, st, last, 0, s);
 }
 
+// One step with the persistent stage kernel: per RK stage, the work counters
+// cleared and one cooperative launch that runs every pass of every member.
+void record_step_persistent(ens_ctx *ctx, cudaStream_t s)
+{
+    const int n = (int)ctx->desc.size();
+    PStageArgs a{};
+    for (size_t gi = 0; gi < ctx->groups.size(); ++gi) a.g[gi] = ctx->groups[gi].geo;
+    a.md = ctx->md;
+    a.items = ctx->pitems;
+    a.nitems = ctx->npitems;
+    a.next = ctx->pwork;
+    a.abort = ctx->pwork + 1;
+    a.done = ctx->pwork + 2;
+    std::memcpy(a.need, ctx->pneed, sizeof a.need);
+    for (int st = 0; st < ctx->rk; ++st) {
+        a.stage = st;
+        a.last = st == ctx->rk - 1;
+        cudaMemsetAsync(ctx->pwork, 0, sizeof(unsigned) * (2 + (size_t)n * kPKinds), s);
+        launch_stage_persist(a, ctx->persist_ctas, s);
+    }
+}
+
 // One step.  Groups of different grid size are independent until the
 // per-member stage reduction, so with several groups each group's pass chain
 // runs on its own stream (a parallel branch of the captured graph), joined
 // before the reduction of every stage.
 void record_step(ens_ctx *ctx, cudaStream_t s)
 {
+    if (ctx->persistent) {
+        record_step_persistent(ctx, s);
+        return;
+    }
     const int nst = ctx->rk;
     const int n = (int)ctx->desc.size();
     const int ng = (int)ctx->groups.size();
@@ -453,6 +507,18 @@ static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, co
         ENS_CUDA(ctx, cudaMemsetAsync(gr.geo.S, 0, sizeof(float2) * 3 * gr.geo.sU * gr.geo.members, st));
         launch_ic(gr.geo, ctx->md, st);
     }
+    std::vector<PItem> items;   // kept until the synchronisation below
+    if (ctx->pitems) {
+        std::vector<Geo> geos;
+        for (auto &gr : ctx->groups) geos.push_back(gr.geo);
+        unsigned need[kPSlots][kPKinds];
+        persist_items(geos, items, need);
+        ENS_CUDA(ctx, persist_prepare());
+        const int per_sm = persist_ctas_per_sm();
+        ctx->persist_ctas = per_sm > 0 ? per_sm * ctx->sms : 0;
+        ENS_CUDA(ctx, cudaMemcpyAsync(ctx->pitems, items.data(), sizeof(PItem) * items.size(),
+                                      cudaMemcpyHostToDevice, st));
+    }
     ENS_CUDA(ctx, cudaGetLastError());
     s = resum(ctx);
     if (s != ENS_OK) return s;
@@ -576,6 +642,7 @@ int ens_member_n(const ens_ctx *ctx, int i)
 int ens_kernels_per_step(const ens_ctx *ctx)
 {
     if (!ctx) return 0;
+    if (ctx->persistent) return ctx->rk;   // one persistent launch per stage
     int per_stage = 1;   // the per-member stage reduction
     for (auto &gr : ctx->groups) per_stage += 5 + gr.geo.fx_split;
     return ctx->rk * per_stage;
@@ -1113,6 +1180,7 @@ void tuning_of(const ens_ctx *ctx, ens_tuning *t)
     std::memset(t, 0, sizeof *t);
     t->groups = (int)ctx->groups.size();
     t->parallel_groups = ctx->parallel_groups;
+    t->persistent = ctx->persistent;
     for (size_t gi = 0; gi < ctx->groups.size() && gi < ENS_MAX_GROUPS; ++gi) {
         const Geo &g = ctx->groups[gi].geo;
         ens_group_tuning &o = t->group[gi];
@@ -1134,6 +1202,14 @@ ens_status tuning_valid(const ens_ctx *ctx, const ens_tuning *t, std::string &wh
     }
     if (t->parallel_groups != 0 && t->parallel_groups != 1) {
         why = "parallel_groups must be 0 or 1";
+        return ENS_EINVAL;
+    }
+    if (t->persistent != 0 && t->persistent != 1) {
+        why = "persistent must be 0 or 1";
+        return ENS_EINVAL;
+    }
+    if (t->persistent == 1 && (!ctx->pitems || ctx->persist_ctas <= 0)) {
+        why = "the persistent stage kernel needs grid sizes among 128, 256 and 384";
         return ENS_EINVAL;
     }
     for (int gi = 0; gi < t->groups; ++gi) {
@@ -1175,7 +1251,10 @@ ens_status sync_nblk(ens_ctx *ctx)
 {
     for (auto &gr : ctx->groups) {
         const Geo &g = gr.geo;
-        const int nblk = g.fx_split ? (int)((g.sU + kUpdChunk - 1) / kUpdChunk) : g.NK * g.NZp / g.tile_x;
+        // the persistent stage kernel runs the fused update pass on 16-column tiles
+        const int nblk = ctx->persistent ? g.NK * g.NZp / 16
+                         : g.fx_split    ? (int)((g.sU + kUpdChunk - 1) / kUpdChunk)
+                                         : g.NK * g.NZp / g.tile_x;
         std::vector<int> v(g.members, nblk);
         ENS_CUDA(ctx, cudaMemcpy2DAsync(&ctx->md[g.first].nblk, sizeof(MemberDev), v.data(), sizeof(int),
                                         sizeof(int), g.members, cudaMemcpyHostToDevice, ctx->stream));
@@ -1189,6 +1268,7 @@ ens_status sync_nblk(ens_ctx *ctx)
 ens_status apply_tuning(ens_ctx *ctx, const ens_tuning *t)
 {
     ctx->parallel_groups = t->parallel_groups;
+    ctx->persistent = t->persistent;
     for (int gi = 0; gi < t->groups; ++gi) {
         Geo &g = ctx->groups[gi].geo;
         const ens_group_tuning &o = t->group[gi];
@@ -1378,6 +1458,11 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
     if (rs == ENS_OK && best.groups > 1) {
         cand = best;
         cand.parallel_groups = 1 - best.parallel_groups;
+        consider(cand);
+    }
+    if (rs == ENS_OK && ctx->pitems && ctx->persist_ctas > 0) {
+        cand = best;
+        cand.persistent = 1;
         consider(cand);
     }
     // install the winner (or, after an error, the starting tuning) and put

@@ -48,44 +48,7 @@ __global__ void k_state_sums(Geo g, MemberDev *md)
 __global__ void k_finish(MemberDev *md, const double *partial, int partial_blocks, int stage, int last_stage,
                          int mode)
 {
-    const int gm = blockIdx.x;
-    MemberDev &d = md[gm];
-    const int lane = threadIdx.x;
-    double e = 0.0, s = 0.0, b = 0.0;
-    const double *pp = partial + (long long)gm * partial_blocks * 4;
-    for (int k = lane; k < d.nblk; k += 32) {
-        e += pp[k * 4 + 0];
-        s += pp[k * 4 + 1];
-        b += pp[k * 4 + 2];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        e += __shfl_xor_sync(0xffffffffu, e, o);
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (lane != 0) return;
-    if (mode == 0 && stage == 0) d.dt = member_dt(d, d.N);
-    // injected power of the stage just taken: alpha(u^s) * 2 E_B(u^s)
-    if (mode == 0) d.P = d.alpha * 2.0 * d.EB;
-    d.E = e;
-    d.diss = s;
-    d.EB = b;
-    // a non-finite value anywhere in the fields reaches every mode through
-    // the nonlinear term and the transforms, hence these sums
-    if (!isfinite(e) || !isfinite(s)) d.flags |= kFlagNonFinite;
-    if (b > 0.0) {
-        d.alpha = d.eps_inj / (2.0 * b);
-    } else {
-        d.alpha = 0.0;
-        d.flags |= kFlagNoBandEnergy;
-    }
-    if (mode == 0 && last_stage) {
-        d.t += d.dt;
-        d.steps += 1;
-        d.umax = (double)__uint_as_float(d.umax_bits[0]);
-        for (int q = 0; q < 4; ++q) d.umax_bits[q] = 0u;
-    }
+    finish_body(md, partial, partial_blocks, stage, last_stage, mode, blockIdx.x, threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------

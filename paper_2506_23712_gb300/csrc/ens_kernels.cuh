@@ -127,19 +127,19 @@ __device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restri
 //   MODE 1: A_ij = i k_j u_i for ij = 11,12,13,21,22,23,31,32
 // grid (NK*NZp/T, members), block T*P.
 // ---------------------------------------------------------------------------
+// The pass bodies take their block coordinates (column tile bx, field,
+// member m) and shared memory as arguments: the __global__ kernels pass
+// blockIdx and their dynamic shared memory, the persistent stage kernel
+// (ens_persist.cu) the coordinates of the work item it runs.
 template <int N, int MODE, int T, int VAR = 0>
-__global__ void __launch_bounds__(ColCfg<N, T, VAR>::threads, ColCfg<N, T, VAR>::min_blocks)
-k_inv_x(Geo g, int use_S)
+__device__ __forceinline__ void inv_x_body(const Geo &g, int use_S, int bx, int m, float2 *sm)
 {
     using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P, V = PI::V;
-    constexpr int NF = MODE == 0 ? 6 : 8;
-    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N, *tile = buf + N * T;   // tile: [3][NK][T]
 
     const int c = threadIdx.x % T, p = threadIdx.x / T;
-    const int m = blockIdx.y;
-    const int col0 = blockIdx.x * T;                    // a tile never straddles ky (NZp % T == 0)
+    const int col0 = bx * T;                            // a tile never straddles ky (NZp % T == 0)
     const int col = col0 + c;
     const int iy = col / Dims<N>::NZP, kz = col % Dims<N>::NZP;
     const int kz0 = col0 % Dims<N>::NZP;                  // first kz of the tile
@@ -244,22 +244,27 @@ k_inv_x(Geo g, int use_S)
     }
 }
 
+template <int N, int MODE, int T, int VAR = 0>
+__global__ void __launch_bounds__(ColCfg<N, T, VAR>::threads, ColCfg<N, T, VAR>::min_blocks)
+k_inv_x(Geo g, int use_S)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    inv_x_body<N, MODE, T, VAR>(g, use_S, blockIdx.x, blockIdx.y, sm);
+}
+
 // ---------------------------------------------------------------------------
 // IY: inverse transform along y of buffer-A fields [f0, f0+nf) into B.
 // grid (N*NZp/T, nf, members).
 // ---------------------------------------------------------------------------
-template <int N, int T>
-__global__ void __launch_bounds__(ColCfg<N, T>::threads)
-k_inv_y(Geo g, int f0)
+template <int N, int T, int VAR = 0>
+__device__ __forceinline__ void inv_y_body(const Geo &g, int bx, int f, int m, float2 *sm)
 {
-    using PI = PlanInfo<N>;
+    using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P, V = PI::V;
-    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N;
     load_twiddles(tw, g.tw, N);
     const int c = threadIdx.x % T, p = threadIdx.x / T;
-    const int f = f0 + blockIdx.y, m = blockIdx.z;
-    const int col = blockIdx.x * T + c;       // (x, kz) flat
+    const int col = bx * T + c;               // (x, kz) flat
     const bool valid = (col % Dims<N>::NZP) < Dims<N>::NZ;
     const long long row = (long long)N * Dims<N>::NZP;
     const float2 *src = g.A + ((long long)m * kFields + f) * Dims<N>::SA + col;
@@ -272,29 +277,34 @@ k_inv_y(Geo g, int f0)
         const int iy = ky >= 0 ? ky : ky + Dims<N>::NK;
         v[i] = keep ? src[iy * row] : make_float2(0.f, 0.f);
     }
-    fft_line<N, false>(v, p, tw, [&](int pos) { return &buf[pos * T + c]; });
+    fft_line<N, false, VAR>(v, p, tw, [&](int pos) { return &buf[pos * T + c]; });
     if (valid) {
 #pragma unroll
         for (int i = 0; i < V; ++i) dst[PI::out_pos(p, i) * row] = v[i];
     }
 }
 
+template <int N, int T, int VAR = 0>
+__global__ void __launch_bounds__(ColCfg<N, T, VAR>::threads)
+k_inv_y(Geo g, int f0)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    inv_y_body<N, T, VAR>(g, blockIdx.x, f0 + blockIdx.y, blockIdx.z, sm);
+}
+
 // ---------------------------------------------------------------------------
 // FY: forward transform along y of B fields [0, nf) into A (kept ky only).
 // grid (N*NZp/T, nf, members).
 // ---------------------------------------------------------------------------
-template <int N, int T>
-__global__ void __launch_bounds__(ColCfg<N, T>::threads)
-k_fwd_y(Geo g)
+template <int N, int T, int VAR = 0>
+__device__ __forceinline__ void fwd_y_body(const Geo &g, int bx, int f, int m, float2 *sm)
 {
-    using PI = PlanInfo<N>;
+    using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P, V = PI::V;
-    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N;
     load_twiddles(tw, g.tw, N);
     const int c = threadIdx.x % T, p = threadIdx.x / T;
-    const int f = blockIdx.y, m = blockIdx.z;
-    const int col = blockIdx.x * T + c;
+    const int col = bx * T + c;
     const bool valid = (col % Dims<N>::NZP) < Dims<N>::NZ;
     const long long row = (long long)N * Dims<N>::NZP;
     const float2 *src = g.B + ((long long)m * kFields + f) * Dims<N>::SB + col;
@@ -302,7 +312,7 @@ k_fwd_y(Geo g)
     float2 v[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) v[i] = valid ? src[PI::in_pos(p, i) * row] : make_float2(0.f, 0.f);
-    fft_line<N, true>(v, p, tw, [&](int pos) { return &buf[pos * T + c]; });
+    fft_line<N, true, VAR>(v, p, tw, [&](int pos) { return &buf[pos * T + c]; });
     if (valid) {
 #pragma unroll
         for (int i = 0; i < V; ++i) {
@@ -310,6 +320,14 @@ k_fwd_y(Geo g)
             if (ky >= -Dims<N>::KC && ky <= Dims<N>::KC) dst[(ky >= 0 ? ky : ky + Dims<N>::NK) * row] = v[i];
         }
     }
+}
+
+template <int N, int T, int VAR = 0>
+__global__ void __launch_bounds__(ColCfg<N, T, VAR>::threads)
+k_fwd_y(Geo g)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    fwd_y_body<N, T, VAR>(g, blockIdx.x, blockIdx.y, blockIdx.z, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -542,6 +560,51 @@ __device__ __forceinline__ double member_dt(const MemberDev &d, int N)
     return dt;
 }
 
+// End of an RK stage for member gm (one warp, lane = 0..31): the FP64
+// partial sums of the update pass -> E, dissipation, band energy, the forcing
+// amplitude alpha = eps_inj / (2 E_B) of the next stage, the CFL step after the
+// first stage, time and step count after the last.
+__device__ __forceinline__ void finish_body(MemberDev *md, const double *partial, int partial_blocks, int stage,
+                                            int last_stage, int mode, int gm, int lane)
+{
+    MemberDev &d = md[gm];
+    double e = 0.0, s = 0.0, b = 0.0;
+    const double *pp = partial + (long long)gm * partial_blocks * 4;
+    for (int k = lane; k < d.nblk; k += 32) {
+        e += pp[k * 4 + 0];
+        s += pp[k * 4 + 1];
+        b += pp[k * 4 + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane != 0) return;
+    if (mode == 0 && stage == 0) d.dt = member_dt(d, d.N);
+    // injected power of the stage just taken: alpha(u^s) * 2 E_B(u^s)
+    if (mode == 0) d.P = d.alpha * 2.0 * d.EB;
+    d.E = e;
+    d.diss = s;
+    d.EB = b;
+    // a non-finite value anywhere in the fields reaches every mode through
+    // the nonlinear term and the transforms, hence these sums
+    if (!isfinite(e) || !isfinite(s)) d.flags |= kFlagNonFinite;
+    if (b > 0.0) {
+        d.alpha = d.eps_inj / (2.0 * b);
+    } else {
+        d.alpha = 0.0;
+        d.flags |= kFlagNoBandEnergy;
+    }
+    if (mode == 0 && last_stage) {
+        d.t += d.dt;
+        d.steps += 1;
+        d.umax = (double)__uint_as_float(d.umax_bits[0]);
+        for (int q = 0; q < 4; ++q) d.umax_bits[q] = 0u;
+    }
+}
+
 template <int NW>
 __device__ __forceinline__ void block_sum_to(double *out, double (&vals)[NW], double *scratch)
 {
@@ -567,17 +630,15 @@ __device__ __forceinline__ void block_sum_to(double *out, double (&vals)[NW], do
 }
 
 template <int N, int MODE, int T, int VAR = 0>
-__global__ void __launch_bounds__(ColCfg<N, T, VAR>::threads, ColCfg<N, T, VAR>::min_blocks)
-k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
+__device__ __forceinline__ void fwd_x_body(const Geo &g, MemberDev *md, int stage, int last_stage, int bx, int m,
+                                           float2 *sm)
 {
     using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P, V = PI::V;
-    extern __shared__ __align__(16) float2 sm[];
     float2 *tw = sm, *buf = sm + N, *tile = buf + N * T;   // tile: [3][NK][T]
     load_twiddles(tw, g.tw, N);
     const int c = threadIdx.x % T, p = threadIdx.x / T;
-    const int m = blockIdx.y;
-    const int col0 = blockIdx.x * T;
+    const int col0 = bx * T;
     const int col = col0 + c;                                  // (ky, kz) flat
     const int iy = col / Dims<N>::NZP, kz = col % Dims<N>::NZP;
     const int kz0 = col0 % Dims<N>::NZP;                  // first kz of the tile
@@ -731,9 +792,17 @@ k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
     if constexpr (MODE == 0) {
         __syncthreads();   // buf is reused as reduction scratch
         double vals[3] = {(double)se, (double)sd, (double)sb};
-        double *out = g.partial + ((long long)(g.first + m) * g.partial_blocks + blockIdx.x) * 4;
+        double *out = g.partial + ((long long)(g.first + m) * g.partial_blocks + bx) * 4;
         block_sum_to<3>(out, vals, reinterpret_cast<double *>(buf));
     }
+}
+
+template <int N, int MODE, int T, int VAR = 0>
+__global__ void __launch_bounds__(ColCfg<N, T, VAR>::threads, ColCfg<N, T, VAR>::min_blocks)
+k_fwd_x(Geo g, MemberDev *md, int stage, int last_stage)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    fwd_x_body<N, MODE, T, VAR>(g, md, stage, last_stage, blockIdx.x, blockIdx.y, sm);
 }
 
 }  // namespace ens

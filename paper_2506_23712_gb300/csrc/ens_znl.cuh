@@ -180,14 +180,20 @@ __device__ __forceinline__ void forward_pair_store_shfl(float2 *v, int p, int li
     }
 }
 
-template <int N, int VAR = 0>
-__global__ void __launch_bounds__(256, VAR == 0 && ZCfg<N, VAR>::smem_bytes() <= 110 * 1024 ? 2 : 1)
-k_znl(Geo g, MemberDev *md, int stage_idx)
+// Body of the z pass over the row groups [first + warp, T) of the group's
+// members (all members' row groups concatenated), stepping W per warp
+// iteration: the persistent kernel passes first = blockIdx.x WPB and
+// W = gridDim.x WPB over every row group; the persistent stage kernel
+// (ens_persist.cu) passes one member's chunk of row groups with W = WPB and
+// TASK set: the shared memory then serves other work next, so the warps
+// invalidate their barriers at the end.
+template <int N, int VAR = 0, bool TASK = false>
+__device__ __forceinline__ void znl_body(const Geo &g, MemberDev *md, int stage_idx, long long first, long long W,
+                                         long long T, unsigned char *smraw)
 {
     using C = ZCfg<N, VAR>;
     using PI = WPlanInfo<N, VAR>;
     constexpr int P = C::P, V = C::V, LPW = C::LPW, NZ2 = C::NZ2;
-    extern __shared__ __align__(16) unsigned char smraw[];
     float2 *tw = reinterpret_cast<float2 *>(smraw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(tw + N);
     float2 *stage = reinterpret_cast<float2 *>(bars + 2 * C::WPB);
@@ -207,9 +213,7 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
     TW.init(p, tw);
 
     const long long G = (long long)N * N / LPW;   // row groups per member
-    const long long T = G * g.members;
-    const long long W = (long long)gridDim.x * C::WPB;
-    long long grp = (long long)blockIdx.x * C::WPB + warp;
+    long long grp = first + warp;
     const uint32_t bytes = (uint32_t)(LPW * 6 * NZ2 * sizeof(float2));
     const long long skip_gi = g.z_skip_member >= 0 ? g.z_skip_member * G : -1;   // failure test only
     auto skipped = [&](long long gi) { return gi == skip_gi; };
@@ -322,15 +326,32 @@ k_znl(Geo g, MemberDev *md, int stage_idx)
         for (int i = 0; i < V; ++i) w[i] = make_float2(nzp[i], 0.f);
         fwd_pair(w, pend, nullptr);
     }
-    if (grp > (long long)blockIdx.x * C::WPB + warp || timed_out) flush(cur_m);
+    if (grp > first + warp || timed_out) flush(cur_m);
     if (timed_out) {
         // this warp's remaining row groups (this member's and those of every
         // later member of the group) stay unprocessed: flag them all
         if (lane == 0)
-            for (long long m = grp / G; m < g.members; ++m) atomicOr(&md[g.first + m].flags, kFlagTimeout);
+            for (long long m = grp / G; m <= (T - 1) / G; ++m) atomicOr(&md[g.first + m].flags, kFlagTimeout);
         // the refill of the other buffer may still be in flight: wait for it (bounded)
         if (grp + W < T) mbar_wait_warp(&bar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
     }
+    if constexpr (TASK) {
+        __syncwarp();
+        if (lane == 0) {
+            mbar_inval(&bar[0]);
+            mbar_inval(&bar[1]);
+        }
+    }
+}
+
+template <int N, int VAR = 0>
+__global__ void __launch_bounds__(256, VAR == 0 && ZCfg<N, VAR>::smem_bytes() <= 110 * 1024 ? 2 : 1)
+k_znl(Geo g, MemberDev *md, int stage_idx)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr long long G = (long long)N * N / ZCfg<N, VAR>::LPW;   // row groups per member
+    znl_body<N, VAR>(g, md, stage_idx, (long long)blockIdx.x * ZCfg<N, VAR>::WPB,
+                     (long long)gridDim.x * ZCfg<N, VAR>::WPB, G * g.members, smraw);
 }
 
 }  // namespace ens

@@ -84,7 +84,7 @@ class GroupTuning(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("groups", ctypes.c_int), ("parallel_groups", ctypes.c_int),
+    _fields_ = [("groups", ctypes.c_int), ("parallel_groups", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("group", GroupTuning * ENS_MAX_GROUPS), ("ms_per_step", ctypes.c_double),
                 ("trials", ctypes.c_int)]
 
@@ -224,7 +224,7 @@ _GROUP_KEYS = ("N", "tile_x", "tile_y", "z_variant", "z_ctas_per_sm", "plan_x", 
 
 
 def _tuning_dict(t: Tuning) -> dict:
-    return {"parallel_groups": t.parallel_groups,
+    return {"parallel_groups": t.parallel_groups, "persistent": t.persistent,
             "groups": [{k: getattr(t.group[i], k) for k in _GROUP_KEYS} for i in range(t.groups)],
             "ms_per_step": t.ms_per_step, "trials": t.trials}
 
@@ -239,6 +239,7 @@ def ens_set_tuning(ctx, tuning: dict):
     t = Tuning()
     t.groups = len(tuning["groups"])
     t.parallel_groups = int(tuning["parallel_groups"])
+    t.persistent = int(tuning.get("persistent", 0))
     for i, g in enumerate(tuning["groups"]):
         for k in _GROUP_KEYS:
             setattr(t.group[i], k, int(g[k]))
