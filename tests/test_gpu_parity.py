@@ -46,37 +46,37 @@ def oracle_member(m):
 
 
 @pytest.mark.parametrize("N", [16, 32, 64])
-def test_initial_field_matches_oracle(E, N):
+def test_initial_field_matches_oracle(E, N, parity_log):
     m = config0(E, N=N, k_hi=min(2, O.kc(N)), seed=7)
     ens = E.Ensemble([m])
     got = ens.field(0)
     ref = O.initial_field(oracle_member(m))
-    assert rel(got, ref) < 2e-6
+    assert parity_log("%d^3 seeded initial field, rel L2" % N, rel(got, ref), 2e-6) < 2e-6
     d = ens.diagnostics()[0]
     assert d["E"] == pytest.approx(0.5, rel=1e-5)
     ens.close()
 
 
 @pytest.mark.parametrize("N", [16, 32, 64, 128])
-def test_inverse_transform_matches_oracle(E, N):
+def test_inverse_transform_matches_oracle(E, N, parity_log):
     ens = E.Ensemble([config0(E, N=N)])
     uh = I.random_spectral(N, 100 + N)
     ens.set_field(0, uh)
     got = ens.velocity(0)
     ref = np.stack([O.irfft3(c) for c in uh])
-    assert rel(got, ref) < 2e-6
+    assert parity_log("%d^3 inverse transform, rel L2" % N, rel(got, ref), 2e-6) < 2e-6
     ens.close()
 
 
 @pytest.mark.parametrize("N", [16, 32, 64, 128])
-def test_forward_transform_matches_oracle(E, N):
+def test_forward_transform_matches_oracle(E, N, parity_log):
     ens = E.Ensemble([config0(E, N=N)])
     u = I.random_physical(N, N)
     ens.set_velocity(0, u)
     got = ens.field(0)
     ref = np.stack([O.rfft3(c) for c in u])
     ref[:, ~I.kept_mask(N)] = 0.0
-    assert rel(got, ref) < 2e-6
+    assert parity_log("%d^3 forward transform, rel L2" % N, rel(got, ref), 2e-6) < 2e-6
     ens.close()
 
 
@@ -98,17 +98,17 @@ def test_transform_round_trip_large(E, N):
 
 
 @pytest.mark.parametrize("N,rk", [(16, 2), (32, 2), (32, 3), (64, 3)])
-def test_rhs_matches_oracle(E, N, rk):
+def test_rhs_matches_oracle(E, N, rk, parity_log):
     m = config0(E, N=N, rk_order=rk, lam=0.4, k_lo=1, k_hi=2, seed=3)
     ens = E.Ensemble([m])
     F = ens.rhs(0)                       # at the library's own initial field
     om = oracle_member(m)
     Fref, nl, umax, alpha = O.rhs(om, O.initial_field(om))
-    assert rel(F, Fref) < 2e-6
+    assert parity_log("%d^3 right-hand side P N(u) + alpha u 1_B, rel L2" % N, rel(F, Fref), 2e-6) < 2e-6
     ens.close()
 
 
-def test_one_step_and_100_steps_config0(E):
+def test_one_step_and_100_steps_config0(E, parity_log):
     """32^3, nu = 0.02, band [1,2], IF-RK2, dt = 0.01 (the single-member
     configuration): rel L2 <= 1e-5 after 1 step, <= 1e-3 after 100."""
     m = config0(E)
@@ -118,16 +118,21 @@ def test_one_step_and_100_steps_config0(E):
     ens.step(1)
     st, d = O.step(om, ref, 1)
     assert st == 0
-    assert rel(ens.field(0), ref) < 1e-5
+    assert parity_log("32^3 RK2 field after 1 step, rel L2", rel(ens.field(0), ref), 1e-5) < 1e-5
     g = ens.diagnostics()[0]
+    parity_log("32^3 RK2 E after 1 step, rel error", abs(g["E"] / d["E"] - 1), 1e-5)
+    parity_log("32^3 RK2 dissipation after 1 step, rel error", abs(g["diss"] / d["diss"] - 1), None)
+    parity_log("32^3 injected power after 1 step, rel error", abs(g["P"] / 0.1 - 1), 1e-5)
     assert g["t"] == pytest.approx(0.01) and g["steps"] == 1
     assert g["E"] == pytest.approx(d["E"], rel=1e-5)
     assert g["P"] == pytest.approx(0.1, rel=1e-5)
     ens.step(99)
     st, d = O.step(om, ref, 99)
-    err = rel(ens.field(0), ref)
+    err = parity_log("32^3 RK2 field after 100 steps, rel L2", rel(ens.field(0), ref), 1e-3)
     assert err < 1e-3, err
     g = ens.diagnostics()[0]
+    parity_log("32^3 RK2 E after 100 steps, rel error", abs(g["E"] / d["E"] - 1), 1e-3)
+    parity_log("32^3 RK2 dissipation after 100 steps, rel error", abs(g["diss"] / d["diss"] - 1), None)
     assert g["steps"] == 100 and g["t"] == pytest.approx(1.0)
     assert g["E"] == pytest.approx(d["E"], rel=1e-3)
     ens.close()
@@ -145,7 +150,7 @@ def test_graph_and_direct_launch_agree(E):
     b.close()
 
 
-def test_cfl_rk3_ensemble_members_match_oracle(E):
+def test_cfl_rk3_ensemble_members_match_oracle(E, parity_log):
     """Several members of uneven lambda in one launch, RK3, CFL-adaptive
     step (Sec. IV: CFL = 0.2), each equal to its own oracle run."""
     lams = [-1.5, 0.0, 1.2]
@@ -158,7 +163,9 @@ def test_cfl_rk3_ensemble_members_match_oracle(E):
         om = oracle_member(m)
         ref = O.initial_field(om)
         st, d = O.step(om, ref, 2)
-        assert rel(ens.field(i), ref) < 1e-5
+        assert parity_log("32^3 RK3 CFL member lambda=%g, field after 2 steps, rel L2" % m.lam,
+                          rel(ens.field(i), ref), 1e-5) < 1e-5
+        parity_log("32^3 RK3 CFL member lambda=%g, dt rel error" % m.lam, abs(diags[i]["dt"] / d["dt"] - 1), 1e-5)
         assert diags[i]["dt"] == pytest.approx(d["dt"], rel=1e-5)
         assert diags[i]["P"] == pytest.approx(math.exp(m.lam) * 0.1, rel=1e-5)
     ens.close()
@@ -179,7 +186,7 @@ def test_uneven_sizes_in_one_context(E):
     ens.close()
 
 
-def test_statistics_match_oracle(E):
+def test_statistics_match_oracle(E, parity_log):
     m = config0(E, init_energy=2.0)
     N = m.N
     h = E.hist_spec(qr_bins=64, q_lim=10.0, r_lim=10.0, tail_bins=256, tail_lo=-8, tail_hi=8, eps_norm=0.1,
@@ -202,8 +209,12 @@ def test_statistics_match_oracle(E):
     for lo, hi in ((0, 64 * 64), (64 * 64, 64 * 64 + 256), (64 * 64 + 256, 64 * 64 + 512)):
         assert c[lo:hi].sum() + 0 == pytest.approx(r[lo:hi].sum(), abs=max(4, 1e-3 * r[lo:hi].sum()))
         big = r[lo:hi] > 1000
+        parity_log("32^3 statistics of the stepped field, bins %d-%d, max deviation (bins > 1000)" % (lo, hi),
+                   float((np.abs(c[lo:hi][big] - r[lo:hi][big]) / r[lo:hi][big]).max()), 0.02)
         assert np.all(np.abs(c[lo:hi][big] - r[lo:hi][big]) <= 0.02 * r[lo:hi][big])
     # moments: FP32 per point, FP64 reductions
+    parity_log("32^3 moment sums (A_ij^2, eps, omega^2), max rel error",
+               max(abs(mom[0, k] / rm2[k] - 1) for k in list(range(0, 36, 4)) + [38, 39]), 1e-4)
     for k in list(range(0, 36, 4)) + [38, 39]:
         assert mom[0, k] == pytest.approx(rm2[k], rel=1e-4)
     # <Q> = <R> = 0 (Sec. V definitions; periodic box): sums small vs |Q| scale
@@ -259,7 +270,7 @@ def test_gradient_component_histograms_match_oracle(E):
     ens.close()
 
 
-def test_mixture_matches_oracle(E):
+def test_mixture_matches_oracle(E, parity_log):
     lams = [-1.0, -0.3, 0.4, 1.1]
     ms = [E.Member(N=16, nu=0.05, lam=l, k_lo=1, k_hi=2, dt=0.01, rk_order=2, seed=i) for i, l in enumerate(lams)]
     h = E.hist_spec(qr_bins=16, q_lim=5.0, r_lim=5.0, tail_bins=32, tail_lo=-4, tail_hi=3, eps_norm=0.1,
@@ -277,6 +288,10 @@ def test_mixture_matches_oracle(E):
         w, cov = OM.member_weights(lams, kind, **kw)
         assert np.allclose(got["weights"], w, rtol=1e-12, atol=1e-15)
         qr, pe, pw = OM.mix_counts(counts, w, oh)
+        parity_log("mixture (%s): weights, max rel error" % kind,
+                   float(np.max(np.abs(got["weights"] - w) / np.abs(w))), 1e-12)
+        parity_log("mixture (%s): Q-R PDF, max abs error / max" % kind,
+                   float(np.max(np.abs(got["pdf_qr"] - qr)) / np.max(qr)), 1e-12)
         assert np.allclose(got["pdf_qr"], qr, rtol=1e-12, atol=1e-15)
         assert np.allclose(got["pdf_eps"], pe, rtol=1e-12, atol=1e-15)
         npts = counts[:, -2]
@@ -417,7 +432,7 @@ def test_histogram_layout_too_large_is_refused(E, capfd):
 
 
 @pytest.mark.parametrize("N", [16, 64, 128, pytest.param(384, marks=pytest.mark.slow)])
-def test_statistics_pass_shapes_match_oracle_on_same_field(E, N):
+def test_statistics_pass_shapes_match_oracle_on_same_field(E, N, parity_log):
     """The statistics pass in each of its launch shapes (several rows per
     warp at N <= 128, several CTAs per member from N = 64, the XOR-swizzled
     non-power-of-two plan at 384) against the oracle's statistics of the very
@@ -436,6 +451,10 @@ def test_statistics_pass_shapes_match_oracle_on_same_field(E, N):
     L = len(r)
     assert c[L - 2] == r[L - 2] == N ** 3
     big = r > 1000
+    parity_log("%d^3 statistics pass on the same field, max bin deviation (bins > 1000)" % N,
+               float((np.abs(c[big] - r[big]) / r[big]).max()), 0.02)
+    parity_log("%d^3 statistics pass on the same field, moment sums max rel error" % N,
+               max(abs(mom[0, k] / rm[k] - 1) for k in list(range(0, 36, 4)) + [38, 39]), 1e-4)
     assert np.all(np.abs(c[big] - r[big]) <= 0.02 * r[big])
     assert abs(int(c.sum()) - int(r.sum())) <= 1e-3 * r.sum()
     for k in list(range(0, 36, 4)) + [38, 39]:
