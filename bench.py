@@ -372,6 +372,8 @@ def held_out_gain(E, lams, counts, h, steps):
     P = np.array([norm(c) for c in cnt_s])
     ev = np.arange(0, len(lam_s), 2)
     od = np.arange(1, len(lam_s) - 1, 2)
+    if len(od) == 0:
+        return {"note": "fewer than three members: no held-out member"}
     S = E.Surrogate(seed=5)
     S.train(lam_s[ev], cnt_s[ev], h, steps, lr=4e-3)
     q = S.density(lam_s[od], h)

@@ -241,9 +241,7 @@ __device__ __forceinline__ float dsilu(float z)
 
 // BF16 rounding (round to nearest, ties to even) on the integer pipe: the
 // upper 16 bits of the result are the BF16 of f, bit for bit the conversion
-// instruction's result for every non-NaN f (a NaN stays a NaN).  The fused
-// inference rounds three activations per weight-row element, and the
-// conversion instruction shares the special-function unit with tanh.
+// instruction's result for every non-NaN f (a NaN stays a NaN).
 __device__ __forceinline__ uint32_t bf16_rne_bits(float f)
 {
     const uint32_t u = __float_as_uint(f);
@@ -254,8 +252,36 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
     return __byte_perm(bf16_rne_bits(lo), bf16_rne_bits(hi), 0x7632);
 }
+// the same with the conversion instruction (round to nearest even, one
+// instruction for the pair): the fused inference's epilogues, where it
+// measured faster than the integer-pipe form
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo, float hi)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
 // f rounded to BF16, as FP32
 __device__ __forceinline__ float round_bf16(float f) { return __uint_as_float(bf16_rne_bits(f) & 0xFFFF0000u); }
+
+// a * b + c on both halves with one packed FP32x2 instruction (each half
+// rounded as the scalar FMA)
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)),
+          "l"(*reinterpret_cast<const unsigned long long *>(&c)));
+    return *reinterpret_cast<const float2 *>(&r);
+}
+// SiLU of two pre-activations in the halved form h = (z + b) / 2 (see
+// silu_h): the FMAs packed, one hardware tanh per element
+__device__ __forceinline__ float2 silu_pair(float2 v, float2 bh)
+{
+    const float2 h = fma2(make_float2(0.5f, 0.5f), v, bh);
+    return fma2(h, make_float2(tanh_approx(h.x), tanh_approx(h.y)), h);
+}
 
 // Z += bias (kept, FP32, for the backward pass); H = SiLU(Z) as BF16 (and H^T)
 __global__ void k_bias_silu(float *Z, const float *bias, long long rows, __nv_bfloat16 *H, __nv_bfloat16 *Ht)
@@ -548,34 +574,66 @@ __global__ void k_init_params(float *p, long long n, unsigned long long seed)
     p[i] = u * scale;
 }
 
+// Feature rows of the fused inference: every bin's row with lambda = 0, as
+// packed BF16 pairs (the row does not depend on lambda except for input 2),
+// and per lambda value the BF16 of lambda / 5, which the kernel puts in
+// place of input 2 (the low half of word 1): the same bits as computing the
+// row for that lambda.
+__global__ void k_feature_table(RowSpec rs, const double *lams, int nlam, uint4 *ftab, uint32_t *lam5)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nlam) lam5[i] = bf16_rne_bits((float)(lams[i] / 5.0)) >> 16;
+    if (i >= rs.per_member) return;
+    float f[kIn];
+    row_features(rs, 0.0, i, f);
+    uint32_t w[kIn / 2];
+#pragma unroll
+    for (int j = 0; j < kIn / 2; ++j) w[j] = pack_bf16x2(f[2 * j], f[2 * j + 1]);
+#pragma unroll
+    for (int j = 0; j < kIn / 8; ++j) ftab[(long long)i * (kIn / 8) + j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+}
+
 // ---------------------------------------------------------------------------
 // Fused inference: features -> 3 x (tcgen05 GEMM + bias + SiLU) -> head, per
 // 128-row tile, activations never leave the SM.  Persistent CTAs (one per
-// SM, 256 threads); per CTA one 256-column FP32 accumulator in TMEM.
+// SM, 16 epilogue warps and one MMA warp); per CTA two 256-column FP32
+// accumulators in TMEM, used by the layers in turn.
 //   shared memory: H  4 K-blocks of 128 rows x 64 BF16 (64 KB; K-block 0
 //                     also holds the features of the tile)
-//                  W1 image (32 KB, loaded once), W2 or W3 image (128 KB,
+//                  W1 image (32 KB, loaded once), W2 or W3 image (128 KB in
+//                     four 32 KB K-blocks, each with its own barrier,
 //                     refilled by bulk copies while the epilogues run)
-//   per tile: features -> MMA(H0, W1) -> epilogue -> MMA(H, W2) -> [copy W3]
-//             epilogue -> MMA(H, W3) -> [copy W2] -> epilogue + head
-// The epilogue warp w reads TMEM lanes 32 (w mod 4) .. +31 (its rows) and
-// columns 64 (w / 4) .. +63 (16 warps: four per lane quarter).  Every mbarrier wait is bounded; a wait that
-// gives up sets *err, waits (bounded) for the copies and MMAs in flight,
-// frees the TMEM and returns.
+// The epilogue of a layer (TMEM -> bias + SiLU -> BF16 A operand of the next
+// layer in H) runs in four 64-column chunks, all warps on chunk 0 first: as
+// soon as every epilogue warp has written chunk c (a per-chunk barrier, one
+// arrival per warp) and K-block c of the next weights has landed, the MMA
+// warp issues the next layer's MMAs on K-block c into the other
+// accumulator, so the tensor cores work while the epilogue proceeds.  The head of a tile (dot product with w4) runs while
+// the next tile's layer-1 MMAs do.
+//   per tile: features -> MMA1 (acc a) -> [head of the previous tile]
+//             epilogue1 | MMA2 (acc a^1) -> [copy W3] epilogue2 | MMA3 (acc a)
+//             -> [copy W2]
+// Epilogue warp w reads TMEM lanes 32 (w mod 4) .. +31 (its rows) and, in
+// chunk c, columns 64 c + 16 (w / 4) .. +15 (the four chunks' loads issued at
+// once).  Every mbarrier wait is bounded; a wait
+// that gives up sets *err, waits (bounded) for the copies and MMAs in
+// flight, frees the TMEM and returns.
 // ---------------------------------------------------------------------------
-constexpr int kInferThreads = 512;
+constexpr int kInferWarps = 16;                       // epilogue warps
+constexpr int kInferThreads = 32 * (kInferWarps + 1);   // + the MMA warp
 
 // biases and head weights by value: kernel parameters live in the constant
-// bank, so the epilogue's warp-uniform reads are broadcasts
+// bank, read in pairs by the epilogues (warp-uniform addresses: broadcasts)
 struct MlpBias {
     float b1[kHid], b2[kHid], b3[kHid];   // halved: the epilogues form (z + b) / 2 in one FMA
     float w4[kHid];
     float b4;
 };
-constexpr size_t kInferSmem = 1024 + 65536 + 32768 + 131072 + 64;
+constexpr size_t kInferSmem = 1024 + 65536 + 32768 + 131072 + 128;
 
 __global__ void __launch_bounds__(kInferThreads, 1)
-k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long long ntiles,
+k_mlp_infer(RowSpec rs, const uint4 *__restrict__ ftab, const uint32_t *__restrict__ lam5, long long real,
+            long long ntiles,
             const unsigned char *__restrict__ img1, const unsigned char *__restrict__ img2,
             const unsigned char *__restrict__ img3, const __grid_constant__ MlpBias bias, float *__restrict__ logit,
             int *err)
@@ -586,16 +644,22 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
     unsigned char *sH = sm;                      // 64 KB
     unsigned char *sW1 = sm + 65536;             // 32 KB
     unsigned char *sW = sW1 + 32768;             // 128 KB
-    uint64_t *bar_mma = reinterpret_cast<uint64_t *>(sW + 131072);
-    uint64_t *bar_w = bar_mma + 1;
-    uint32_t *holder = reinterpret_cast<uint32_t *>(bar_w + 1);
-    float *part = reinterpret_cast<float *>(sH);   // head partials [4][128], once layer 3 is done
+    uint64_t *bar_l = reinterpret_cast<uint64_t *>(sW + 131072);   // a layer's MMAs complete
+    uint64_t *bar_w1 = bar_l + 1;                // W1 image landed
+    uint64_t *bar_w = bar_l + 2;                 // [4] K-block of the W2/W3 image landed
+    uint64_t *bar_c = bar_l + 6;                 // [4] epilogue chunk written by every thread
+    uint32_t *holder = reinterpret_cast<uint32_t *>(bar_l + 10);
+    float *part = reinterpret_cast<float *>(sH + 16384);   // head partials [4][128] in K-block 1 of H
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;   // half: which 64 columns (0..3)
-    if (warp == 0) tmem_alloc(holder, 256);
+    const int quarter = warp & 3, cpart = warp >> 2;
+    if (warp == 0) tmem_alloc(holder, 512);
     if (tid == 0) {
-        mbar_init(bar_mma, 1);
-        mbar_init(bar_w, 1);
+        mbar_init(bar_l, 1);
+        mbar_init(bar_w1, 1);
+        for (int c = 0; c < 4; ++c) {
+            mbar_init(&bar_w[c], 1);
+            mbar_init(&bar_c[c], kInferWarps);
+        }
         fence_mbar_init();
     }
     tc_fence_before();
@@ -603,93 +667,146 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
     tc_fence_after();
     const uint32_t taddr = *holder;
     constexpr uint32_t idesc = idesc_bf16(128, kHid);
-    uint32_t n_mma = 0, n_w = 0;   // completed phases expected on each barrier
+    uint32_t n_l = 0, n_w1 = 0, n_w = 0, n_c = 0;   // completed phases expected on each barrier (set)
     bool ok = true;
-    auto copy_w = [&](const unsigned char *img, unsigned char *dst, uint32_t bytes) {   // thread 0
-        mbar_arrive_expect_tx(bar_w, bytes);
-        for (uint32_t o = 0; o < bytes; o += 32768) bulk_g2s(dst + o, img + o, 32768, bar_w);
+    auto copy_w = [&](const unsigned char *img) {   // thread 0: the four K-blocks of a W2/W3 image
+        for (int c = 0; c < 4; ++c) {
+            mbar_arrive_expect_tx(&bar_w[c], 32768);
+            bulk_g2s(sW + c * 32768, img + c * 32768, 32768, &bar_w[c]);
+        }
     };
     auto wait = [&](uint64_t *bar, uint32_t &n) {   // the phase stays pending on failure
         const bool r = mbar_wait_warp(bar, n & 1);
         if (r) ++n;
         return r;
     };
-    // prologue: W1 and W2 images
     if (tid == 0) {
-        mbar_arrive_expect_tx(bar_w, 32768 + 131072);
-        bulk_g2s(sW1, img1, 32768, bar_w);
-        for (uint32_t o = 0; o < 131072; o += 32768) bulk_g2s(sW + o, img2 + o, 32768, bar_w);
+        mbar_arrive_expect_tx(bar_w1, 32768);
+        bulk_g2s(sW1, img1, 32768, bar_w1);
+        copy_w(img2);
     }
-    ok = wait(bar_w, n_w);
-    // issue one layer: D = A[kblocks] * W^T (thread 0), commit to bar_mma
-    auto mma_layer = [&](const unsigned char *W, int kblocks) {
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll 1
-            for (int kb = 0; kb < kblocks; ++kb) {
-                const uint64_t da = desc_sw128(sH + kb * 16384), db = desc_sw128(W + kb * 32768);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) tc_mma_bf16(taddr, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-            }
-            tc_commit(bar_mma);
-        }
-    };
+    ok = wait(bar_w1, n_w1);
     const int row = quarter * 32 + lane;                       // this thread's TMEM lane = tile row
     const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16);
-    // bias + SiLU of this thread's 64 columns into H (BF16, swizzled K-blocks);
-    // the second 32-column TMEM load is in flight while the first is processed
-    auto epilogue = [&](const float *bv) {
-        uint32_t ra[32], rb[32];
-        tc_ld_32cols_issue(tl + (uint32_t)(half * 64), ra);
-        tc_ld_wait(ra);
-        tc_ld_32cols_issue(tl + (uint32_t)(half * 64 + 32), rb);
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const int c0 = half * 64 + 32 * h2;
-            if (h2 == 1) tc_ld_wait(rb);
-            const uint32_t *rr = h2 == 0 ? ra : rb;
-            float v[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]);
-#pragma unroll
-            for (int j = 0; j < 32; j += 8) {
-                float bb[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) bb[t] = bv[c0 + j + t];
-                uint32_t w[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    w[t] = pack_bf16x2(silu_h(fmaf(0.5f, v[j + 2 * t], bb[2 * t])),
-                                       silu_h(fmaf(0.5f, v[j + 2 * t + 1], bb[2 * t + 1])));
-                }
-                const int col = c0 + j;
-                *reinterpret_cast<uint4 *>(sH + (col >> 6) * 16384 + sw128_offset(row, col & 63)) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
-            }
-        }
-    };
     auto publish = [&]() {   // generic smem writes -> tensor-core reads; TMEM reads done
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
     };
+    // Epilogue of the layer in accumulator `acc` (bias + SiLU into H, BF16,
+    // swizzled K-blocks) in four column chunks; warp 0 issues the next
+    // layer's MMAs (into `acc_next`, weights in sW) chunk by chunk and
+    // commits them to bar_l.  The load of chunk c + 1 is in flight while
+    // chunk c is processed.
+    auto epilogue_chain = [&](uint32_t acc, const float *bv, uint32_t acc_next) {
+        if (warp < kInferWarps) {
+            uint32_t r[4][16];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tc_ld_16cols_issue(tl + acc + (uint32_t)(64 * c + 16 * cpart), r[c]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tc_ld_wait16(r[c]);
+            const float2 *bv2 = reinterpret_cast<const float2 *>(bv);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t *rc = r[c];
+                const int col0 = 64 * c + 16 * cpart;
+                uint32_t w[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float2 y = silu_pair(make_float2(__uint_as_float(rc[2 * t]), __uint_as_float(rc[2 * t + 1])),
+                                               bv2[col0 / 2 + t]);
+                    w[t] = cvt_bf16x2(y.x, y.y);
+                }
+                unsigned char *blk = sH + c * 16384;
+                *reinterpret_cast<uint4 *>(blk + sw128_offset(row, 16 * cpart)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(blk + sw128_offset(row, 16 * cpart + 8)) =
+                    make_uint4(w[4], w[5], w[6], w[7]);
+                fence_proxy_async_smem();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_c[c]);
+            }
+        } else {
+            // the MMA warp: K-block c of the next layer once chunk c is
+            // written and K-block c of its weights has landed
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                ok = ok && mbar_wait_warp(&bar_c[c], n_c & 1) && mbar_wait_warp(&bar_w[c], n_w & 1);
+                if (ok && lane == 0) {
+                    tc_fence_after();
+                    const uint64_t da = desc_sw128(sH + c * 16384), db = desc_sw128(sW + c * 32768);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        tc_mma_bf16(taddr + acc_next, da + 2 * k, db + 2 * k, idesc, (c > 0 || k > 0) ? 1u : 0u);
+                    if (c == 3) tc_commit(bar_l);
+                }
+                __syncwarp();
+            }
+        }
+        ++n_c;
+        ++n_w;
+    };
+    // head of a finished tile: logit = sum_c BF16(SiLU(z3 + b3)) w4 + b4
+    auto head = [&](uint32_t acc, long long r0) {
+        if (warp < kInferWarps) {
+            uint32_t r[4][16];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tc_ld_16cols_issue(tl + acc + (uint32_t)(64 * c + 16 * cpart), r[c]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tc_ld_wait16(r[c]);
+            const float2 *b3 = reinterpret_cast<const float2 *>(bias.b3);
+            const float2 *w4 = reinterpret_cast<const float2 *>(bias.w4);
+            float2 sum = make_float2(0.f, 0.f);   // even and odd columns
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t *rc = r[c];
+                const int col0 = 64 * c + 16 * cpart;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float2 y = silu_pair(make_float2(__uint_as_float(rc[2 * t]), __uint_as_float(rc[2 * t + 1])),
+                                               b3[col0 / 2 + t]);
+                    const uint32_t hb = cvt_bf16x2(y.x, y.y);   // the activations rounded to BF16
+                    sum = fma2(make_float2(__uint_as_float(hb << 16), __uint_as_float(hb & 0xFFFF0000u)),
+                               w4[col0 / 2 + t], sum);
+                }
+            }
+            part[cpart * 128 + row] = sum.x + sum.y;
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (tid < 128 && r0 + tid < real)
+            logit[r0 + tid] = ((part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid])) + bias.b4;
+    };
     // features of a tile's rows (threads 0..127, one row each) as packed BF16
-    // pairs; computed for the next tile while the layer-3 MMAs of this one run
+    // pairs: the bin's row of the feature table with lambda / 5 in place;
+    // fetched for the next tile while the last layer-3 MMAs run
     uint32_t fw[kIn / 2];
     auto features = [&](long long t) {
-        float f[kIn];
         const long long rr = t * 128 + tid;
-        if (rr < real) row_features(rs, lams[rr / rs.per_member], (int)(rr % rs.per_member), f);
-        else
-            for (int i = 0; i < kIn; ++i) f[i] = 0.f;
+        if (rr < real) {
+            const int li = (int)(rr / rs.per_member);
+            const long long bin = rr - (long long)li * rs.per_member;
 #pragma unroll
-        for (int j = 0; j < kIn / 2; ++j) fw[j] = pack_bf16x2(f[2 * j], f[2 * j + 1]);
+            for (int j = 0; j < kIn / 8; ++j) {
+                const uint4 x = ftab[bin * (kIn / 8) + j];
+                fw[4 * j] = x.x;
+                fw[4 * j + 1] = x.y;
+                fw[4 * j + 2] = x.z;
+                fw[4 * j + 3] = x.w;
+            }
+            fw[1] = (fw[1] & 0xFFFF0000u) | lam5[li];
+        } else {
+#pragma unroll
+            for (int j = 0; j < kIn / 2; ++j) fw[j] = 0u;
+        }
     };
     if (tid < 128 && (long long)blockIdx.x < ntiles) features(blockIdx.x);
+    uint32_t a = 0;              // accumulator (TMEM column offset) of the next layer
+    long long prev = -1;         // tile whose head is pending
+    uint32_t acc_prev = 0;
 #pragma unroll 1
     for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-        const long long r0 = tile * 128;
-        // features of the tile into K-block 0 of H
+        // features of the tile into K-block 0 of H (layer 3 of the previous tile is done)
         if (tid < 128) {
 #pragma unroll
             for (int j = 0; j < kIn; j += 8)
@@ -697,79 +814,52 @@ k_mlp_infer(RowSpec rs, const double *__restrict__ lams, long long real, long lo
                     make_uint4(fw[j / 2], fw[j / 2 + 1], fw[j / 2 + 2], fw[j / 2 + 3]);
         }
         publish();
-        // layer 1 (K = 64): the W2 image of this tile may still be arriving
-        mma_layer(sW1, 1);
-        ok = wait(bar_mma, n_mma);
-        if (tile != blockIdx.x) ok = ok && wait(bar_w, n_w);   // W2 refilled during the last epilogue
-        tc_fence_after();
-        if (!__syncthreads_and(ok)) break;
-        epilogue(bias.b1);
-        publish();
-        // layer 2, then W3 streams in while the epilogue runs
-        mma_layer(sW, 4);
-        ok = wait(bar_mma, n_mma);
-        tc_fence_after();
-        if (!__syncthreads_and(ok)) break;
-        if (tid == 0) copy_w(img3, sW, 131072);
-        epilogue(bias.b2);
-        publish();
-        ok = wait(bar_w, n_w);
-        if (!__syncthreads_and(ok)) break;
-        mma_layer(sW, 4);
-        // the next tile's features while the layer-3 MMAs run
-        if (tid < 128 && tile + gridDim.x < ntiles) features(tile + gridDim.x);
-        ok = wait(bar_mma, n_mma);
-        tc_fence_after();
-        if (!__syncthreads_and(ok)) break;
-        if (tid == 0) copy_w(img2, sW, 131072);   // for the next tile
-        // head: logit = sum_c BF16(SiLU(z3 + b3)) w4 + b4
-        float acc = 0.f;
-        uint32_t ra[32], rb[32];
-        tc_ld_32cols_issue(tl + (uint32_t)(half * 64), ra);
-        tc_ld_wait(ra);
-        tc_ld_32cols_issue(tl + (uint32_t)(half * 64 + 32), rb);
+        // layer 1 (K = 64) into accumulator a
+        const uint32_t a1 = a;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint64_t da = desc_sw128(sH), db = desc_sw128(sW1);
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const int c0 = half * 64 + 32 * h2;
-            if (h2 == 1) tc_ld_wait(rb);
-            const uint32_t *rr = h2 == 0 ? ra : rb;
-            float v[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]);
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-                float bb[4], ww[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    bb[t] = bias.b3[c0 + j + t];
-                    ww[t] = bias.w4[c0 + j + t];
-                }
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const float h = round_bf16(silu_h(fmaf(0.5f, v[j + t], bb[t])));
-                    acc = fmaf(h, ww[t], acc);
-                }
-            }
+            for (int k = 0; k < 4; ++k) tc_mma_bf16(taddr + a1, da + 2 * k, db + 2 * k, idesc, k > 0 ? 1u : 0u);
+            tc_commit(bar_l);
         }
-        part[half * 128 + row] = acc;
-        tc_fence_before();
-        __syncthreads();
-        if (tid < 128 && r0 + tid < real)
-            logit[r0 + tid] = ((part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid])) + bias.b4;
-        __syncthreads();   // part (in H) is rewritten by the next tile's features
+        a ^= 256;
+        // the previous tile's head reads the other accumulator meanwhile
+        if (prev >= 0) head(acc_prev, prev * 128);
+        ok = wait(bar_l, n_l);
+        tc_fence_after();
+        if (!__syncthreads_and(ok)) break;
+        // epilogue 1, layer-2 MMAs chunk by chunk into accumulator a
+        const uint32_t a2 = a;
+        epilogue_chain(a1, bias.b1, a2);
+        a ^= 256;
+        ok = ok && wait(bar_l, n_l);
+        tc_fence_after();
+        if (!__syncthreads_and(ok)) break;
+        if (tid == 0) copy_w(img3);   // the layer-2 MMAs no longer read sW
+        // epilogue 2, layer-3 MMAs chunk by chunk as the W3 K-blocks land
+        const uint32_t a3 = a;
+        epilogue_chain(a2, bias.b2, a3);
+        a ^= 256;
+        // the next tile's features while the last layer-3 MMAs run
+        if (tid < 128 && tile + gridDim.x < ntiles) features(tile + gridDim.x);
+        ok = ok && wait(bar_l, n_l);
+        tc_fence_after();
+        if (!__syncthreads_and(ok)) break;
+        if (tid == 0 && tile + gridDim.x < ntiles) copy_w(img2);   // for the next tile
+        prev = tile;
+        acc_prev = a3;
     }
+    if (ok && prev >= 0) head(acc_prev, prev * 128);
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
         // copies or MMAs may still be in flight: bounded waits before freeing
-        mbar_wait_warp(bar_w, n_w & 1);
-        mbar_wait_warp(bar_mma, n_mma & 1);
-    } else if (n_w > 0 && ntiles > (long long)blockIdx.x) {
-        // the last tile started a W2 refill nobody consumes: let it land
-        mbar_wait_warp(bar_w, n_w & 1);
+        for (int c = 0; c < 4; ++c) mbar_wait_warp(&bar_w[c], n_w & 1);
+        mbar_wait_warp(bar_l, n_l & 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(taddr, 256);
+    if (warp == 0) tmem_dealloc(taddr, 512);
 }
 
 }  // namespace ens
@@ -793,6 +883,7 @@ struct ens_surrogate {
     float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *logit = nullptr, *dlogit = nullptr, *q = nullptr,
           *target = nullptr, *dH = nullptr, *part = nullptr;
     double *lam = nullptr, *loss = nullptr, *wq = nullptr, *pdf = nullptr;
+    uint32_t *lam5 = nullptr;   // BF16 of lambda / 5 per lambda value (fused inference)
     int groups_cap = 0;
     unsigned char *img = nullptr;   // swizzled W1 | W2 | W3 images for the fused inference kernel
     int sms = 0;
@@ -809,7 +900,7 @@ bool alloc_work(ens_surrogate *S, long long rows, int groups)
     for (void *p : {(void *)S->X, (void *)S->Xt, (void *)S->H1, (void *)S->H2, (void *)S->H3, (void *)S->H1t,
                     (void *)S->H2t, (void *)S->dZ, (void *)S->dZt, (void *)S->Z1, (void *)S->Z2, (void *)S->Z3,
                     (void *)S->logit, (void *)S->dlogit, (void *)S->q, (void *)S->target, (void *)S->dH,
-                    (void *)S->part, (void *)S->lam, (void *)S->loss})
+                    (void *)S->part, (void *)S->lam, (void *)S->lam5, (void *)S->loss})
         fr(p);
     bool ok = true;
     auto al = [&](auto **p, size_t bytes) {
@@ -828,6 +919,7 @@ bool alloc_work(ens_surrogate *S, long long rows, int groups)
     al(&S->target, sizeof(float) * rows);
     al(&S->part, sizeof(float) * kMaxSplit * kHid * kHid);
     al(&S->lam, sizeof(double) * 4096);
+    al(&S->lam5, sizeof(uint32_t) * 4096);
     al(&S->loss, sizeof(double) * (groups + 1));
     S->cap = ok ? rows : 0;
     S->groups_cap = ok ? groups : 0;
@@ -885,7 +977,10 @@ bool forward_fused(ens_surrogate *S, const RowSpec &rs, long long real)
     k_pack_weights_img<<<blocks(n, 256), 256, 0, s>>>(S->p, S->img, S->img + 32768, S->img + 32768 + 131072);
     const long long ntiles = (real + 127) / 128;
     const int grid = (int)std::min<long long>(ntiles, S->sms > 0 ? S->sms : 1);
-    k_mlp_infer<<<grid, kInferThreads, kInferSmem, s>>>(rs, S->lam, real, ntiles, S->img, S->img + 32768,
+    const int nlam = (int)(real / rs.per_member);
+    uint4 *ftab = reinterpret_cast<uint4 *>(S->Xt);   // the training path's transposed features: free here
+    k_feature_table<<<blocks(std::max(rs.per_member, nlam), 256), 256, 0, s>>>(rs, S->lam, nlam, ftab, S->lam5);
+    k_mlp_infer<<<grid, kInferThreads, kInferSmem, s>>>(rs, ftab, S->lam5, real, ntiles, S->img, S->img + 32768,
                                                        S->img + 32768 + 131072, bias, S->logit, S->err);
     return cudaGetLastError() == cudaSuccess;
 }
@@ -1001,7 +1096,7 @@ ens_status ens_surrogate_destroy(ens_surrogate *S)
                     (void *)S->X, (void *)S->Xt, (void *)S->H1, (void *)S->H2, (void *)S->H3, (void *)S->H1t,
                     (void *)S->H2t, (void *)S->dZ, (void *)S->dZt, (void *)S->Z1, (void *)S->Z2, (void *)S->Z3,
                     (void *)S->logit, (void *)S->dlogit, (void *)S->q, (void *)S->target, (void *)S->dH,
-                    (void *)S->part, (void *)S->lam, (void *)S->loss})
+                    (void *)S->part, (void *)S->lam, (void *)S->lam5, (void *)S->loss})
         if (p) cudaFree(p);
     delete S;
     return ENS_OK;
@@ -1237,9 +1332,12 @@ ens_status ens_surrogate_time_infer(ens_surrogate *S, const ens_hist_spec *h, in
                                                                               S->img + 32768 + 131072);
     MlpBias bias;
     if (!mlp_bias(S, &bias)) return ENS_ECUDA;
+    uint4 *ftab = reinterpret_cast<uint4 *>(S->Xt);
+    k_feature_table<<<blocks(std::max(rs.per_member, nquad), 256), 256, 0, S->s>>>(rs, S->lam, nquad, ftab, S->lam5);
     auto launch = [&]() {
-        k_mlp_infer<<<grid, kInferThreads, kInferSmem, S->s>>>(rs, S->lam, real, ntiles, S->img, S->img + 32768,
-                                                               S->img + 32768 + 131072, bias, S->logit, S->err);
+        k_mlp_infer<<<grid, kInferThreads, kInferSmem, S->s>>>(rs, ftab, S->lam5, real, ntiles, S->img,
+                                                               S->img + 32768, S->img + 32768 + 131072, bias,
+                                                               S->logit, S->err);
     };
     launch();   // warm-up
     cudaEvent_t a, b;
