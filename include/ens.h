@@ -199,7 +199,10 @@ ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
  * copy streams while a chunk computes.  Overlap needs page-locked host
  * memory; pageable memory gives the same results without it.  The device
  * copy of the state and the diagnostics end as after ens_set_state,
- * ens_step and ens_get_state; the call returns once host_out is written.
+ * ens_step and ens_get_state, to FP32 rounding (bit for bit where each
+ * member's z-pass rows go through the same warp streams in a chunk as in
+ * the whole group: the z pass pairs the n_z rows of a stream into one
+ * complex line); the call returns once host_out is written.
  * ENS_EINVAL for null buffers, too few bytes or chunk < 0. */
 ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size_t bytes, int chunk);
 
@@ -216,6 +219,11 @@ ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size
  *                   projection, forcing, RK update in one launch); 1: two
  *                   launches (transform into a compact spectral buffer, then
  *                   a streaming update), more HBM bytes, lighter kernels;
+ *                   2 (N = 256 only): fused, in persistent CTAs of two warp
+ *                   groups (one transforms a column tile while the other
+ *                   updates the previous tile, its state reads overlapping
+ *                   the transforms; the fields and sums of fx_split 0 with
+ *                   16-column tiles, bit for bit);
  *   z_variant       0: persistent TMA-pipelined z pass with z_ctas_per_sm
  *                   CTAs per SM (1 .. the kernel's occupancy limit),
  *                   1: one CTA per group of rows (z_ctas_per_sm unused
@@ -262,7 +270,7 @@ ens_status ens_get_tuning(const ens_ctx *ctx, ens_tuning *out);
 ens_status ens_set_tuning(ens_ctx *ctx, const ens_tuning *t);
 /* Time the variants on this context's own members and install the fastest:
  * coordinate descent over plan_x, tile_x, tile_y, the z variant and its CTAs
- * per SM, fx_split for each group, then parallel_groups, then persistent
+ * per SM, fx_split (0, 1, 2) for each group, then parallel_groups, then persistent
  * (where available); each trial restores the member
  * state from a device snapshot, runs one untimed step and times `steps`
  * graph replays with CUDA events; a candidate wins only if it is more than

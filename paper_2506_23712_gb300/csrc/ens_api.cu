@@ -502,6 +502,7 @@ static ens_status init_context(ens_ctx *ctx, const ens_member_desc *m, int n, co
         const int per_sm = znl_ctas_per_sm(gr.geo.N);
         if (per_sm <= 0 || ctx->sms <= 0) return fail(ctx, ENS_ECUDA, "occupancy query of the z pass failed");
         gr.geo.z_ctas = per_sm * ctx->sms;
+        gr.geo.sms = ctx->sms;
         launch_twiddles(const_cast<float2 *>(gr.geo.tw), gr.geo.N, st);
         ENS_CUDA(ctx, cudaMemsetAsync(gr.geo.U, 0, sizeof(float2) * 3 * gr.geo.sU * gr.geo.members, st));
         ENS_CUDA(ctx, cudaMemsetAsync(gr.geo.S, 0, sizeof(float2) * 3 * gr.geo.sU * gr.geo.members, st));
@@ -644,7 +645,7 @@ int ens_kernels_per_step(const ens_ctx *ctx)
     if (!ctx) return 0;
     if (ctx->persistent) return ctx->rk;   // one persistent launch per stage
     int per_stage = 1;   // the per-member stage reduction
-    for (auto &gr : ctx->groups) per_stage += 5 + gr.geo.fx_split;
+    for (auto &gr : ctx->groups) per_stage += 5 + (gr.geo.fx_split == 1 ? 1 : 0);
     return ctx->rk * per_stage;
 }
 
@@ -1228,8 +1229,8 @@ ens_status tuning_valid(const ens_ctx *ctx, const ens_tuning *t, std::string &wh
             why = "plan_x must be 0, or 1 for N = 128, 256, 512";
             return ENS_EINVAL;
         }
-        if (o.fx_split != 0 && o.fx_split != 1) {
-            why = "fx_split must be 0 or 1";
+        if (o.fx_split < 0 || o.fx_split > 2 || (o.fx_split == 2 && !fx_ws_available(N))) {
+            why = "fx_split must be 0, 1, or 2 for N = 256";
             return ENS_EINVAL;
         }
         if (o.z_variant < 0 || o.z_variant > 2 || (o.z_variant == 2 && !zplan_variant_available(N))) {
@@ -1252,9 +1253,9 @@ ens_status sync_nblk(ens_ctx *ctx)
     for (auto &gr : ctx->groups) {
         const Geo &g = gr.geo;
         // the persistent stage kernel runs the fused update pass on 16-column tiles
-        const int nblk = ctx->persistent ? g.NK * g.NZp / 16
-                         : g.fx_split    ? (int)((g.sU + kUpdChunk - 1) / kUpdChunk)
-                                         : g.NK * g.NZp / g.tile_x;
+        const int nblk = ctx->persistent || g.fx_split == 2 ? g.NK * g.NZp / 16
+                         : g.fx_split                     ? (int)((g.sU + kUpdChunk - 1) / kUpdChunk)
+                                                          : g.NK * g.NZp / g.tile_x;
         std::vector<int> v(g.members, nblk);
         ENS_CUDA(ctx, cudaMemcpy2DAsync(&ctx->md[g.first].nblk, sizeof(MemberDev), v.data(), sizeof(int),
                                         sizeof(int), g.members, cudaMemcpyHostToDevice, ctx->stream));
@@ -1449,9 +1450,10 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
             cand.group[gi].z_variant = 1;
             consider(cand);
         }
-        if (rs == ENS_OK) {
+        for (int fx = 0; rs == ENS_OK && fx <= 2; ++fx) {
+            if (fx == best.group[gi].fx_split || (fx == 2 && !fx_ws_available(N))) continue;
             cand = best;
-            cand.group[gi].fx_split = 1 - best.group[gi].fx_split;
+            cand.group[gi].fx_split = fx;
             consider(cand);
         }
     }

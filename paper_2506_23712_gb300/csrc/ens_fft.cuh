@@ -296,15 +296,26 @@ __device__ __forceinline__ void pass_regs(float2 *v, int p, const float2 *__rest
     }
 }
 
+// The barrier of the column-pass exchanges: the whole block, or (NamedSync)
+// the ID-th hardware barrier over COUNT threads, for kernels whose warps
+// form groups doing different work.
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <int ID, int COUNT>
+struct NamedSync {
+    __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory"); }
+};
+
 // Hand the outputs of a pass (radix R, Ns) to the next pass (radix R2n).
 // `at(pos)` returns the shared-memory slot of line position pos for this
-// thread's line.  Brackets the exchange with block barriers.
-template <int N, int R, int Ns, int Rn, int P, class At>
-__device__ __forceinline__ void exchange(float2 *v, int p, At at)
+// thread's line.  Brackets the exchange with block (or group) barriers.
+template <int N, int R, int Ns, int Rn, int P, class At, class Sync = BlockSync>
+__device__ __forceinline__ void exchange(float2 *v, int p, At at, Sync sync = Sync())
 {
     constexpr int B = N / (R * P);
     constexpr int Bn = N / (Rn * P);
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int j = p + b * P;
@@ -312,7 +323,7 @@ __device__ __forceinline__ void exchange(float2 *v, int p, At at)
 #pragma unroll
         for (int t = 0; t < R; ++t) *at(base + t * Ns) = v[b * R + t];
     }
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int b = 0; b < Bn; ++b) {
         const int j = p + b * P;
@@ -322,18 +333,18 @@ __device__ __forceinline__ void exchange(float2 *v, int p, At at)
 }
 
 // Full line transform.  In: v in first-pass input order.  Out: v in
-// last-pass output order (PlanInfo::out_pos).  Every thread of the block
-// must call it (it contains block barriers).
-template <int N, bool FWD, int VAR = 0, class At>
-__device__ __forceinline__ void fft_line(float2 *v, int p, const float2 *__restrict__ tw, At at)
+// last-pass output order (PlanInfo::out_pos).  Every thread of the block (of
+// the group, with a NamedSync) must call it: it contains barriers.
+template <int N, bool FWD, int VAR = 0, class At, class Sync = BlockSync>
+__device__ __forceinline__ void fft_line(float2 *v, int p, const float2 *__restrict__ tw, At at, Sync sync = Sync())
 {
     using PI = PlanInfo<N, VAR>;
     constexpr int P = PI::P;
     pass_regs<N, PI::R0, 1, P, FWD>(v, p, tw);
-    exchange<N, PI::R0, 1, PI::R1, P>(v, p, at);
+    exchange<N, PI::R0, 1, PI::R1, P>(v, p, at, sync);
     pass_regs<N, PI::R1, PI::R0, P, FWD>(v, p, tw);
     if constexpr (PI::NP == 3) {
-        exchange<N, PI::R1, PI::R0, PI::R2, P>(v, p, at);
+        exchange<N, PI::R1, PI::R0, PI::R2, P>(v, p, at, sync);
         pass_regs<N, PI::R2, PI::R0 * PI::R1, P, FWD>(v, p, tw);
     }
 }

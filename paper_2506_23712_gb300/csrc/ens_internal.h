@@ -56,9 +56,11 @@ struct Geo {
     // tuning of the stage passes (chosen by the autotuner)
     int tile_x, tile_y;          // columns per CTA of the x / y passes (8 or 16)
     int plan_x;                  // FFT plan of the x passes (0: default, 1: more threads per line)
-    int fx_split;                // last pass of a stage: 0 fused, 1 transform + update launches
+    int fx_split;                // last pass of a stage: 0 fused, 1 transform + update launches,
+                                 // 2 fused with the two halves in overlapping warp groups
     int z_mode;                  // 0: persistent TMA z pass, 1: one CTA per row group
     int z_ctas;                  // persistent CTAs of the z-direction nonlinear pass
+    int sms;                     // streaming multiprocessors of the device (persistent launches)
     // failure test only (ens_test_skip_copy): the persistent z pass issues no
     // bulk copy for the first row group of this member (local index in the
     // group; -1: none) and waits for that group's barrier at most

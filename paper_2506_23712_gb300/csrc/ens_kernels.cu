@@ -316,6 +316,12 @@ int znl_ctas_per_sm(int N, int var)
 
 bool zplan_variant_available(int N) { return has_zplan_variant(N); }
 
+bool fx_ws_available(int N)
+{
+    const SizedOps *o = sized_ops(N);
+    return o && o->fx_ws();
+}
+
 void launch_pass(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last, int arg,
                  cudaStream_t s)
 {

@@ -32,6 +32,7 @@ cudaError_t prepare_kernels(int N, int nq, int nt, int ng);
 int znl_ctas_per_sm(int N, int var = 0);   // resident CTAs per SM of the persistent z pass (0 on error)
 bool zplan_variant_available(int N);       // the persistent z pass has a second warp plan for this size
 bool plan_variant_available(int N);   // the x passes have a second FFT plan for this size
+bool fx_ws_available(int N);          // the last pass has its warp-group variant (fx_split 2) for this size
 
 // Pass launchers of one grid size (ens_sized.cu, one translation unit per N).
 struct SizedOps {
@@ -39,6 +40,7 @@ struct SizedOps {
     int (*znl_ctas_per_sm)(int var);
     void (*launch)(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, int stage, int last,
                    int arg, cudaStream_t s);
+    bool (*fx_ws)();   // the warp-group variant of the last pass exists for this size
 };
 template <int N>
 const SizedOps *sized_ops_for();

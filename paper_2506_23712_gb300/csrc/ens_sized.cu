@@ -2,6 +2,7 @@
 // once per supported N (-DENS_N=16 ... 512), so the heavy template
 // instantiations of the FFT passes spread over parallel compiler jobs.
 #include "ens_fxsplit.cuh"
+#include "ens_fxws.cuh"
 #include "ens_launch.h"
 #include "ens_stats.cuh"
 #include "ens_znl.cuh"
@@ -30,6 +31,8 @@ template <int M>
 cudaError_t prepare_variants()
 {
     cudaError_t e = cudaSuccess;
+    if constexpr (has_fx_ws<M>())
+        e = cudaFuncSetAttribute(k_fwd_x_ws<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WsCfg<M>::smem());
     if constexpr (has_zplan_variant(M)) {
         if (ZCfg<M, 1>::smem_bytes() > 48 * 1024)
             e = cudaFuncSetAttribute(k_znl<M, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -102,6 +105,16 @@ void launch_znl_t(const Geo &g, MemberDev *md, int stage, cudaStream_t s)
         }
     }
     k_znl<M><<<g.z_ctas, 256, ZCfg<M>::smem_bytes(), s>>>(g, md, stage);
+}
+
+template <int M>
+void launch_fx_ws_t(const Geo &g, MemberDev *md, int stage, int last, cudaStream_t s)
+{
+    if constexpr (has_fx_ws<M>()) {
+        const long long tiles = (long long)WsCfg<M>::TILES * g.members;
+        const int grid = (int)(tiles < g.sms ? tiles : g.sms);
+        k_fwd_x_ws<M><<<grid, 2 * WsCfg<M>::TH, WsCfg<M>::smem(), s>>>(g, md, stage, last);
+    }
 }
 
 template <int T, int VAR = 0>
@@ -191,7 +204,9 @@ void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, 
     case Pass::FX:
         switch (mode) {
         case 0:
-            if (g.fx_split) {
+            if (g.fx_split == 2) {
+                launch_fx_ws_t<N>(g, md, stage, last, s);
+            } else if (g.fx_split) {
                 k_fwd_x_fft<N, 16><<<dim3(g.NK * g.NZp / 16, 3, g.members), ColCfg<N, 16>::threads,
                                      smem_cols<N, 16>(), s>>>(g);
                 k_update<N><<<dim3(update_blocks<N>(), g.members), kUpdThreads, 0, s>>>(g, md, stage, last);
@@ -212,7 +227,9 @@ void launch(Pass pass, int mode, const Geo &g, MemberDev *md, const HistDev *h, 
     }
 }
 
-const SizedOps kOps = {prepare, znl_per_sm, launch};
+bool fx_ws() { return has_fx_ws<N>(); }
+
+const SizedOps kOps = {prepare, znl_per_sm, launch, fx_ws};
 
 }  // namespace
 

@@ -71,14 +71,15 @@ def oracle_member(d):
 
 def tunings(E, ens, N):
     """Every combination of the variants the autotuner searches at N (column
-    tile of the x passes, x-pass FFT plan where a second one exists, fused or
-    split last pass, z-pass variant), the y tile and CTAs per SM at their
-    defaults."""
+    tile of the x passes, x-pass FFT plan where a second one exists, fused,
+    split or warp-group last pass, z-pass variant), the y tile and CTAs per SM
+    at their defaults."""
     base = ens.tuning()
     plans = (0, 1) if N in (128, 256, 512) else (0,)
     zvars = (0, 1, 2) if N == 256 else (0, 1)
+    splits = (0, 1, 2) if N == 256 else (0, 1)
     out = []
-    for tx, plan, split, zv in itertools.product((16, 8), plans, (0, 1), zvars):
+    for tx, plan, split, zv in itertools.product((16, 8), plans, splits, zvars):
         t = json.loads(json.dumps(base))
         t["groups"][0].update(tile_x=tx, plan_x=plan, fx_split=split, z_variant=zv)
         if zv == 2:

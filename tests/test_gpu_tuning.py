@@ -231,3 +231,43 @@ def test_autotune_preserves_state_and_caches(E, tmp_path):
     assert t2["cached"] and other.tuning()["groups"] == t["groups"]
     other.close()
     ens.close()
+
+
+def test_warp_group_last_pass_equals_fused(E):
+    """The last pass in two overlapping warp groups (fx_split 2, N = 256)
+    gives, bit for bit, the fields and energy sums of the fused pass on
+    16-column tiles, over two steps with CFL time steps; and ens_step_host
+    (members in chunks of one) runs it too.  Chunked launches agree with the
+    whole group's launch to FP32 rounding, not bit for bit: the z pass
+    pairs the n_z rows of a warp's stream of rows, and the stream depends on
+    the members in the launch."""
+    ms = [E.Member(N=256, nu=0.005, lam=l, k_lo=6, k_hi=8, dt=-1, cfl=0.2, rk_order=3, seed=300 + i)
+          for i, l in enumerate((-1.0, 0.4, 2.1))]
+    a, b = E.Ensemble(ms), E.Ensemble(ms)
+    ta = a.tuning()
+    ta["groups"][0].update(fx_split=0, tile_x=16, plan_x=0)
+    a.set_tuning(ta)
+    tb = b.tuning()
+    tb["groups"][0].update(fx_split=2, tile_x=16, plan_x=0)
+    b.set_tuning(tb)
+    assert b.tuning()["groups"][0]["fx_split"] == 2
+    a.step(2)
+    b.step(2)
+    da, db = a.diagnostics(), b.diagnostics()
+    for i in range(len(ms)):
+        assert np.array_equal(a.field(i), b.field(i)), i
+        for k in ("dt", "E", "diss", "EB", "P"):
+            assert da[i][k] == db[i][k], (i, k)
+    nbytes = E.ens_state_bytes(b.ctx)
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    E.ens_get_state(b.ctx, host.data_ptr(), nbytes)
+    ref = host.clone()
+    E.ens_step_host(b.ctx, host.data_ptr(), host.data_ptr(), nbytes, 1)
+    E.ens_set_state(a.ctx, ref.data_ptr(), nbytes)
+    a.step(1)
+    E.ens_set_state(b.ctx, host.data_ptr(), nbytes)
+    for i in range(len(ms)):
+        fa, fb = a.field(i), b.field(i)
+        assert np.linalg.norm(fb - fa) <= 1e-6 * np.linalg.norm(fa), i
+    a.close()
+    b.close()
