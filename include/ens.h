@@ -193,7 +193,10 @@ ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
  * (bytes >= ens_state_bytes), the stepped state is written to host_out
  * (host_out may equal host_in).  The members go through in chunks of
  * `chunk` members of one grid size (0: an eighth of each group, at least
- * one): a chunk's upload, its energy sums (as after ens_set_state), its
+ * one, with the first three and the last three chunks an eighth, a quarter
+ * and a half of that, so that the pipeline fills and drains quickly): a
+ * chunk's upload,
+ * its energy sums (as after ens_set_state), its
  * three RK stages and its download are ordered on the device, and the
  * upload of the next chunk and the download of the previous one run on two
  * copy streams while a chunk computes.  Overlap needs page-locked host

@@ -723,10 +723,35 @@ ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size
         ENS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
         ENS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
     }
+    // chunk sizes per group: `chunk` members each, or (chunk = 0) an eighth
+    // of the group with the first three and the last three chunks an eighth,
+    // a quarter and a half of that, so that the upload before the first
+    // compute and the download after the last one are short
+    std::vector<std::vector<int>> sched(ctx->groups.size());
     int nchunks = 0;
-    for (auto &gr : ctx->groups) {
-        const int c = chunk > 0 ? chunk : std::max(1, (gr.geo.members + 7) / 8);
-        nchunks += (gr.geo.members + c - 1) / c;
+    for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
+        const int M = ctx->groups[gi].geo.members;
+        std::vector<int> &v = sched[gi];
+        if (chunk > 0) {
+            for (int k = 0; k < M; k += chunk) v.push_back(std::min(chunk, M - k));
+        } else {
+            const int c = std::max(1, (M + 7) / 8);
+            const int e = std::max(1, c / 8), q = std::max(1, c / 4), h = std::max(1, c / 2);
+            if (M >= 2 * (e + q + h) + c) {
+                v = {e, q, h};
+                int left = M - 2 * (e + q + h);
+                while (left > 0) {
+                    v.push_back(std::min(c, left));
+                    left -= v.back();
+                }
+                v.push_back(h);
+                v.push_back(q);
+                v.push_back(e);
+            } else {
+                for (int k = 0; k < M; k += c) v.push_back(std::min(c, M - k));
+            }
+        }
+        nchunks += (int)v.size();
     }
     while ((int)ctx->ev_in.size() < nchunks) {
         cudaEvent_t a, b;
@@ -744,11 +769,11 @@ ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size
     char *out = static_cast<char *>(host_out);
     size_t off = 0;
     int ci = 0;
-    for (auto &gr : ctx->groups) {
-        const int c = chunk > 0 ? chunk : std::max(1, (gr.geo.members + 7) / 8);
+    for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
+        const Group &gr = ctx->groups[gi];
         const size_t per = sizeof(float2) * 3 * gr.geo.sU;
-        for (int k0 = 0; k0 < gr.geo.members; k0 += c, ++ci) {
-            const int cnt = std::min(c, gr.geo.members - k0);
+        int k0 = 0;
+        for (const int cnt : sched[gi]) {
             const Geo g = member_range(gr.geo, k0, cnt);
             const size_t b = per * cnt;
             MemberDev *md = ctx->md + g.first;
@@ -769,6 +794,8 @@ ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size
             ENS_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_out, ctx->ev_done[ci], 0));
             ENS_CUDA(ctx, cudaMemcpyAsync(out + off, g.U, b, cudaMemcpyDeviceToHost, ctx->copy_out));
             off += b;
+            k0 += cnt;
+            ++ci;
         }
     }
     ENS_CUDA(ctx, cudaGetLastError());
