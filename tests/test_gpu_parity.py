@@ -437,7 +437,9 @@ def test_statistics_pass_shapes_match_oracle_on_same_field(E, N, parity_log):
     warp at N <= 128, several CTAs per member from N = 64, the XOR-swizzled
     non-power-of-two plan at 384) against the oracle's statistics of the very
     same spectral field: 2% in every bin above 1000 counts, exact point
-    count, moments to 1e-4."""
+    count, moments to 1e-4.  On the same field the sparse bins (the tails)
+    can differ only where FP32 rounding moves a point across an edge: their
+    counts together differ by at most 1e-4 of the points (plus 20)."""
     m = E.Member(N=N, nu=0.02, lam=0.0, eps_bar=0.1, k_lo=1, k_hi=2, dt=0.002, rk_order=3, seed=5,
                  init_energy=2.0)
     kw = dict(qr_bins=64, q_lim=10.0, r_lim=10.0, tail_bins=128, tail_lo=-8, tail_hi=8, eps_norm=0.1, nu_norm=0.02)
@@ -457,6 +459,12 @@ def test_statistics_pass_shapes_match_oracle_on_same_field(E, N, parity_log):
                max(abs(mom[0, k] / rm[k] - 1) for k in list(range(0, 36, 4)) + [38, 39]), 1e-4)
     assert np.all(np.abs(c[big] - r[big]) <= 0.02 * r[big])
     assert abs(int(c.sum()) - int(r.sum())) <= 1e-3 * r.sum()
+    sparse = ~big
+    sparse[L - 8:] = False          # the counters, checked above
+    moved = int(np.abs(c[sparse] - r[sparse]).sum())
+    parity_log("%d^3 statistics pass on the same field, sparse bins (<= 1000 counts): summed |count difference| "
+               "/ points" % N, moved / N ** 3, 1e-4)
+    assert moved <= 1e-4 * N ** 3 + 20, moved
     for k in list(range(0, 36, 4)) + [38, 39]:
         assert mom[0, k] == pytest.approx(rm[k], rel=1e-4), k
     ens.close()
