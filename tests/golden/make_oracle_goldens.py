@@ -2,7 +2,7 @@
 against.  Calls only ``oracle/`` (the FP64 CPU oracle) and the seeded input
 module ``ens_inputs``; nothing here touches the CUDA library.
 
-Two kinds of files, both numpy ``.npz`` beside this script:
+Three kinds of files, all numpy ``.npz`` beside this script:
 
 * ``one_step_<N>.npz``: one IF-RK3 step (CFL 0.2, Sec. IV) of members at the
   grid sizes whose oracle step takes minutes (256, 384, 512), from the seeded
@@ -13,6 +13,9 @@ Two kinds of files, both numpy ``.npz`` beside this script:
   dissipation and enstrophy histograms, moments).  The GPU tests compare
   their own field on the same sample (relative L2, Sec. IV tolerances) and
   their statistics of their own field under the 2% rule.
+* ``ten_steps_256.npz``: ten IF-RK3 steps (CFL 0.2) of the central member
+  of the 64 x 256^3 benchmark ensemble, stored on the same kind of mode
+  sample, with the diagnostics after every step.
 * ``ensemble_64_long_run.npz``: the 16-member 64^3 ensemble (nu 0.01, band
   [3, 5], lambda on a uniform grid over [-3, 3], IF-RK3, CFL 0.2 capped at
   0.01) run 1000 steps; gradient statistics accumulated every 10 steps after
@@ -21,6 +24,7 @@ Two kinds of files, both numpy ``.npz`` beside this script:
 
 Run from the repository root:
     python tests/golden/make_oracle_goldens.py one_step 256 384 512
+    python tests/golden/make_oracle_goldens.py ten_steps
     python tests/golden/make_oracle_goldens.py long_run [--jobs 4]
 """
 from __future__ import annotations
@@ -122,6 +126,29 @@ def run_one_step(N):
     print("wrote", path)
 
 
+def run_ten_steps():
+    ds = I.ensemble_256()
+    lams = np.array([d["lam"] for d in ds])
+    i = int(np.argmin(np.abs(lams)))
+    d = ds[i]
+    m = oracle_member(d)
+    uh = O.initial_field(m)
+    keys = ("t", "dt", "E", "diss", "EB", "P", "umax")
+    diags = []
+    t = 0.0
+    t0 = time.time()
+    for s in range(10):
+        st, diag = O.step(m, uh, 1, t)
+        assert st == 0, (s, st)
+        t = diag["t"]
+        diags.append([diag[k] for k in keys])
+    modes = mode_sample(d["N"], d["k_lo"], d["k_hi"], seed=2560)
+    path = os.path.join(HERE, "ten_steps_256.npz")
+    np.savez_compressed(path, desc=json.dumps(dict(d, name="ensemble_256[%d]" % i, index=i)), modes=modes,
+                        values=uh[:, modes[:, 0], modes[:, 1], modes[:, 2]], diags=np.array(diags))
+    print("wrote %s in %.0f s" % (path, time.time() - t0))
+
+
 def long_run_member(i):
     d = I.ensemble_64()[i]
     m = oracle_member(d)
@@ -164,7 +191,7 @@ def run_long(jobs):
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("what", choices=["one_step", "long_run"])
+    p.add_argument("what", choices=["one_step", "ten_steps", "long_run"])
     p.add_argument("sizes", nargs="*", type=int)
     p.add_argument("--jobs", type=int, default=1)
     a = p.parse_args()
@@ -172,6 +199,8 @@ def main():
     if a.what == "one_step":
         for N in a.sizes or [256, 384, 512]:
             run_one_step(N)
+    elif a.what == "ten_steps":
+        run_ten_steps()
     else:
         run_long(a.jobs)
 

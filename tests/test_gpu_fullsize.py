@@ -5,7 +5,15 @@ autotuner's choice installed, exactly as bench.py runs it; sampled members
 (the extreme and the central lambda) against the FP64 oracle run on their
 own: relative L2 <= 1e-5 after one step, the same CFL step, and the
 gradient statistics of each of them within 2% in every bin above 1000 counts.
+Ten steps of the same launch configuration against the oracle's ten steps of
+the central member (stored, ``tests/golden/ten_steps_256.npz``, sampled
+modes): relative L2 <= 1e-4 (the one-step bound grows with the steps; the
+32^3 runs are held to 1e-3 after 100), the CFL step and energy of every step
+within 1e-5.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -73,4 +81,36 @@ def test_benchmark_ensemble_sampled_members_match_oracle(E, parity_log):
         parity_log("256^3 benchmark member lambda=%.3f: statistics max bin deviation (bins > 1000)" % d["lam"],
                    dev, 0.02)
         assert dev <= 0.02
+    ens.close()
+
+
+def test_benchmark_ensemble_ten_steps_match_stored_oracle(E, parity_log):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ten_steps_256.npz")
+    if not os.path.exists(path):
+        pytest.fail("missing %s: run tests/golden/make_oracle_goldens.py ten_steps" % path)
+    z = np.load(path)
+    gd = json.loads(str(z["desc"]))
+    ds = I.ensemble_256()
+    i = gd["index"]
+    assert ds[i]["seed"] == gd["seed"] and ds[i]["lam"] == gd["lam"]
+    ms = [E.Member(N=d["N"], nu=d["nu"], lam=d["lam"], eps_bar=d["eps_bar"], k_lo=d["k_lo"], k_hi=d["k_hi"],
+                   dt=d["dt"], cfl=d["cfl"], dt_max=d["dt_max"], rk_order=d["rk_order"], seed=d["seed"],
+                   init_energy=d["init_energy"]) for d in ds]
+    ens = E.Ensemble(ms, hist=E.hist_spec(nu_norm=0.005))
+    ens.autotune(steps=1)
+    worst_dt = worst_E = 0.0
+    for s in range(10):
+        ens.step(1)
+        g = ens.diagnostics()[i]
+        t_, dt, E_, diss, EB, P, umax = z["diags"][s]
+        worst_dt = max(worst_dt, abs(g["dt"] / dt - 1))
+        worst_E = max(worst_E, abs(g["E"] / E_ - 1))
+    modes = z["modes"]
+    got = ens.field(i)[:, modes[:, 0], modes[:, 1], modes[:, 2]]
+    err = parity_log("256^3 benchmark ensemble (autotuned), central member: field after 10 steps, sampled rel L2",
+                     rel(got, z["values"]), 1e-4)
+    parity_log("256^3 benchmark ensemble, central member: dt over 10 steps, max rel error", worst_dt, 1e-5)
+    parity_log("256^3 benchmark ensemble, central member: E over 10 steps, max rel error", worst_E, 1e-5)
+    assert err < 1e-4
+    assert worst_dt < 1e-5 and worst_E < 1e-5
     ens.close()
