@@ -847,9 +847,10 @@ double ens_pass_bytes(const ens_ctx *ctx, int pass, int stage)
         case 2: bytes = 6 * b + 3 * b; break;
         case 3: bytes = 3 * b + 3 * a; break;
         case 4: bytes = 3 * a + (stage > 0 ? 2 : 1) * 3 * st + 3 * st; break;
-        // statistics snapshot: 8 gradient components along x (3 state comps
-        // in), along y, then the z pass that reads them for the invariants
-        case 5: bytes = 3 * st + 8 * a + 8 * a + 8 * b + 8 * b; break;
+        // statistics snapshot: 6 fields along x (u_i, i kx u_i from the 3
+        // state comps), the 8 gradient components along y, then the z pass
+        // that reads them for the invariants
+        case 5: bytes = 3 * st + 6 * a + 6 * a + 8 * b + 8 * b; break;
         default: bytes = 0.0;
         }
         total += bytes * g.members;
@@ -871,7 +872,7 @@ ens_status ens_gradient_stats(ens_ctx *ctx, int accumulate)
     for (auto &gr : ctx->groups) {
         const Geo &g = gr.geo;
         launch_pass(Pass::IX, 1, g, ctx->md, nullptr, 0, 0, 0, st);
-        launch_pass(Pass::IY, 0, g, ctx->md, nullptr, 0, 0, 8, st);
+        launch_pass(Pass::IY, kIYGrad, g, ctx->md, nullptr, 0, 0, 6, st);
         launch_pass(Pass::ZSTAT, 0, g, ctx->md, &ctx->hd, 0, 0, 0, st);
     }
     launch_finish_stats(ctx->mom_partial, ctx->mom_blocks, ctx->moments, n, accumulate, st);

@@ -197,7 +197,8 @@ __device__ __forceinline__ void inv_x_body(const Geo &g, int use_S, int bx, int 
         }
     };
     // ky and kz are constant along x, so their derivatives are applied after
-    // the transform: 5 transforms give u and omega, 6 give the 8 gradients
+    // the transform: 5 transforms give u and omega; for the gradient the 6
+    // transforms of u_i and i kx u_i go to the y pass, which applies ky, kz
     float2 Ua[V], Ub[V];
     if constexpr (MODE == 0) {
         // omega = i k x u: (k x u)_x = ky uz - kz uy, _y = kz ux - kx uz, _z = kx uy - ky ux
@@ -225,21 +226,16 @@ __device__ __forceinline__ void inv_x_body(const Geo &g, int use_S, int bx, int 
             Ub[i] = make_float2(Ub[i].x + ky * Ua[i].y, Ub[i].y - ky * Ua[i].x);      // i kx uy - i ky ux
         store(Ub, 5);                                             // omega_z
     } else {
-        // A_ij = i k_j u_i, f = 3 i + j (A_33 is not stored)
+        // velocity gradient A_ij = i k_j u_i, x part: u_i to field i and
+        // i kx u_i to field 3 + i; the y pass forms the ky and kz
+        // derivatives from field i (k_inv_y_grad)
 #pragma unroll 1
         for (int ci = 0; ci < 3; ++ci) {
             landed(ci);
             transform(Ua, ci, false);
-#pragma unroll
-            for (int i = 0; i < V; ++i) Ub[i] = mul_i(cscale(Ua[i], ky));
-            store(Ub, 3 * ci + 1);
-            if (ci < 2) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) Ub[i] = mul_i(cscale(Ua[i], kzf));
-                store(Ub, 3 * ci + 2);
-            }
+            store(Ua, ci);
             transform(Ub, ci, true);
-            store(Ub, 3 * ci);
+            store(Ub, 3 + ci);
         }
     }
 }
@@ -290,6 +286,61 @@ k_inv_y(Geo g, int f0)
 {
     extern __shared__ __align__(16) float2 sm[];
     inv_y_body<N, T, VAR>(g, blockIdx.x, f0 + blockIdx.y, blockIdx.z, sm);
+}
+
+// IY of the velocity gradient (statistics snapshot): from the six x-pass
+// fields of a member (u_i in field i, i kx u_i in field 3 + i) the eight
+// stored components A_ij = i k_j u_i into B field 3 i + j (A_33 = -A_11 -
+// A_22 is not stored):
+//   j = 1 : transform of field 3 + i
+//   j = 2 : transform of i ky times field i (ky varies along y: applied
+//           before the transform)
+//   j = 3 : i kz times the transform of field i (kz is constant along y:
+//           applied after it), i < 2
+// so the x pass writes and this pass reads six fields instead of eight.  One
+// transform per CTA; the eight jobs of a column tile are consecutive CTAs
+// (blockIdx.x), so the second read of field i comes from L2.
+// grid (8, N*NZp/T, members).
+// (N <= 256: registers capped for 40 resident warps per SM, the plain y
+// pass's occupancy; the larger plans keep their registers)
+template <int N, int T>
+__global__ void __launch_bounds__(ColCfg<N, T, 0>::threads, N <= 256 ? 1280 / ColCfg<N, T, 0>::threads : 1)
+k_inv_y_grad(Geo g)
+{
+    using PI = PlanInfo<N, 0>;
+    constexpr int P = PI::P, V = PI::V;
+    extern __shared__ __align__(16) float2 sm[];
+    float2 *tw = sm, *buf = sm + N;
+    load_twiddles(tw, g.tw, N);
+    const int fo = blockIdx.x, m = blockIdx.z;
+    const int ci = fo / 3, jj = fo % 3;
+    const int fi = jj == 0 ? 3 + ci : ci;
+    const int c = threadIdx.x % T, p = threadIdx.x / T;
+    const int col = blockIdx.y * T + c;        // (x, kz) flat
+    const int kz = col % Dims<N>::NZP;
+    const bool valid = kz < Dims<N>::NZ;
+    const long long row = (long long)N * Dims<N>::NZP;
+    const float2 *src = g.A + ((long long)m * kFields + fi) * Dims<N>::SA + col;
+    float2 v[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int ky = wnum(PI::in_pos(p, i), N);
+        const bool keep = valid && ky >= -Dims<N>::KC && ky <= Dims<N>::KC;
+        const int iy = ky >= 0 ? ky : ky + Dims<N>::NK;
+        const float2 u = keep ? src[iy * row] : make_float2(0.f, 0.f);
+        v[i] = jj == 1 ? mul_i(cscale(u, (float)ky)) : u;
+    }
+    fft_line<N, false, 0>(v, p, tw, [&](int pos) { return &buf[pos * T + c]; });
+    if (jj == 2) {
+        const float kzf = (float)kz;
+#pragma unroll
+        for (int i = 0; i < V; ++i) v[i] = mul_i(cscale(v[i], kzf));
+    }
+    if (valid) {
+        float2 *dst = g.B + ((long long)m * kFields + fo) * Dims<N>::SB + col;
+#pragma unroll
+        for (int i = 0; i < V; ++i) dst[PI::out_pos(p, i) * row] = v[i];
+    }
 }
 
 // ---------------------------------------------------------------------------

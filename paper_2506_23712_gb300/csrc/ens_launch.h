@@ -6,6 +6,9 @@
 namespace ens {
 
 enum class Pass { IX, IY, Z, FY, FX, ZSTAT };
+// IY mode of the statistics snapshot: the eight gradient components from the
+// six x-pass fields (u_i, i kx u_i)
+constexpr int kIYGrad = -1;
 
 // lambda-weight specification on the device (kind: 0 Gaussian with the
 // paper's mean and variance from c and Z, 1 Gaussian (mu, sigma), 2 user

@@ -59,6 +59,8 @@ cudaError_t prepare(int nq, int nt, int ng)
     chk(allow_smem(k_inv_x<N, 1, 16>, smem_x<N, 16>()));
     chk(allow_smem(k_inv_y<N, 16>, smem_cols<N, 16>()));
     chk(allow_smem(k_inv_y<N, 8>, smem_cols<N, 8>()));
+    chk(allow_smem(k_inv_y_grad<N, 16>, smem_cols<N, 16>()));
+    chk(allow_smem(k_inv_y_grad<N, 8>, smem_cols<N, 8>()));
     chk(allow_smem(k_fwd_y<N, 16>, smem_cols<N, 16>()));
     chk(allow_smem(k_fwd_y<N, 8>, smem_cols<N, 8>()));
     chk(allow_smem(k_fwd_x<N, 0, 16>, smem_x<N, 16>()));
@@ -128,8 +130,10 @@ void launch_cols(Pass pass, int mode, const Geo &g, MemberDev *md, int stage, in
         if (mode == 0) k_inv_x<N, 0, T, VAR><<<grid_state, TC, smem_x<N, T>(), s>>>(g, arg);
         break;
     case Pass::IY:
-        // arg = number of fields, mode = first field
-        k_inv_y<N, T><<<dim3(col_tiles_mid, arg, g.members), TC, smem_cols<N, T>(), s>>>(g, mode);
+        // arg = number of fields, mode = first field (kIYGrad: the gradient
+        // components from the six x-pass fields)
+        if (mode == kIYGrad) k_inv_y_grad<N, T><<<dim3(8, col_tiles_mid, g.members), TC, smem_cols<N, T>(), s>>>(g);
+        else k_inv_y<N, T><<<dim3(col_tiles_mid, arg, g.members), TC, smem_cols<N, T>(), s>>>(g, mode);
         break;
     case Pass::FY:
         k_fwd_y<N, T><<<dim3(col_tiles_mid, 3, g.members), TC, smem_cols<N, T>(), s>>>(g);
