@@ -95,14 +95,13 @@ __device__ __forceinline__ float update_mode(const UpdCoef &c, int kx, int ky, i
 #pragma unroll
     for (int q = 0; q < 3; ++q)
         if (band) n[q] = make_float2(n[q].x + c.alpha * us[q].x, n[q].y + c.alpha * us[q].y);
-    const float ea = c.a != 0.f ? expf(-c.nu * k2 * c.ha * c.dtf) : 0.f;
-    const float eb = expf(-c.nu * k2 * c.hb * c.dtf);
+    const IfCoef ic = if_coef(StageCoef{c.a, c.ha, c.b, c.hb}, c.nu, k2, c.dtf);
     float a2 = 0.f;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const float rx = us[q].x + c.dtf * n[q].x, ry = us[q].y + c.dtf * n[q].y;
-        const float ox = c.a * ea * un[q].x + c.b * eb * rx;
-        const float oy = c.a * ea * un[q].y + c.b * eb * ry;
+        const float ox = if_combine(ic, un[q].x, rx);
+        const float oy = if_combine(ic, un[q].y, ry);
         out[q] = make_float2(ox, oy);
         a2 += ox * ox + oy * oy;
     }

@@ -176,15 +176,14 @@ k_fwd_x_ws(Geo g, MemberDev *md, int stage, int last_stage)
                         us[q] = usb[u][q];
                         if (band) n[q] = make_float2(n[q].x + alpha * us[q].x, n[q].y + alpha * us[q].y);
                     }
-                    const float ea = co.a != 0.f ? expf(-nu * k2 * co.ha * dtf) : 0.f;
-                    const float eb = expf(-nu * k2 * co.hb * dtf);
+                    const IfCoef ic = if_coef(co, nu, k2, dtf);
                     float2 *dst = last_stage ? U : S;
                     float a2 = 0.f;
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         const float rx = us[q].x + dtf * n[q].x, ry = us[q].y + dtf * n[q].y;
-                        const float ox = co.a * ea * un[q].x + co.b * eb * rx;
-                        const float oy = co.a * ea * un[q].y + co.b * eb * ry;
+                        const float ox = if_combine(ic, un[q].x, rx);
+                        const float oy = if_combine(ic, un[q].y, ry);
                         dst[q * Dims<N>::SU + off] = make_float2(ox, oy);
                         a2 += ox * ox + oy * oy;
                     }
