@@ -331,11 +331,10 @@ ens_status ens_mixture_host(int n, const double *lambdas, const uint64_t *counts
  * on stderr (use ens_mixture_host for them).
  *
  * The first call on a device, made while that device is current, looks up
- * the scratch array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls on a device share the one
- * array and it keeps the last call's contents: calls that overlap on the
- * GPU (from several threads or streams at once) race and give wrong
- * results.  The call synchronises `stream` before it returns, so calls made
+ * the scratch array's device address (cudaGetSymbolAddress).  All calls on a
+ * device share the one array and it keeps the last call's contents: calls
+ * that overlap on the GPU (from several threads or streams at once) race and
+ * give wrong results.  The call synchronises `stream` before it returns, so calls made
  * one after another from one thread do not overlap. */
 #define ENS_NOALLOC_MAX_MEMBERS 64
 #define ENS_NOALLOC_MAX_COUNTS 8192
