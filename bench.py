@@ -348,7 +348,7 @@ def measure_surrogate(E, ens, descs, torch, steps=800):
             "train_rows_per_step": len(lams) * per, "final_loss": loss,
             "quadrature_points": 512, "mixture_s": t_inf,
             "hellinger_vs_member_quadrature": {k: hellinger(sur[k], ref[k]) for k in ("pdf_qr", "pdf_eps", "pdf_ens")},
-            "Z": Z, "roofline": {"bound": "tensor", "kernel": "k_mlp_infer", "achieved": tflops, "peak": peak[0],
+            "Z": Z, "roofline": {"bound": "tensor", "kernel": "k_mlp_infer_pair", "achieved": tflops, "peak": peak[0],
                                   "unit": "TFLOP/s", "frac": tflops / peak[0], "peak_source": peak[1],
                                   "rows": rows_q, "flops_per_launch": infer_flops, "ms": infer_ms},
             "layer_gemm": {"kernel": "k_gemm_tc<256>", "shape": "%d x 256 x 256 BF16 -> FP32" % pad128(rows_q),

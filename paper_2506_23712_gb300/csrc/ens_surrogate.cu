@@ -593,35 +593,6 @@ __global__ void k_feature_table(RowSpec rs, const double *lams, int nlam, uint4 
     for (int j = 0; j < kIn / 8; ++j) ftab[(long long)i * (kIn / 8) + j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
 }
 
-// ---------------------------------------------------------------------------
-// Fused inference: features -> 3 x (tcgen05 GEMM + bias + SiLU) -> head, per
-// 128-row tile, activations never leave the SM.  Persistent CTAs (one per
-// SM, 16 epilogue warps and one MMA warp); per CTA two 256-column FP32
-// accumulators in TMEM, used by the layers in turn.
-//   shared memory: H  4 K-blocks of 128 rows x 64 BF16 (64 KB; K-block 0
-//                     also holds the features of the tile)
-//                  W1 image (32 KB, loaded once), W2 or W3 image (128 KB in
-//                     four 32 KB K-blocks, each with its own barrier,
-//                     refilled by bulk copies while the epilogues run)
-// The epilogue of a layer (TMEM -> bias + SiLU -> BF16 A operand of the next
-// layer in H) runs in four 64-column chunks, all warps on chunk 0 first: as
-// soon as every epilogue warp has written chunk c (a per-chunk barrier, one
-// arrival per warp) and K-block c of the next weights has landed, the MMA
-// warp issues the next layer's MMAs on K-block c into the other
-// accumulator, so the tensor cores work while the epilogue proceeds.  The head of a tile (dot product with w4) runs while
-// the next tile's layer-1 MMAs do.
-//   per tile: features -> MMA1 (acc a) -> [head of the previous tile]
-//             epilogue1 | MMA2 (acc a^1) -> [copy W3] epilogue2 | MMA3 (acc a)
-//             -> [copy W2]
-// Epilogue warp w reads TMEM lanes 32 (w mod 4) .. +31 (its rows) and, in
-// chunk c, columns 64 c + 16 (w / 4) .. +15 (the four chunks' loads issued at
-// once).  Every mbarrier wait is bounded; a wait
-// that gives up sets *err, waits (bounded) for the copies and MMAs in
-// flight, frees the TMEM and returns.
-// ---------------------------------------------------------------------------
-constexpr int kInferWarps = 16;                       // epilogue warps
-constexpr int kInferThreads = 32 * (kInferWarps + 1);   // + the MMA warp
-
 // biases and head weights by value: kernel parameters live in the constant
 // bank, read in pairs by the epilogues (warp-uniform addresses: broadcasts)
 struct MlpBias {
@@ -629,80 +600,225 @@ struct MlpBias {
     float w4[kHid];
     float b4;
 };
-constexpr size_t kInferSmem = 1024 + 65536 + 32768 + 131072 + 128;
 
-__global__ void __launch_bounds__(kInferThreads, 1)
-k_mlp_infer(RowSpec rs, const uint4 *__restrict__ ftab, const uint32_t *__restrict__ lam5, long long real,
-            long long ntiles,
-            const unsigned char *__restrict__ img1, const unsigned char *__restrict__ img2,
-            const unsigned char *__restrict__ img3, const __grid_constant__ MlpBias bias, float *__restrict__ logit,
-            int *err)
+// ---------------------------------------------------------------------------
+// Fused inference: features -> 3 x (tcgen05 GEMM + bias + SiLU) -> head, per
+// 128-row tile; activations never leave the SM.  Persistent CTAs, two tiles
+// in flight per CTA (tiles A and B of a tile pair), so that the tensor cores
+// work on one tile while the epilogue warps work on the other.  Per CTA:
+//   TMEM          one 256-column FP32 accumulator per tile (512 columns)
+//   shared memory H_A, H_B: 4 K-blocks of 128 rows x 64 BF16 each (64 KB
+//                 each; K-block 0 also holds the tile's features, K-block 1
+//                 the head's partial sums); a ring of three 32 KB slots for
+//                 the weight K-blocks, streamed in the order they are used
+//                 (W1, W2 blocks 0-3, W3 blocks 0-3 per tile pair)
+//   warps 0-15    epilogues, in the order E1(A) E1(B) E2(A) E2(B) head(A)
+//                 head(B): TMEM -> bias + SiLU -> BF16 K-blocks of the next
+//                 layer's A operand (one arrival per warp and chunk), the
+//                 head's dot product with w4; the next pair's features
+//   warp 16       MMA issue: per hidden layer A0 A1 A2 B0 B1 B2 A3 B3
+//                 (K-block c of tile X once its chunk c is written and the
+//                 block has landed); a weight slot is released by a commit
+//                 after the B tile's MMAs on it
+//   warp 17       bulk copies of the weight K-blocks into free slots
+// An accumulator is reused by the next layer of its tile: every epilogue
+// warp loads all four chunks of it before its first chunk arrival, so the
+// next layer's first MMA (which overwrites it) waits on that arrival.
+// Epilogue warp w reads TMEM lanes 32 (w mod 4) .. +31 (its rows) and, in
+// chunk c, columns 64 c + 16 (w / 4) .. +15; SiLU(z + b) = h + h tanh(h)
+// with h = z / 2 + b / 2 (halved biases), the activations rounded to BF16,
+// the head's partial sums over each warp's columns added in a fixed order.
+// Every wait is bounded; a role whose wait gives up leaves its loop, sets
+// *err, and the CTA drains its copies and MMAs before freeing the TMEM.
+// ---------------------------------------------------------------------------
+constexpr int kPairWarps = 16;                           // epilogue warps
+constexpr int kPairThreads = 32 * (kPairWarps + 2);      // + MMA warp + copy warp
+constexpr int kPairSlots = 3;                            // weight K-block slots
+constexpr size_t kPairSmem = 1024 + 2 * 65536 + (size_t)kPairSlots * 32768 + 256;
+
+__global__ void __launch_bounds__(kPairThreads, 1)
+k_mlp_infer_pair(RowSpec rs, const uint4 *__restrict__ ftab, const uint32_t *__restrict__ lam5, long long real,
+                 long long ntiles, const unsigned char *__restrict__ img1, const unsigned char *__restrict__ img2,
+                 const unsigned char *__restrict__ img3, const __grid_constant__ MlpBias bias,
+                 float *__restrict__ logit, int *err)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    unsigned char *sH = sm;                      // 64 KB
-    unsigned char *sW1 = sm + 65536;             // 32 KB
-    unsigned char *sW = sW1 + 32768;             // 128 KB
-    uint64_t *bar_l = reinterpret_cast<uint64_t *>(sW + 131072);   // a layer's MMAs complete
-    uint64_t *bar_w1 = bar_l + 1;                // W1 image landed
-    uint64_t *bar_w = bar_l + 2;                 // [4] K-block of the W2/W3 image landed
-    uint64_t *bar_c = bar_l + 6;                 // [4] epilogue chunk written by every thread
-    uint32_t *holder = reinterpret_cast<uint32_t *>(bar_l + 10);
-    float *part = reinterpret_cast<float *>(sH + 16384);   // head partials [4][128] in K-block 1 of H
+    unsigned char *const sH0 = sm, *const sH1 = sm + 65536;   // H of tile A, B
+    unsigned char *const sW = sm + 2 * 65536;                  // weight slots
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sW + kPairSlots * 32768);
+    uint64_t *full = bars;                       // [3] slot holds its K-block
+    uint64_t *empty = bars + 3;                  // [3] slot's MMAs done (both tiles)
+    uint64_t *accr = bars + 6;                   // [2] a layer's MMAs of tile X done
+    uint64_t *chunk = bars + 8;                  // [2][4] chunk c of tile X written
+    uint64_t *feat = bars + 16;                  // [2] features written, accumulator read
+    uint64_t *drain = bars + 18;                 // every issued MMA done
+    uint64_t *partd = bars + 19;                 // [2] head partial sums of tile X written
+    uint32_t *holder = reinterpret_cast<uint32_t *>(bars + 21);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, cpart = warp >> 2;
     if (warp == 0) tmem_alloc(holder, 512);
     if (tid == 0) {
-        mbar_init(bar_l, 1);
-        mbar_init(bar_w1, 1);
-        for (int c = 0; c < 4; ++c) {
-            mbar_init(&bar_w[c], 1);
-            mbar_init(&bar_c[c], kInferWarps);
+        for (int s = 0; s < kPairSlots; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
         }
+        for (int x = 0; x < 2; ++x) {
+            mbar_init(&accr[x], 1);
+            mbar_init(&feat[x], kPairWarps);
+            mbar_init(&partd[x], kPairWarps);
+        }
+        for (int i = 0; i < 8; ++i) mbar_init(&chunk[i], kPairWarps);
+        mbar_init(drain, 1);
         fence_mbar_init();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = *holder;
-    constexpr uint32_t idesc = idesc_bf16(128, kHid);
-    uint32_t n_l = 0, n_w1 = 0, n_w = 0, n_c = 0;   // completed phases expected on each barrier (set)
+    const long long npairs = (ntiles + 1) / 2;
+    auto slot = [&](long long q) { return sW + (int)(q % kPairSlots) * 32768; };
     bool ok = true;
-    auto copy_w = [&](const unsigned char *img) {   // thread 0: the four K-blocks of a W2/W3 image
-        for (int c = 0; c < 4; ++c) {
-            mbar_arrive_expect_tx(&bar_w[c], 32768);
-            bulk_g2s(sW + c * 32768, img + c * 32768, 32768, &bar_w[c]);
+    if (warp == kPairWarps + 1) {
+        // ---- copy warp: K-block q of the sequence into slot q mod 3 once the
+        // block that held it (q - 3) is released ----
+        long long q = 0;
+        long long lastq[kPairSlots] = {-1, -1, -1};
+        for (long long p = blockIdx.x; ok && p < npairs; p += gridDim.x) {
+            for (int j = 0; j < 9; ++j, ++q) {
+                const int s = (int)(q % kPairSlots);
+                if (q >= kPairSlots) ok = mbar_wait_warp(&empty[s], (uint32_t)(((q / kPairSlots) & 1) ^ 1));
+                if (!ok) break;
+                if (lane == 0) {
+                    const unsigned char *src = j == 0 ? img1 : (j < 5 ? img2 + (j - 1) * 32768 : img3 + (j - 5) * 32768);
+                    mbar_arrive_expect_tx(&full[s], 32768);
+                    bulk_g2s(sW + s * 32768, src, 32768, &full[s]);
+                }
+                lastq[s] = q;
+            }
         }
-    };
-    auto wait = [&](uint64_t *bar, uint32_t &n) {   // the phase stays pending on failure
-        const bool r = mbar_wait_warp(bar, n & 1);
-        if (r) ++n;
-        return r;
-    };
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar_w1, 32768);
-        bulk_g2s(sW1, img1, 32768, bar_w1);
-        copy_w(img2);
-    }
-    ok = wait(bar_w1, n_w1);
-    const int row = quarter * 32 + lane;                       // this thread's TMEM lane = tile row
-    const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16);
-    auto publish = [&]() {   // generic smem writes -> tensor-core reads; TMEM reads done
+        if (!ok) {
+            // the copies this warp issued complete before the CTA ends (bounded)
+            for (int s = 0; s < kPairSlots; ++s)
+                if (lastq[s] >= 0) mbar_wait_warp(&full[s], (uint32_t)((lastq[s] / kPairSlots) & 1));
+        }
+    } else if (warp == kPairWarps) {
+        // ---- MMA warp ----
+        constexpr uint32_t idesc = idesc_bf16(128, kHid);
+        uint32_t nfeat[2] = {0, 0}, nchunk[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        long long q = 0;
+        auto wfull = [&](long long qq) {
+            return mbar_wait_warp(&full[qq % kPairSlots], (uint32_t)((qq / kPairSlots) & 1));
+        };
+        auto wchunk = [&](int x, int c) {
+            const bool r = mbar_wait_warp(&chunk[4 * x + c], nchunk[4 * x + c] & 1);
+            if (r) ++nchunk[4 * x + c];
+            return r;
+        };
+        // the four K = 16 MMAs of one K-block of tile x (a: its A operand block)
+        auto mma_kb = [&](int x, const unsigned char *a, const unsigned char *b, bool first) {
+            if (lane == 0) {
+                tc_fence_after();
+                const uint64_t da = desc_sw128(a), db = desc_sw128(b);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tc_mma_bf16(taddr + 256u * x, da + 2 * k, db + 2 * k, idesc, (!first || k > 0) ? 1u : 0u);
+            }
+            __syncwarp();
+        };
+        for (long long p = blockIdx.x; ok && p < npairs; p += gridDim.x) {
+            // layer 1 (K = 64: one block, the features)
+            ok = wfull(q) && mbar_wait_warp(&feat[0], nfeat[0] & 1);
+            if (!ok) break;
+            ++nfeat[0];
+            mma_kb(0, sH0, slot(q), true);
+            if (lane == 0) tc_commit(&accr[0]);
+            ok = mbar_wait_warp(&feat[1], nfeat[1] & 1);
+            if (!ok) break;
+            ++nfeat[1];
+            mma_kb(1, sH1, slot(q), true);
+            if (lane == 0) {
+                tc_commit(&accr[1]);
+                tc_commit(&empty[q % kPairSlots]);
+            }
+            ++q;
+            // layers 2 and 3: A0 A1 A2 B0 B1 B2 A3 B3
+            for (int l = 0; l < 2 && ok; ++l, q += 4) {
+                for (int c = 0; c < 3 && ok; ++c) {
+                    ok = wfull(q + c) && wchunk(0, c);
+                    if (ok) mma_kb(0, sH0 + c * 16384, slot(q + c), c == 0);
+                }
+                for (int c = 0; c < 3 && ok; ++c) {
+                    ok = wchunk(1, c);
+                    if (ok) {
+                        mma_kb(1, sH1 + c * 16384, slot(q + c), c == 0);
+                        if (lane == 0) tc_commit(&empty[(q + c) % kPairSlots]);
+                    }
+                }
+                if (ok) ok = wfull(q + 3) && wchunk(0, 3);
+                if (ok) {
+                    mma_kb(0, sH0 + 3 * 16384, slot(q + 3), false);
+                    if (lane == 0) tc_commit(&accr[0]);
+                    ok = wchunk(1, 3);
+                }
+                if (ok) {
+                    mma_kb(1, sH1 + 3 * 16384, slot(q + 3), false);
+                    if (lane == 0) {
+                        tc_commit(&accr[1]);
+                        tc_commit(&empty[(q + 3) % kPairSlots]);
+                    }
+                }
+            }
+        }
+        // every MMA this warp issued completes before the TMEM is freed (bounded)
+        if (lane == 0) tc_commit(drain);
+        __syncwarp();
+        mbar_wait_warp(drain, 0);
+    } else {
+        // ---- epilogue warps ----
+        const int quarter = warp & 3, cpart = warp >> 2;
+        const int row = quarter * 32 + lane;                  // this thread's TMEM lane = tile row
+        const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
+        uint32_t nacc[2] = {0, 0}, npart[2] = {0, 0};
+        // the features of tile t into K-block 0 of H, spread over every
+        // epilogue thread: row tid / 4, 16-byte words 2 (tid mod 4) and the
+        // next one; the bin's row of the table with lambda / 5 in place of
+        // input 2 (the low half of word 1)
+        auto features = [&](long long t, unsigned char *H) {
+            const int r = tid >> 2, j0 = (tid & 3) * 2;
+            const long long rr = t * 128 + r;
+            uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
+            if (rr < real) {
+                const int li = (int)(rr / rs.per_member);
+                const long long bin = rr - (long long)li * rs.per_member;
+                v0 = ftab[bin * (kIn / 8) + j0];
+                v1 = ftab[bin * (kIn / 8) + j0 + 1];
+                if (j0 == 0) v0.y = (v0.y & 0xFFFF0000u) | lam5[li];
+            }
+            *reinterpret_cast<uint4 *>(H + sw128_offset(r, 8 * j0)) = v0;
+            *reinterpret_cast<uint4 *>(H + sw128_offset(r, 8 * j0 + 8)) = v1;
+        };
+        // the first pair's features
+        features(2 * (long long)blockIdx.x, sH0);
+        features(2 * (long long)blockIdx.x + 1, sH1);
         fence_proxy_async_smem();
-        tc_fence_before();
-        __syncthreads();
-    };
-    // Epilogue of the layer in accumulator `acc` (bias + SiLU into H, BF16,
-    // swizzled K-blocks) in four column chunks; warp 0 issues the next
-    // layer's MMAs (into `acc_next`, weights in sW) chunk by chunk and
-    // commits them to bar_l.  The load of chunk c + 1 is in flight while
-    // chunk c is processed.
-    auto epilogue_chain = [&](uint32_t acc, const float *bv, uint32_t acc_next) {
-        if (warp < kInferWarps) {
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&feat[0]);
+            mbar_arrive(&feat[1]);
+        }
+        // epilogue of a hidden layer of tile x (bias bv): H_x chunk c, arrival c
+        // (every chunk's load is waited for before the first arrival: the
+        // next layer's first MMA overwrites the whole accumulator)
+        auto epilogue = [&](int x, const float *bv) {
+            if (!(ok && mbar_wait_warp(&accr[x], nacc[x] & 1))) return false;
+            ++nacc[x];
+            tc_fence_after();
+            unsigned char *H = x ? sH1 : sH0;
+            const uint32_t acc = taddr + 256u * x + lanes + (uint32_t)(16 * cpart);
             uint32_t r[4][16];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) tc_ld_16cols_issue(tl + acc + (uint32_t)(64 * c + 16 * cpart), r[c]);
+            for (int c = 0; c < 4; ++c) tc_ld_16cols_issue(acc + 64u * c, r[c]);
 #pragma unroll
             for (int c = 0; c < 4; ++c) tc_ld_wait16(r[c]);
             const float2 *bv2 = reinterpret_cast<const float2 *>(bv);
@@ -717,41 +833,35 @@ k_mlp_infer(RowSpec rs, const uint4 *__restrict__ ftab, const uint32_t *__restri
                                                bv2[col0 / 2 + t]);
                     w[t] = cvt_bf16x2(y.x, y.y);
                 }
-                unsigned char *blk = sH + c * 16384;
+                unsigned char *blk = H + c * 16384;
                 *reinterpret_cast<uint4 *>(blk + sw128_offset(row, 16 * cpart)) = make_uint4(w[0], w[1], w[2], w[3]);
                 *reinterpret_cast<uint4 *>(blk + sw128_offset(row, 16 * cpart + 8)) =
                     make_uint4(w[4], w[5], w[6], w[7]);
                 fence_proxy_async_smem();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bar_c[c]);
+                if (lane == 0) mbar_arrive(&chunk[4 * x + c]);
             }
-        } else {
-            // the MMA warp: K-block c of the next layer once chunk c is
-            // written and K-block c of its weights has landed
-#pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                ok = ok && mbar_wait_warp(&bar_c[c], n_c & 1) && mbar_wait_warp(&bar_w[c], n_w & 1);
-                if (ok && lane == 0) {
-                    tc_fence_after();
-                    const uint64_t da = desc_sw128(sH + c * 16384), db = desc_sw128(sW + c * 32768);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        tc_mma_bf16(taddr + acc_next, da + 2 * k, db + 2 * k, idesc, (c > 0 || k > 0) ? 1u : 0u);
-                    if (c == 3) tc_commit(bar_l);
-                }
-                __syncwarp();
-            }
-        }
-        ++n_c;
-        ++n_w;
-    };
-    // head of a finished tile: logit = sum_c BF16(SiLU(z3 + b3)) w4 + b4
-    auto head = [&](uint32_t acc, long long r0) {
-        if (warp < kInferWarps) {
+            return true;
+        };
+        // head of tile x (tile index t): logit = sum_c BF16(SiLU(z3 + b3)) w4 + b4.
+        // Every warp writes its partial sums and arrives on partd[x]; warps
+        // 0-3 (one row each, threads 0..127) wait for them and write the
+        // logits; every warp then puts its share of the next pair's features
+        // of this slot (tile tn) into K-block 0.  The feature arrival comes
+        // last: the next layer-1 MMAs (which overwrite the accumulator) and
+        // the epilogues after them (which overwrite K-block 1, the partial
+        // sums) wait for it.
+        auto head = [&](int x, long long t, bool next, long long tn) {
+            if (!(ok && mbar_wait_warp(&accr[x], nacc[x] & 1))) return false;
+            ++nacc[x];
+            tc_fence_after();
+            unsigned char *H = x ? sH1 : sH0;
+            float *part = reinterpret_cast<float *>(H + 16384);   // [4][128] in K-block 1
+            const uint32_t acc = taddr + 256u * x + lanes + (uint32_t)(16 * cpart);
             uint32_t r[4][16];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) tc_ld_16cols_issue(tl + acc + (uint32_t)(64 * c + 16 * cpart), r[c]);
+            for (int c = 0; c < 4; ++c) tc_ld_16cols_issue(acc + 64u * c, r[c]);
 #pragma unroll
             for (int c = 0; c < 4; ++c) tc_ld_wait16(r[c]);
             const float2 *b3 = reinterpret_cast<const float2 *>(bias.b3);
@@ -762,103 +872,47 @@ k_mlp_infer(RowSpec rs, const uint4 *__restrict__ ftab, const uint32_t *__restri
                 const uint32_t *rc = r[c];
                 const int col0 = 64 * c + 16 * cpart;
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const float2 y = silu_pair(make_float2(__uint_as_float(rc[2 * t]), __uint_as_float(rc[2 * t + 1])),
-                                               b3[col0 / 2 + t]);
+                for (int t2 = 0; t2 < 8; ++t2) {
+                    const float2 y = silu_pair(make_float2(__uint_as_float(rc[2 * t2]), __uint_as_float(rc[2 * t2 + 1])),
+                                               b3[col0 / 2 + t2]);
                     const uint32_t hb = cvt_bf16x2(y.x, y.y);   // the activations rounded to BF16
                     sum = fma2(make_float2(__uint_as_float(hb << 16), __uint_as_float(hb & 0xFFFF0000u)),
-                               w4[col0 / 2 + t], sum);
+                               w4[col0 / 2 + t2], sum);
                 }
             }
             part[cpart * 128 + row] = sum.x + sum.y;
-        }
-        tc_fence_before();
-        __syncthreads();
-        if (tid < 128 && r0 + tid < real)
-            logit[r0 + tid] = ((part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid])) + bias.b4;
-    };
-    // features of a tile's rows (threads 0..127, one row each) as packed BF16
-    // pairs: the bin's row of the feature table with lambda / 5 in place;
-    // fetched for the next tile while the last layer-3 MMAs run
-    uint32_t fw[kIn / 2];
-    auto features = [&](long long t) {
-        const long long rr = t * 128 + tid;
-        if (rr < real) {
-            const int li = (int)(rr / rs.per_member);
-            const long long bin = rr - (long long)li * rs.per_member;
-#pragma unroll
-            for (int j = 0; j < kIn / 8; ++j) {
-                const uint4 x = ftab[bin * (kIn / 8) + j];
-                fw[4 * j] = x.x;
-                fw[4 * j + 1] = x.y;
-                fw[4 * j + 2] = x.z;
-                fw[4 * j + 3] = x.w;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&partd[x]);
+            bool good = true;
+            if (warp < 4) {
+                good = mbar_wait_warp(&partd[x], npart[x] & 1);
+                if (good && t * 128 + tid < real)
+                    logit[t * 128 + tid] = ((part[tid] + part[128 + tid]) + (part[256 + tid] + part[384 + tid])) + bias.b4;
             }
-            fw[1] = (fw[1] & 0xFFFF0000u) | lam5[li];
-        } else {
-#pragma unroll
-            for (int j = 0; j < kIn / 2; ++j) fw[j] = 0u;
+            ++npart[x];
+            if (good && next) features(tn, H);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0 && good) mbar_arrive(&feat[x]);
+            return good;
+        };
+        for (long long p = blockIdx.x; p < npairs; p += gridDim.x) {
+            const long long pn = p + gridDim.x;
+            const bool next = pn < npairs;
+            ok = epilogue(0, bias.b1);
+            ok = epilogue(1, bias.b1);
+            ok = epilogue(0, bias.b2);
+            ok = epilogue(1, bias.b2);
+            ok = head(0, 2 * p, next, 2 * pn);
+            ok = head(1, 2 * p + 1, next, 2 * pn + 1);
+            if (!ok) break;   // (each warp on its own: no CTA-wide barrier in the loop)
         }
-    };
-    if (tid < 128 && (long long)blockIdx.x < ntiles) features(blockIdx.x);
-    uint32_t a = 0;              // accumulator (TMEM column offset) of the next layer
-    long long prev = -1;         // tile whose head is pending
-    uint32_t acc_prev = 0;
-#pragma unroll 1
-    for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-        // features of the tile into K-block 0 of H (layer 3 of the previous tile is done)
-        if (tid < 128) {
-#pragma unroll
-            for (int j = 0; j < kIn; j += 8)
-                *reinterpret_cast<uint4 *>(sH + sw128_offset(tid, j)) =
-                    make_uint4(fw[j / 2], fw[j / 2 + 1], fw[j / 2 + 2], fw[j / 2 + 3]);
-        }
-        publish();
-        // layer 1 (K = 64) into accumulator a
-        const uint32_t a1 = a;
-        if (tid == 0) {
-            tc_fence_after();
-            const uint64_t da = desc_sw128(sH), db = desc_sw128(sW1);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) tc_mma_bf16(taddr + a1, da + 2 * k, db + 2 * k, idesc, k > 0 ? 1u : 0u);
-            tc_commit(bar_l);
-        }
-        a ^= 256;
-        // the previous tile's head reads the other accumulator meanwhile
-        if (prev >= 0) head(acc_prev, prev * 128);
-        ok = wait(bar_l, n_l);
-        tc_fence_after();
-        if (!__syncthreads_and(ok)) break;
-        // epilogue 1, layer-2 MMAs chunk by chunk into accumulator a
-        const uint32_t a2 = a;
-        epilogue_chain(a1, bias.b1, a2);
-        a ^= 256;
-        ok = ok && wait(bar_l, n_l);
-        tc_fence_after();
-        if (!__syncthreads_and(ok)) break;
-        if (tid == 0) copy_w(img3);   // the layer-2 MMAs no longer read sW
-        // epilogue 2, layer-3 MMAs chunk by chunk as the W3 K-blocks land
-        const uint32_t a3 = a;
-        epilogue_chain(a2, bias.b2, a3);
-        a ^= 256;
-        // the next tile's features while the last layer-3 MMAs run
-        if (tid < 128 && tile + gridDim.x < ntiles) features(tile + gridDim.x);
-        ok = ok && wait(bar_l, n_l);
-        tc_fence_after();
-        if (!__syncthreads_and(ok)) break;
-        if (tid == 0 && tile + gridDim.x < ntiles) copy_w(img2);   // for the next tile
-        prev = tile;
-        acc_prev = a3;
     }
-    if (ok && prev >= 0) head(acc_prev, prev * 128);
-    if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-        // copies or MMAs may still be in flight: bounded waits before freeing
-        for (int c = 0; c < 4; ++c) mbar_wait_warp(&bar_w[c], n_w & 1);
-        mbar_wait_warp(bar_l, n_l & 1);
-    }
+    if (!ok && lane == 0) atomicExch(err, 1);
     tc_fence_before();
     __syncthreads();
+    tc_fence_after();
     if (warp == 0) tmem_dealloc(taddr, 512);
 }
 
@@ -967,6 +1021,17 @@ bool mlp_bias(ens_surrogate *S, MlpBias *b)
            cudaStreamSynchronize(s) == cudaSuccess && halve_biases(b);
 }
 
+// the fused inference kernel over `real` rows of the feature table ftab
+// (one CTA per tile pair, at most one per SM)
+void launch_infer(ens_surrogate *S, const RowSpec &rs, const uint4 *ftab, long long real, const MlpBias &bias)
+{
+    const long long ntiles = (real + 127) / 128;
+    const int grid = (int)std::min<long long>((ntiles + 1) / 2, S->sms > 0 ? S->sms : 1);
+    unsigned char *i1 = S->img, *i2 = S->img + 32768, *i3 = S->img + 32768 + 131072;
+    k_mlp_infer_pair<<<grid, kPairThreads, kPairSmem, S->s>>>(rs, ftab, S->lam5, real, ntiles, i1, i2, i3, bias,
+                                                              S->logit, S->err);
+}
+
 // fused inference of `real` rows (lambda values in S->lam) into S->logit
 bool forward_fused(ens_surrogate *S, const RowSpec &rs, long long real)
 {
@@ -975,13 +1040,10 @@ bool forward_fused(ens_surrogate *S, const RowSpec &rs, long long real)
     MlpBias bias;
     if (!mlp_bias(S, &bias)) return false;
     k_pack_weights_img<<<blocks(n, 256), 256, 0, s>>>(S->p, S->img, S->img + 32768, S->img + 32768 + 131072);
-    const long long ntiles = (real + 127) / 128;
-    const int grid = (int)std::min<long long>(ntiles, S->sms > 0 ? S->sms : 1);
     const int nlam = (int)(real / rs.per_member);
     uint4 *ftab = reinterpret_cast<uint4 *>(S->Xt);   // the training path's transposed features: free here
     k_feature_table<<<blocks(std::max(rs.per_member, nlam), 256), 256, 0, s>>>(rs, S->lam, nlam, ftab, S->lam5);
-    k_mlp_infer<<<grid, kInferThreads, kInferSmem, s>>>(rs, ftab, S->lam5, real, ntiles, S->img, S->img + 32768,
-                                                       S->img + 32768 + 131072, bias, S->logit, S->err);
+    launch_infer(S, rs, ftab, real, bias);
     return cudaGetLastError() == cudaSuccess;
 }
 
@@ -1064,7 +1126,7 @@ ens_status ens_surrogate_create(uint64_t seed, void *stream, ens_surrogate **out
          cudaMalloc(&S->err, sizeof(int)) == cudaSuccess && cudaMalloc(&S->wq, sizeof(double) * 4096) == cudaSuccess &&
          cudaMalloc(&S->pdf, sizeof(double) * 1 << 20) == cudaSuccess &&
          cudaMalloc(&S->img, 32768 + 2 * 131072) == cudaSuccess &&
-         cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem) ==
+         cudaFuncSetAttribute(k_mlp_infer_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem) ==
              cudaSuccess;
     int dev = 0;
     ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
@@ -1326,19 +1388,13 @@ ens_status ens_surrogate_time_infer(ens_surrogate *S, const ens_hist_spec *h, in
     const long long real = (long long)nquad * rs.per_member, rows = pad128(real);
     if (!alloc_work(S, rows, 3 * nquad)) return ENS_ENOMEM;
     k_quad_weights<<<1, 256, 0, S->s>>>(-5.0, 5.0, nquad, 1, 0.0, 0.0, 0.0, 1.0, S->lam, S->wq);
-    const long long ntiles = (real + 127) / 128;
-    const int grid = (int)std::min<long long>(ntiles, S->sms > 0 ? S->sms : 1);
     k_pack_weights_img<<<blocks((long long)kHid * kHid, 256), 256, 0, S->s>>>(S->p, S->img, S->img + 32768,
                                                                               S->img + 32768 + 131072);
     MlpBias bias;
     if (!mlp_bias(S, &bias)) return ENS_ECUDA;
     uint4 *ftab = reinterpret_cast<uint4 *>(S->Xt);
     k_feature_table<<<blocks(std::max(rs.per_member, nquad), 256), 256, 0, S->s>>>(rs, S->lam, nquad, ftab, S->lam5);
-    auto launch = [&]() {
-        k_mlp_infer<<<grid, kInferThreads, kInferSmem, S->s>>>(rs, ftab, S->lam5, real, ntiles, S->img,
-                                                               S->img + 32768, S->img + 32768 + 131072, bias,
-                                                               S->logit, S->err);
-    };
+    auto launch = [&]() { launch_infer(S, rs, ftab, real, bias); };
     launch();   // warm-up
     cudaEvent_t a, b;
     cudaEventCreate(&a);
