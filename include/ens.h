@@ -272,8 +272,9 @@ ens_status ens_get_tuning(const ens_ctx *ctx, ens_tuning *out);
  * the next ens_step captures a new graph. */
 ens_status ens_set_tuning(ens_ctx *ctx, const ens_tuning *t);
 /* Time the variants on this context's own members and install the fastest:
- * coordinate descent over plan_x, tile_x, tile_y, the z variant and its CTAs
- * per SM, fx_split (0, 1, 2) for each group, then parallel_groups, then persistent
+ * coordinate descent in two sweeps, each over parallel_groups and then, for
+ * each group, plan_x, tile_x, tile_y, the z variant and its CTAs per SM and
+ * fx_split (0, 1, 2); then persistent
  * (where available); each trial restores the member
  * state from a device snapshot, runs one untimed step and times `steps`
  * graph replays with CUDA events; a candidate wins only if it is more than

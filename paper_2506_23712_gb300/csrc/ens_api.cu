@@ -1434,8 +1434,28 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
         best_ms = trial(best);
         if (best_ms < 0.0) rs = rs == ENS_OK ? ENS_ECUDA : rs;
     }
-    // coordinate descent over the knobs, group by group
-    for (int gi = 0; rs == ENS_OK && gi < best.groups; ++gi) {
+    // coordinate descent over the knobs in two sweeps: parallel or serial
+    // grid-size groups first (the groups' own knobs rank differently under
+    // the two), then group by group; in the first sweep a group's gain is
+    // judged against a step whose later groups are still untuned (a smaller
+    // relative gain than once they are tuned)
+    for (int sweep = 0; sweep < 2; ++sweep)
+    for (int gi = -1; rs == ENS_OK && gi < best.groups; ++gi) {
+        if (gi < 0) {
+            if (sweep == 1) {
+                // the incumbent's time afresh: the time it won with is biased
+                // low (the fastest of several noisy trials)
+                const double ms = trial(best);
+                if (ms < 0.0) break;
+                best_ms = ms;
+            }
+            if (best.groups > 1) {
+                cand = best;
+                cand.parallel_groups = 1 - best.parallel_groups;
+                if (!consider(cand)) break;
+            }
+            continue;
+        }
         const int N = best.group[gi].N;
         if (plan_variant_available(N)) {
             cand = best;
@@ -1484,11 +1504,6 @@ ens_status ens_autotune(ens_ctx *ctx, int steps, ens_tuning *out)
             cand.group[gi].fx_split = fx;
             consider(cand);
         }
-    }
-    if (rs == ENS_OK && best.groups > 1) {
-        cand = best;
-        cand.parallel_groups = 1 - best.parallel_groups;
-        consider(cand);
     }
     if (rs == ENS_OK && ctx->pitems && ctx->persist_ctas > 0) {
         cand = best;
