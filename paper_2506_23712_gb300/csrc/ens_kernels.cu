@@ -371,10 +371,10 @@ __global__ void k_bin_check(HistDev h, int axis, const float *__restrict__ x, in
     if (i >= n) return;
     const float v = x[i];
     int b;
-    if (axis == 0) b = bin_lin(v, h.q_lo, h.q_inv_w, h.edges_q, h.nq);
-    else if (axis == 1) b = bin_lin(v, h.r_lo, h.r_inv_w, h.edges_r, h.nq);
-    else if (axis == 2) b = bin_log(v, h.t_lo, h.t_inv_w, h.edges_t, h.nt);
-    else b = bin_lin(v, h.g_lo, h.g_inv_w, h.edges_g, h.ng);
+    if (axis == 0) b = bin_lin(v, lin_map(h.q_lo, h.q_inv_w), h.edges_q, h.nq);
+    else if (axis == 1) b = bin_lin(v, lin_map(h.r_lo, h.r_inv_w), h.edges_r, h.nq);
+    else if (axis == 2) b = bin_log(v, log_map(h.t_lo, h.t_inv_w), h.edges_t, h.nt);
+    else b = bin_lin(v, lin_map(h.g_lo, h.g_inv_w), h.edges_g, h.ng);
     out[i] = b;
 }
 

@@ -49,15 +49,23 @@ __device__ __forceinline__ int bin_tab(float x, float t, const float *e, int n)
     return b + (x >= e[b + 1] ? 1 : 0) - (x < e[b] ? 1 : 0);
 }
 
-__device__ __forceinline__ int bin_lin(float x, float lo, float inv_w, const float *e, int n)
+// Estimate maps in one FMA each: (x - lo) / w as x a + c, log10(x) -
+// lo over w as log2(x) a + c (the edge comparison decides)
+struct BinMap {
+    float a, c;
+};
+__device__ __forceinline__ BinMap lin_map(float lo, float inv_w) { return {inv_w, -lo * inv_w}; }
+__device__ __forceinline__ BinMap log_map(float lo, float inv_w) { return {0.30102999566f * inv_w, -lo * inv_w}; }
+
+__device__ __forceinline__ int bin_lin(float x, BinMap m, const float *e, int n)
 {
-    return bin_tab(x, (x - lo) * inv_w, e, n);
+    return bin_tab(x, fmaf(x, m.a, m.c), e, n);
 }
 
-// log10 bins from the hardware log2 (the edge comparison decides)
-__device__ __forceinline__ int bin_log(float x, float lo, float inv_w, const float *e, int n)
+// log10 bins from the hardware log2
+__device__ __forceinline__ int bin_log(float x, BinMap m, const float *e, int n)
 {
-    return bin_tab(x, (__log2f(x) * 0.30102999566f - lo) * inv_w, e, n);
+    return bin_tab(x, fmaf(__log2f(x), m.a, m.c), e, n);
 }
 
 // increment of hist[key] without aggregation (key < 0: none)
@@ -92,8 +100,11 @@ struct SCfg {
     static constexpr bool PAD = WPad<N>::on;
     static constexpr int SROW = PAD ? WPad<N>::SROW : RowCfg<N>::SROW;
     // warps per CTA: 12 where the plan's four lines fit the register share
-    // of 12 resident warps, 8 for the 12- and 16-value plans (384, 512)
-    static constexpr int WPB = V > 8 ? 8 : 12;
+    // of 12 resident warps, 8 for the 12- and 16-value plans (384, 512); 16
+    // at 256 (128 registers with a few spilled: 24.7 against 25.1 ms per
+    // 64-member snapshot; 14 warps, unevenly spread over the four schedulers,
+    // 26.3 ms)
+    static constexpr int WPB = V > 8 ? 8 : (N == 256 ? 16 : 12);
     static constexpr int GROUPS = N * N / LPW;               // row groups per member
     static constexpr int LT = PAD ? (LaneTw<N>::SIZE + 1) / 2 * 2 : 0;   // lane-major twiddles (float2)
     // CTAs per member: a power of two up to 32, at least 32 row groups per warp
@@ -199,6 +210,8 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
     auto at = [&](int pos) { return row_slot<N>(rowbuf, line, pos); };
     float2 *myrow = rowbuf + line * C::SROW;
     const int off_e = h.nq * h.nq, off_w = off_e + h.nt, off_c = off_w + h.nt;
+    const BinMap mq = lin_map(h.q_lo, h.q_inv_w), mr = lin_map(h.r_lo, h.r_inv_w);
+    const BinMap mt = log_map(h.t_lo, h.t_inv_w), mg = lin_map(h.g_lo, h.g_inv_w);
     const int off_gl = off_c + 8, off_gt = off_gl + h.ng, off_gc = off_gt + h.ng;
 
     // FP32 moment partials: component pairs (2q, 2q + 1) packed, A_33 alone,
@@ -276,10 +289,10 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
             const bool finite = isfinite(ss);
             // keys of all four lookups, then one select for a non-finite
             // point (its bins are meaningless but in the table's range)
-            const int bq = bin_lin(xq, h.q_lo, h.q_inv_w, eq, h.nq);
-            const int br = bin_lin(xr, h.r_lo, h.r_inv_w, er, h.nq);
-            const int be = bin_log(xe, h.t_lo, h.t_inv_w, et, h.nt);
-            const int bw = bin_log(xw, h.t_lo, h.t_inv_w, et, h.nt);
+            const int bq = bin_lin(xq, mq, eq, h.nq);
+            const int br = bin_lin(xr, mr, er, h.nq);
+            const int be = bin_log(xe, mt, et, h.nt);
+            const int bw = bin_log(xw, mt, et, h.nt);
             int kq = ((unsigned)bq < (unsigned)h.nq && (unsigned)br < (unsigned)h.nq) ? bq * h.nq + br : off_c + 0;
             int ke = be < 0 ? off_c + 1 : (be >= h.nt ? off_c + 2 : off_e + be);
             int kw = bw < 0 ? off_c + 3 : (bw >= h.nt ? off_c + 4 : off_w + bw);
@@ -298,7 +311,7 @@ k_z_stats(Geo g, HistDev h, const MemberDev *md)
                 for (int c = 0; c < 9; ++c) {
                     int kg = -1;
                     if (finite) {
-                        const int bg = bin_lin(A[c] * h.g_scale, h.g_lo, h.g_inv_w, eg, h.ng);
+                        const int bg = bin_lin(A[c] * h.g_scale, mg, eg, h.ng);
                         const bool lon = c % 4 == 0;
                         kg = bg < 0 ? off_gc + (lon ? 0 : 2)
                                     : (bg >= h.ng ? off_gc + (lon ? 1 : 3) : (lon ? off_gl : off_gt) + bg);
