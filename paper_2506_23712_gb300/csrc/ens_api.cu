@@ -142,6 +142,25 @@ ens_status validate(const ens_member_desc *m, int n, const ens_hist_spec *h, std
             why = buf;
             return ENS_EINVAL;
         }
+        {
+            // the band must hold a wave vector other than k = 0: an integer
+            // k^2 >= 1 in [k_lo^2, k_hi^2] that is a sum of three squares (not
+            // of the form 4^a (8 b + 7)); its components are <= |k| <= kc, so
+            // the mode is kept.  Otherwise E_B = 0 and the forcing is undefined.
+            const long long lo2 = std::max(1LL, (long long)std::ceil(d.k_lo * d.k_lo - 1e-9));
+            const long long hi2 = (long long)std::floor(d.k_hi * d.k_hi + 1e-9);
+            bool any = false;
+            for (long long q = lo2; q <= hi2 && !any; ++q) {
+                long long r = q;
+                while (r % 4 == 0) r /= 4;
+                any = r % 8 != 7;
+            }
+            if (!any) {
+                snprintf(buf, sizeof buf, "member %d: band [%g, %g] holds no wave vector besides k = 0", i, d.k_lo, d.k_hi);
+                why = buf;
+                return ENS_EINVAL;
+            }
+        }
         if (!(d.dt > 0.0) && !(d.cfl > 0.0)) { snprintf(buf, sizeof buf, "member %d: need dt > 0 or cfl > 0", i); why = buf; return ENS_EINVAL; }
         if (!(d.init_energy > 0.0)) { snprintf(buf, sizeof buf, "member %d: init_energy must be > 0", i); why = buf; return ENS_EINVAL; }
     }

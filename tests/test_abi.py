@@ -49,6 +49,16 @@ def test_query_validates_on_host(lib):
     assert e.value.status == 1
     with pytest.raises(E.EnsError):
         E.ens_query([E.Member(N=32, nu=-1.0).c()], h)
+    # degenerate forcing bands: no wave vector at all, only k = 0, or only
+    # |k|^2 = 7 (not a sum of three squares): the forcing amplitude would be
+    # undefined (E_B = 0)
+    for lo, hi in ((2.5, 2.6), (0.0, 0.5), (7 ** 0.5, 7 ** 0.5)):
+        with pytest.raises(E.EnsError) as e:
+            E.ens_query([E.Member(N=32, nu=0.02, k_lo=lo, k_hi=hi).c()], h)
+        assert e.value.status == 1, (lo, hi)
+    assert E.ens_query([E.Member(N=32, nu=0.02, k_lo=6 ** 0.5, k_hi=6 ** 0.5).c()], h) > 0   # (1, 1, 2)
+    with pytest.raises(E.EnsError):        # no members
+        E.ens_query([], h)
     with pytest.raises(E.EnsError):        # mixed RK orders
         E.ens_query([E.Member(N=32, nu=0.02, rk_order=2).c(), E.Member(N=32, nu=0.02, rk_order=3).c()], h)
     # workspace grows with the member count and with N
