@@ -304,7 +304,8 @@ k_inv_y(Geo g, int f0)
 // (N <= 256: registers capped for 40 resident warps per SM, the plain y
 // pass's occupancy; the larger plans keep their registers)
 template <int N, int T>
-__global__ void __launch_bounds__(ColCfg<N, T, 0>::threads, N <= 256 ? 1280 / ColCfg<N, T, 0>::threads : 1)
+__global__ void __launch_bounds__(ColCfg<N, T, 0>::threads,
+                                   N <= 256 ? (1280 / ColCfg<N, T, 0>::threads < 32 ? 1280 / ColCfg<N, T, 0>::threads : 32) : 1)
 k_inv_y_grad(Geo g)
 {
     using PI = PlanInfo<N, 0>;
