@@ -679,7 +679,7 @@ def main():
         e2e = {"value": world * n_mem * e2e_steps / sec, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + diag_bytes, "steps": e2e_steps,
                "windows_member_steps_per_s": [round(world * n_mem * e2e_steps / w, 1) for w in windows],
-               "path": "ens_step_host(pinned host in/out, members in eight chunks: upload, step and download "
+               "path": "ens_step_host(pinned host in/out, members in chunks tapered by a factor 3 at both ends: upload, step and download "
                        "overlapped) + ens_diagnostics", "serial_value": serial, "host_binding": numa}
 
     plain = None

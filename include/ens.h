@@ -192,9 +192,10 @@ ens_status ens_step_sequential(ens_ctx *ctx, int nsteps);
  * in host memory: host_in holds the state in the layout of ens_get_state
  * (bytes >= ens_state_bytes), the stepped state is written to host_out
  * (host_out may equal host_in).  The members go through in chunks of
- * `chunk` members of one grid size (0: an eighth of each group, at least
- * one, with the first three and the last three chunks an eighth, a quarter
- * and a half of that, so that the pipeline fills and drains quickly): a
+ * `chunk` members of one grid size (0: per group, sizes growing by a factor
+ * 3 from one member up to a third of the group, the middle in chunks of at
+ * most that and the same sizes shrinking at the end, e.g. 1 3 9 19 19 9 3 1
+ * for 64 members, so that the pipeline fills and drains quickly): a
  * chunk's upload,
  * its energy sums (as after ens_set_state), its
  * three RK stages and its download are ordered on the device, and the

@@ -742,10 +742,14 @@ ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size
         ENS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
         ENS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
     }
-    // chunk sizes per group: `chunk` members each, or (chunk = 0) an eighth
-    // of the group with the first three and the last three chunks an eighth,
-    // a quarter and a half of that, so that the upload before the first
-    // compute and the download after the last one are short
+    // chunk sizes per group: `chunk` members each, or (chunk = 0) sizes
+    // growing by a factor 3 from one member up to a third of the group, the
+    // middle in chunks of at most that, and the same sizes shrinking at the
+    // end (M = 64: 1 3 9 19 19 9 3 1): the upload before the first compute and
+    // the download after the last one are one member each, and each upload
+    // (1/2.7 of its chunk's compute time per member at ~200 GB/s) lands while
+    // the chunk before it computes; fewer chunks than equal eighths, so fewer
+    // small launches
     std::vector<std::vector<int>> sched(ctx->groups.size());
     int nchunks = 0;
     for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
@@ -754,21 +758,22 @@ ens_status ens_step_host(ens_ctx *ctx, const void *host_in, void *host_out, size
         if (chunk > 0) {
             for (int k = 0; k < M; k += chunk) v.push_back(std::min(chunk, M - k));
         } else {
-            const int c = std::max(1, (M + 7) / 8);
-            const int e = std::max(1, c / 8), q = std::max(1, c / 4), h = std::max(1, c / 2);
-            if (M >= 2 * (e + q + h) + c) {
-                v = {e, q, h};
-                int left = M - 2 * (e + q + h);
-                while (left > 0) {
-                    v.push_back(std::min(c, left));
-                    left -= v.back();
-                }
-                v.push_back(h);
-                v.push_back(q);
-                v.push_back(e);
-            } else {
-                for (int k = 0; k < M; k += c) v.push_back(std::min(c, M - k));
+            const int cap = std::max(1, M / 3);
+            std::vector<int> up;
+            int used = 0;
+            for (int sz = 1; sz <= cap && used + 2 * sz <= M; sz *= 3) {
+                up.push_back(sz);
+                used += 2 * sz;
             }
+            int left = M - used;
+            const int nmid = (left + cap - 1) / cap;
+            v = up;
+            for (int k = 0; k < nmid; ++k) {
+                const int sz = left / (nmid - k);
+                v.push_back(sz);
+                left -= sz;
+            }
+            for (int k = (int)up.size() - 1; k >= 0; --k) v.push_back(up[k]);
         }
         nchunks += (int)v.size();
     }
