@@ -432,12 +432,12 @@ def test_histogram_layout_too_large_is_refused(E, capfd):
 
 
 @pytest.mark.parametrize("N", [16, 64, 128, pytest.param(256, marks=pytest.mark.slow),
-                               pytest.param(384, marks=pytest.mark.slow)])
+                               pytest.param(384, marks=pytest.mark.slow), pytest.param(512, marks=pytest.mark.slow)])
 def test_statistics_pass_shapes_match_oracle_on_same_field(E, N, parity_log):
     """The statistics pass in each of its launch shapes (several rows per
     warp at N <= 128, several CTAs per member from N = 64, 16 warps per CTA
-    at 256, the XOR-swizzled non-power-of-two plan at 384) against the
-    oracle's statistics of the very
+    at 256, the XOR-swizzled non-power-of-two plan at 384, 8 warps of the
+    16-value plan at 512) against the oracle's statistics of the very
     same spectral field: 2% in every bin above 1000 counts, exact point
     count, moments to 1e-4.  On the same field the sparse bins (the tails)
     can differ only where FP32 rounding moves a point across an edge: their
