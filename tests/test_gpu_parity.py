@@ -270,6 +270,48 @@ def test_gradient_component_histograms_match_oracle(E):
     ens.close()
 
 
+@pytest.mark.slow
+def test_gradient_component_histograms_256_same_field(E, parity_log):
+    """The gradient-component histograms at 256^3 (the 16-warp launch shape
+    of the statistics pass, warp-aggregated increments) against the oracle's
+    on the very same field: 2% in every bin above 1000 counts, 3 and 6
+    samples per point, and the Q-R / tail part equal to a context without
+    gradient bins."""
+    m = E.Member(N=256, nu=0.02, lam=0.0, eps_bar=0.1, k_lo=1, k_hi=2, dt=0.002, rk_order=3, seed=5,
+                 init_energy=2.0)
+    kw = dict(qr_bins=16, q_lim=10.0, r_lim=10.0, tail_bins=64, tail_lo=-8, tail_hi=8, eps_norm=0.1, nu_norm=0.02)
+    h = E.hist_spec(grad_bins=128, grad_lim=8.0, **kw)
+    oh = O.HistSpec(grad_bins=128, grad_lim=8.0, **kw)
+    ens = E.Ensemble([m], hist=h)
+    ens.step(1)
+    ens.gradient_stats(accumulate=False)
+    counts, _ = ens.stats()
+    uh = ens.field(0)
+    rc, _ = O.gradient_stats(uh, m.nu, oh)
+    c, r = counts[0].astype(np.int64), rc.astype(np.int64)
+    N = 256
+    off = 16 * 16 + 2 * 64 + 8
+    assert c[off - 2] == N ** 3
+    worst = 0.0
+    for lo, hi, k in ((off, off + 128, 3), (off + 128, off + 256, 6)):
+        g = c[lo:hi].sum() + c[off + 256 + (0 if k == 3 else 2)] + c[off + 256 + (1 if k == 3 else 3)]
+        assert g == k * N ** 3
+        big = r[lo:hi] > 1000
+        assert big.sum() >= 20
+        dev = float((np.abs(c[lo:hi][big] - r[lo:hi][big]) / r[lo:hi][big]).max())
+        worst = max(worst, dev)
+        assert dev <= 0.02, (k, dev)
+    parity_log("256^3 gradient-component histograms on the same field, max bin deviation (bins > 1000)", worst, 0.02)
+    # the Q-R / tail part is the one a context without gradient bins produces
+    ens0 = E.Ensemble([m], hist=E.hist_spec(**kw))
+    ens0.set_field(0, uh)
+    ens0.gradient_stats(accumulate=False)
+    c0, _ = ens0.stats()
+    assert np.array_equal(c0[0], counts[0][: len(c0[0])])
+    ens.close()
+    ens0.close()
+
+
 def test_mixture_matches_oracle(E, parity_log):
     lams = [-1.0, -0.3, 0.4, 1.1]
     ms = [E.Member(N=16, nu=0.05, lam=l, k_lo=1, k_hi=2, dt=0.01, rk_order=2, seed=i) for i, l in enumerate(lams)]
